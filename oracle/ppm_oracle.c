@@ -1,0 +1,743 @@
+/*
+ * ppm_oracle.c -- FP64 CPU oracle of the energy-resolved pulse-profile
+ * forward model and Poisson likelihood of Zhou & Huang, "GPU-accelerated
+ * X-ray pulse profile modeling" (arXiv 2510.07764).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * reference that the CUDA path is checked against.  It is called only by the
+ * test-suite, by the smoke check and by the CPU-baseline leg of the
+ * benchmark; the library's product path never links, loads or calls it.  It
+ * shares no code, header, table or constant generator with the CUDA path.
+ *
+ * Everything is double precision, single threaded, in the order of the
+ * paper's computation recipe (Sect. 2.8):
+ *   light bending + time delay integrals  .... Sect. 2.3, Eqs. salmi_lf,
+ *                                              salmi_td, rho, tot_time_delay
+ *   lens-table generation ................... Sect. 2.8.2
+ *   star shape, slope, gravity .............. Sect. 2.1-2.2, Eqs. def_f,
+ *                                              Rtheta, Omega_c_def, area_oblate
+ *   Doppler / aberration .................... Sect. 2.4, App. A
+ *   per-ring pseudo-patch template .......... Sect. 2.8.3 (steps 1-5)
+ *   invisible-segment fill .................. Sect. 2.8.3
+ *   shift-and-add ........................... Sect. 2.8.3, Eq. add_Ft
+ *   flux formula ............................ Sect. 2.5, App. C
+ *   mixed-order atmosphere interpolation .... Sect. 4
+ *   ISM, response ........................... Sect. 2.7, 2.8.4
+ *   Poisson log-likelihood .................. Sect. 5 (Eq. chi2_def context), Sect. 6
+ *
+ * Where the paper is silent the reading is stated next to the code.
+ * Compile with -ffp-contract=off so x86 and Arm builds round identically.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- physical constants (CODATA 2018, IAU 2015 nominal GM_sun) ---- */
+#define ORC_PI 3.14159265358979323846
+static const double GM_SUN = 1.32712440018e20;      /* m^3 s^-2 */
+static const double C_MS = 299792458.0;             /* m s^-1 */
+static const double C_CMS = 29979245800.0;          /* cm s^-1 */
+static const double H_KEVS = 4.135667696e-18;       /* keV s */
+static const double KB_KEVK = 8.617333262e-8;       /* keV K^-1 */
+static const double KPC_M = 3.0856775814913673e19;  /* m */
+
+/* =====================================================================
+ * Adaptive Gauss-Kronrod (7,15) quadrature
+ * ===================================================================== */
+typedef double (*orc_fn)(double x, const void *ctx);
+
+static const double XGK[8] = {
+    0.991455371120812639206854697526329, 0.949107912342758524526189684047851,
+    0.864864423359769072789712788640926, 0.741531185599394439863864773280788,
+    0.586087235467691130294144845693013, 0.405845151377397166906606412076961,
+    0.207784955007898467600689403773245, 0.0};
+static const double WGK[8] = {
+    0.022935322010529224963732008058970, 0.063092092629978553290700663189204,
+    0.104790010322250183839876322541518, 0.140653259715525918745189590510238,
+    0.169004726639267902826583426598550, 0.190350578064785409913256402421014,
+    0.204432940075298892414161999234649, 0.209482141084727828012999174891714};
+static const double WG7[4] = {
+    0.129484966168869693270611432679082, 0.279705391489276667901467771423780,
+    0.381830050505118944950369775488975, 0.417959183673469387755102040816327};
+
+static void gk15(orc_fn f, const void *ctx, double a, double b, double *res, double *err)
+{
+    double c = 0.5 * (a + b), h = 0.5 * (b - a);
+    double fc = f(c, ctx);
+    double rk = fc * WGK[7], rg = fc * WG7[3];
+    for (int j = 0; j < 7; j++) {
+        double dx = h * XGK[j];
+        double f1 = f(c - dx, ctx), f2 = f(c + dx, ctx);
+        rk += WGK[j] * (f1 + f2);
+        if (j % 2 == 1) rg += WG7[j / 2] * (f1 + f2);
+    }
+    *res = rk * h;
+    *err = fabs((rk - rg) * h);
+}
+
+static double adapt(orc_fn f, const void *ctx, double a, double b, double whole,
+                    double tol, int depth)
+{
+    double r, e;
+    gk15(f, ctx, a, b, &r, &e);
+    if (e <= tol || depth >= 48 || (b - a) < 1e-15 * (1.0 + fabs(a))) return r;
+    double m = 0.5 * (a + b);
+    return adapt(f, ctx, a, m, whole, 0.5 * tol, depth + 1) +
+           adapt(f, ctx, m, b, whole, 0.5 * tol, depth + 1);
+}
+
+/* integral over [a, b] to ~1e-14 relative */
+static double integrate(orc_fn f, const void *ctx, double a, double b)
+{
+    double r, e;
+    gk15(f, ctx, a, b, &r, &e);
+    double tol = 1e-14 * fabs(r) + 1e-300;
+    if (e <= tol) return r;
+    double m = 0.5 * (a + b);
+    return adapt(f, ctx, a, m, r, 0.5 * tol, 1) + adapt(f, ctx, m, b, r, 0.5 * tol, 1);
+}
+
+/* =====================================================================
+ * Light bending and time delay (Sect. 2.3, 2.8.2)
+ * ===================================================================== */
+typedef struct { double u, c2, s2; } bend_ctx;
+
+/* q(x) = [2 - x^2 - u (1-x^2)^2 / (1-u)] sin^2(alpha)   (Eq. under salmi_lf) */
+static double bend_q(double x, const bend_ctx *b)
+{
+    double y = 1.0 - x * x;
+    return (2.0 - x * x - b->u * y * y / (1.0 - b->u)) * b->s2;
+}
+
+static double psi_integrand(double x, const void *p)
+{
+    const bend_ctx *b = (const bend_ctx *)p;
+    return x / sqrt(b->c2 + x * x * bend_q(x, b));
+}
+
+static double td_integrand(double x, const void *p)
+{
+    const bend_ctx *b = (const bend_ctx *)p;
+    double w = sqrt(b->c2 + x * x * bend_q(x, b));
+    return x / (w * (1.0 + w));
+}
+
+/* integrate on [0,1] with extra break points near x ~ |cos alpha| where the
+ * integrand turns over for near-grazing rays */
+static double bend_integral(orc_fn f, const bend_ctx *b)
+{
+    double c = sqrt(b->c2);
+    double brk[4];
+    int nb = 0;
+    brk[nb++] = 0.0;
+    if (c > 0.0 && c < 0.1) {
+        brk[nb++] = c;
+        if (10.0 * c < 0.5) brk[nb++] = 10.0 * c;
+    }
+    brk[nb++] = 1.0;
+    double s = 0.0;
+    for (int i = 0; i + 1 < nb; i++) s += integrate(f, b, brk[i], brk[i + 1]);
+    return s;
+}
+
+/* Eq. salmi_lf: bending angle psi(u, alpha) of an outgoing ray, alpha <= pi/2 */
+double orc_psi_out(double u, double alpha)
+{
+    double s = sin(alpha), c = cos(alpha);
+    if (s == 0.0) return 0.0;
+    bend_ctx b = {u, c * c, s * s};
+    return 2.0 * s / sqrt(1.0 - u) * bend_integral(psi_integrand, &b);
+}
+
+/* Eq. salmi_td: c Delta t_p / R of an outgoing ray, alpha <= pi/2 */
+double orc_td_out(double u, double alpha)
+{
+    double s = sin(alpha), c = cos(alpha);
+    if (s == 0.0) return 0.0;
+    bend_ctx b = {u, c * c, s * s};
+    return 2.0 * s * s / (1.0 - u) * bend_integral(td_integrand, &b);
+}
+
+/* Eq. rho: periastron radius / R of an inward ray (alpha > pi/2).
+ * Returns NaN when the arccos argument exceeds 1 (ray captured; reading). */
+double orc_rho(double u, double alpha)
+{
+    double s = sin(alpha);
+    double k = sqrt(3.0 * (1.0 - u));
+    double arg = 3.0 * u * k / (2.0 * s);
+    if (!(arg <= 1.0)) return NAN;
+    return -2.0 * s / k * cos((acos(arg) + 2.0 * ORC_PI) / 3.0);
+}
+
+/* psi(u, alpha) for any alpha: inward rays use 2 psi(u/rho, pi/2) - psi(u, pi-alpha) */
+double orc_psi(double u, double alpha)
+{
+    if (alpha <= 0.5 * ORC_PI) return orc_psi_out(u, alpha);
+    double rho = orc_rho(u, alpha);
+    if (isnan(rho)) return NAN;
+    return 2.0 * orc_psi_out(u / rho, 0.5 * ORC_PI) - orc_psi_out(u, ORC_PI - alpha);
+}
+
+/* c Delta t / R for any alpha.  Inward rays (reading of Eq. tot_time_delay):
+ * the periastron leg Delta t_p(u_p, pi/2) is measured in units of R_p = rho R,
+ * and the radial-delay difference 2[delta t(R_p) - delta t(R)] is folded into
+ * the table so that the run-time delay is (R/c) TD + delta t(R) for every ray:
+ *   TD = 2 rho TDp(u/rho, pi/2) - TDp(u, pi - alpha)
+ *        + 2 [(1 - rho) + u ln((1 - u) / (rho - u))].                        */
+double orc_td(double u, double alpha)
+{
+    if (alpha <= 0.5 * ORC_PI) return orc_td_out(u, alpha);
+    double rho = orc_rho(u, alpha);
+    if (isnan(rho)) return NAN;
+    return 2.0 * rho * orc_td_out(u / rho, 0.5 * ORC_PI) - orc_td_out(u, ORC_PI - alpha) +
+           2.0 * ((1.0 - rho) + u * log((1.0 - u) / (rho - u)));
+}
+
+/* =====================================================================
+ * Lens tables C_alpha, LF on (u, cos psi) and TD on (u, cos alpha)
+ * (Sect. 2.8.2)
+ * ===================================================================== */
+typedef struct {
+    double u_min, u_max; int n_u;
+    double cpsi_min, cpsi_max; int n_cpsi;
+    double calpha_min, calpha_max; int n_calpha;
+    double dalpha;
+} orc_lens_spec;
+
+typedef struct {
+    orc_lens_spec spec;
+    const double *Ca;  /* [n_u][n_cpsi] cos alpha, NaN = not reached */
+    const double *LF;  /* [n_u][n_cpsi] d cos alpha / d cos psi */
+    const double *TD;  /* [n_u][n_calpha] c Delta t / R, NaN = captured */
+} orc_lens;
+
+/* Linspace(x_min, x_max, n)[i] */
+static double linspace_at(double lo, double hi, int n, int i)
+{
+    return lo + (hi - lo) * (double)i / (double)(n - 1);
+}
+
+/* Build the three tables.  For each u: march alpha = 0, dalpha, 2 dalpha, ...
+ * appending (alpha, psi) until psi > arccos(cpsi_min); the march also stops
+ * (reading) when the ray is captured or psi would pass pi.  Convert to
+ * (cos psi, cos alpha); d cos alpha / d cos psi by central differences on the
+ * list (one-sided at the two ends, reading); linear interpolation of both
+ * lists onto the cos psi grid (reading); grid points beyond the march are NaN.
+ * TD is evaluated directly at every (u, cos alpha) grid point.
+ * Returns the longest march length, or -1 on bad input. */
+int orc_lens_build(const orc_lens_spec *sp, double *Ca, double *LF, double *TD)
+{
+    if (sp->n_u < 2 || sp->n_cpsi < 2 || sp->n_calpha < 2 || !(sp->dalpha > 0.0)) return -1;
+    int cap = (int)(ORC_PI / sp->dalpha) + 4;
+    double *lp = (double *)malloc(sizeof(double) * cap);
+    double *la = (double *)malloc(sizeof(double) * cap);
+    double *ld = (double *)malloc(sizeof(double) * cap);
+    double psi_stop = acos(sp->cpsi_min);
+    int longest = 0;
+    for (int iu = 0; iu < sp->n_u; iu++) {
+        double u = linspace_at(sp->u_min, sp->u_max, sp->n_u, iu);
+        int n = 0;
+        for (int j = 0; j < cap; j++) {
+            double alpha = j * sp->dalpha;
+            if (alpha > ORC_PI) break;
+            double psi = orc_psi(u, alpha);
+            if (isnan(psi) || psi > ORC_PI) break;
+            lp[n] = cos(psi);
+            la[n] = cos(alpha);
+            n++;
+            if (psi > psi_stop) break;
+        }
+        if (n > longest) longest = n;
+        for (int j = 0; j < n; j++) {
+            int a = j > 0 ? j - 1 : j, b = j < n - 1 ? j + 1 : j;
+            ld[j] = (b > a) ? (la[b] - la[a]) / (lp[b] - lp[a]) : NAN;
+        }
+        for (int ic = 0; ic < sp->n_cpsi; ic++) {
+            double cp = linspace_at(sp->cpsi_min, sp->cpsi_max, sp->n_cpsi, ic);
+            double *ca = &Ca[(size_t)iu * sp->n_cpsi + ic];
+            double *lf = &LF[(size_t)iu * sp->n_cpsi + ic];
+            if (n < 2 || cp < lp[n - 1]) { *ca = NAN; *lf = NAN; continue; }
+            /* lp is decreasing: find j with lp[j] >= cp >= lp[j+1] */
+            int lo = 0, hi = n - 1;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) / 2;
+                if (lp[mid] >= cp) lo = mid; else hi = mid;
+            }
+            double w = (cp - lp[lo]) / (lp[hi] - lp[lo]);
+            *ca = la[lo] + w * (la[hi] - la[lo]);
+            *lf = ld[lo] + w * (ld[hi] - ld[lo]);
+        }
+        for (int ia = 0; ia < sp->n_calpha; ia++) {
+            double ca = linspace_at(sp->calpha_min, sp->calpha_max, sp->n_calpha, ia);
+            TD[(size_t)iu * sp->n_calpha + ia] = orc_td(u, acos(ca));
+        }
+    }
+    free(lp); free(la); free(ld);
+    return longest;
+}
+
+/* Bilinear lookup of C_alpha and LF at (u, cos psi) (reading: bilinear).
+ * Returns 1 if all four corners are valid, 0 otherwise (point invisible). */
+int orc_lens_lookup(const orc_lens *L, double u, double cpsi, double *ca, double *lf)
+{
+    const orc_lens_spec *s = &L->spec;
+    double fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
+    double fc = (cpsi - s->cpsi_min) / (s->cpsi_max - s->cpsi_min) * (s->n_cpsi - 1);
+    int iu = (int)floor(fu), ic = (int)floor(fc);
+    if (iu < 0) iu = 0;
+    if (iu > s->n_u - 2) iu = s->n_u - 2;
+    if (ic < 0) ic = 0;
+    if (ic > s->n_cpsi - 2) ic = s->n_cpsi - 2;
+    double tu = fu - iu, tc = fc - ic;
+    size_t k00 = (size_t)iu * s->n_cpsi + ic, k10 = k00 + s->n_cpsi;
+    double a00 = L->Ca[k00], a01 = L->Ca[k00 + 1], a10 = L->Ca[k10], a11 = L->Ca[k10 + 1];
+    double d00 = L->LF[k00], d01 = L->LF[k00 + 1], d10 = L->LF[k10], d11 = L->LF[k10 + 1];
+    if (isnan(a00) || isnan(a01) || isnan(a10) || isnan(a11)) return 0;
+    *ca = (1.0 - tu) * ((1.0 - tc) * a00 + tc * a01) + tu * ((1.0 - tc) * a10 + tc * a11);
+    *lf = (1.0 - tu) * ((1.0 - tc) * d00 + tc * d01) + tu * ((1.0 - tc) * d10 + tc * d11);
+    return 1;
+}
+
+/* Bilinear lookup of TD at (u, cos alpha); cos alpha is clamped to the grid. */
+double orc_td_lookup(const orc_lens *L, double u, double calpha)
+{
+    const orc_lens_spec *s = &L->spec;
+    if (calpha < s->calpha_min) calpha = s->calpha_min;
+    if (calpha > s->calpha_max) calpha = s->calpha_max;
+    double fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
+    double fc = (calpha - s->calpha_min) / (s->calpha_max - s->calpha_min) * (s->n_calpha - 1);
+    int iu = (int)floor(fu), ic = (int)floor(fc);
+    if (iu < 0) iu = 0;
+    if (iu > s->n_u - 2) iu = s->n_u - 2;
+    if (ic < 0) ic = 0;
+    if (ic > s->n_calpha - 2) ic = s->n_calpha - 2;
+    double tu = fu - iu, tc = fc - ic;
+    size_t k00 = (size_t)iu * s->n_calpha + ic, k10 = k00 + s->n_calpha;
+    return (1.0 - tu) * ((1.0 - tc) * L->TD[k00] + tc * L->TD[k00 + 1]) +
+           tu * ((1.0 - tc) * L->TD[k10] + tc * L->TD[k10 + 1]);
+}
+
+/* =====================================================================
+ * Atmosphere table and mixed-order interpolation (Sect. 4)
+ * ===================================================================== */
+typedef struct {
+    int nT, ng, nmu, nE, n_protect;
+    const double *logT, *logg, *mu, *lnE;  /* node positions */
+    const float *I;                         /* [nT][ng][nmu][nE], linear intensity */
+} orc_atm;
+
+/* interval index i with x[i] <= q < x[i+1] after clamping q to [x0, x_{n-1}] */
+static int find_interval(const double *x, int n, double *q)
+{
+    if (*q <= x[0]) { *q = x[0]; return 0; }
+    if (*q >= x[n - 1]) { *q = x[n - 1]; return n - 2; }
+    int lo = 0, hi = n - 1;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) / 2;
+        if (x[mid] <= *q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Interpolation weights along one axis.  Writes node indices idx[] and
+ * weights w[] (n_taps = 2 or 4).  cubic: Lagrange on the four nodes
+ * i-1..i+2 around interval i (actual node positions); falls back to linear
+ * on (i, i+1) when the interval lies in the protected zone (i < n_protect-1)
+ * or when the four-node stencil would leave the grid. */
+static int axis_weights(const double *x, int n, double q, int cubic, int n_protect,
+                        int *idx, double *w)
+{
+    int i = find_interval(x, n, &q);
+    if (cubic && i >= 1 && i + 2 <= n - 1 && i >= n_protect - 1) {
+        for (int a = 0; a < 4; a++) {
+            int ka = i - 1 + a;
+            double l = 1.0;
+            for (int b = 0; b < 4; b++) {
+                if (b == a) continue;
+                int kb = i - 1 + b;
+                l *= (q - x[kb]) / (x[ka] - x[kb]);
+            }
+            idx[a] = ka;
+            w[a] = l;
+        }
+        return 4;
+    }
+    double t = (q - x[i]) / (x[i + 1] - x[i]);
+    idx[0] = i; w[0] = 1.0 - t;
+    idx[1] = i + 1; w[1] = t;
+    return 2;
+}
+
+/* I(E', mu; logT, logg): linear in logT and logg, cubic (mixed) in mu and ln E.
+ * Out-of-range queries clamp to the edge node; negative interpolants are kept. */
+double orc_atm_interp(const orc_atm *A, double logT, double logg, double mu, double E_keV)
+{
+    int iT[4], ig[4], im[4], ie[4];
+    double wT[4], wg[4], wm[4], we[4];
+    int nT = axis_weights(A->logT, A->nT, logT, 0, 0, iT, wT);
+    int ng = axis_weights(A->logg, A->ng, logg, 0, 0, ig, wg);
+    int nm = axis_weights(A->mu, A->nmu, mu, 1, A->n_protect, im, wm);
+    int ne = axis_weights(A->lnE, A->nE, log(E_keV), 1, 0, ie, we);
+    double v = 0.0;
+    for (int a = 0; a < nT; a++)
+        for (int b = 0; b < ng; b++)
+            for (int c = 0; c < nm; c++)
+                for (int d = 0; d < ne; d++) {
+                    size_t k = (((size_t)iT[a] * A->ng + ig[b]) * A->nmu + im[c]) * A->nE + ie[d];
+                    v += wT[a] * wg[b] * wm[c] * we[d] * (double)A->I[k];
+                }
+    return v;
+}
+
+/* comoving blackbody specific intensity 2 E^3 / (h^3 c^2) / (e^{E/kT} - 1)
+ * in keV cm^-2 s^-1 keV^-1 sr^-1 (App. C) */
+double orc_bb_intensity(double E_keV, double kT_keV)
+{
+    return 2.0 * E_keV * E_keV * E_keV / (H_KEVS * H_KEVS * H_KEVS * C_CMS * C_CMS) /
+           expm1(E_keV / kT_keV);
+}
+
+/* =====================================================================
+ * Star, rings, elements (Sect. 2.1, 2.2, 2.4, 2.6)
+ * ===================================================================== */
+typedef struct {
+    double mass_msun, radius_km, spin_hz, incl_rad, dist_kpc, nh_1e20;
+    double colat[2], azim[2], zeta[2], logT[2], mask_colat[2], mask_azim[2], mask_zeta[2];
+    int n_spots, oblate, emission, n_theta, n_phi, n_phase, n_fp;
+} orc_inst;
+
+typedef struct {
+    double GM, Rs, Re, nu, Obar, x, o2, g0, sini, cosi, D;
+    int oblate;
+} orc_star;
+
+static void star_init(const orc_inst *in, orc_star *s)
+{
+    s->GM = in->mass_msun * GM_SUN;
+    s->Rs = 2.0 * s->GM / (C_MS * C_MS);
+    s->Re = in->radius_km * 1e3;
+    s->nu = in->spin_hz;
+    s->Obar = 2.0 * ORC_PI * s->nu * sqrt(s->Re * s->Re * s->Re / s->GM);  /* Eq. Omega_c_def */
+    s->x = s->GM / (C_MS * C_MS * s->Re);
+    s->oblate = in->oblate;
+    /* Eq. Rtheta; the S+D mode is the spherical star o2 = 0 */
+    s->o2 = in->oblate ? s->Obar * s->Obar * (-0.788 + 1.030 * s->x) : 0.0;
+    s->g0 = s->GM / (s->Re * s->Re) / sqrt(1.0 - s->Rs / s->Re);
+    s->sini = sin(in->incl_rad);
+    s->cosi = cos(in->incl_rad);
+    s->D = in->dist_kpc * KPC_M;
+}
+
+typedef struct {
+    double theta, dcos, R, u, f, cos_eta, sin_eta, logg, beta, gamma;
+} orc_ring;
+
+/* Ring quantities at colatitude theta (Eqs. Rtheta, def_f, the g(theta)
+ * polynomial of Sect. 2.2, beta/gamma of Sect. 2.4).  Readings: R and u are
+ * the local R(theta), u(theta) (Omega_bar and x use R_e); dR/dtheta =
+ * -2 o2 R_e cos(theta) sin(theta); in the S+D mode g = g0. */
+static void ring_geom(const orc_star *s, double theta, double dcos, orc_ring *r)
+{
+    double ct = cos(theta), st = sin(theta);
+    r->theta = theta;
+    r->dcos = dcos;
+    r->R = s->Re * (1.0 + s->o2 * ct * ct);
+    r->u = s->Rs / r->R;
+    double dRdth = -2.0 * s->o2 * s->Re * ct * st;
+    r->f = dRdth / (r->R * sqrt(1.0 - r->u));
+    r->cos_eta = 1.0 / sqrt(1.0 + r->f * r->f);
+    r->sin_eta = r->f / sqrt(1.0 + r->f * r->f);
+    double g = s->g0;
+    if (s->oblate) {
+        double O2 = s->Obar * s->Obar, O4 = O2 * O2, O6 = O4 * O2, x = s->x;
+        double c2 = ct * ct, s2 = st * st;
+        double ratio = 1.0
+            + s2 * (O2 * (-0.791 + 0.776 * x) + O4 * (-1.315 * x + 2.431 * x * x) + O6 * (-1.172 * x))
+            + c2 * (O2 * (1.138 - 1.431 * x) + O4 * (0.653 * x - 2.864 * x * x) + O6 * (0.975 * x)
+                    - O4 * (13.47 * x - 27.13 * x * x))
+            + fabs(ct) * O4 * (13.47 * x - 27.13 * x * x);
+        g = s->g0 * ratio;
+    }
+    r->logg = log10(g * 100.0); /* m s^-2 -> cm s^-2 */
+    r->beta = 2.0 * ORC_PI * s->nu * r->R * st / (C_MS * sqrt(1.0 - r->u));
+    r->gamma = 1.0 / sqrt(1.0 - r->beta * r->beta);
+}
+
+/* Element grid of one spot (reading): n_theta rings uniform in theta over
+ * [max(0, theta_c - zeta), min(pi, theta_c + zeta)]; each ring holds n_phi
+ * elements uniform over the emitter's azimuth span phi_c +- Delta_i; an
+ * element is active unless its centre lies inside the spot's masking cap. */
+static void ring_of_spot(const orc_inst *in, int spot, int r, double *theta,
+                         double *dcos, double *half)
+{
+    double tc = in->colat[spot], z = in->zeta[spot];
+    double lo = tc - z > 0.0 ? tc - z : 0.0;
+    double hi = tc + z < ORC_PI ? tc + z : ORC_PI;
+    double dth = (hi - lo) / in->n_theta;
+    double e0 = lo + r * dth, e1 = lo + (r + 1) * dth;
+    *theta = lo + (r + 0.5) * dth;
+    *dcos = cos(e0) - cos(e1);
+    double num = cos(z) - cos(*theta) * cos(tc);
+    double den = sin(*theta) * sin(tc);
+    if (den <= 0.0) {
+        *half = num <= 0.0 ? ORC_PI : 0.0;
+    } else {
+        double a = num / den;
+        if (a < -1.0) a = -1.0;
+        if (a > 1.0) a = 1.0;
+        *half = acos(a);
+    }
+}
+
+static int element_active(const orc_inst *in, int spot, double theta, double phi)
+{
+    double mz = in->mask_zeta[spot];
+    if (!(mz > 0.0)) return 1;
+    double cd = cos(theta) * cos(in->mask_colat[spot]) +
+                sin(theta) * sin(in->mask_colat[spot]) * cos(phi - in->mask_azim[spot]);
+    return !(cd > cos(mz));
+}
+
+/* =====================================================================
+ * Per-ring pseudo-patch template (Sect. 2.8.3, steps 1-5, and the
+ * invisible-segment fill).  Arrays have n_fp + 1 entries.
+ * Returns 1 if the ring contributes, 0 if it is invisible at i_fp = 0
+ * (whole ring skipped), -1 if u lies outside the lens table.
+ * ===================================================================== */
+static int ring_template(const orc_star *s, const orc_ring *rg, double dphi,
+                         const orc_lens *L, int n_fp, double *F, double *z,
+                         double *phio, double *mu)
+{
+    const orc_lens_spec *ls = &L->spec;
+    if (rg->u < ls->u_min || rg->u > ls->u_max) return -1;
+    double st = sin(rg->theta), ct = cos(rg->theta);
+    double sq = sqrt(1.0 - rg->u);
+    /* area element R^2 sqrt(1+f^2) dcos(theta) dphi / D^2 (Eq. area_oblate) */
+    double area = rg->R * rg->R * sqrt(1.0 + rg->f * rg->f) * rg->dcos * dphi / (s->D * s->D);
+    /* radial delay of emission radius R relative to R_e (Eq. delta_t_oblate) */
+    double dt_obl = (s->Re - rg->R + s->Rs * log((s->Re - s->Rs) / (rg->R - s->Rs))) / C_MS;
+    int inv_min = n_fp, inv_max = 0;
+    int vis0 = 0;
+    for (int i = 0; i <= n_fp; i++) {
+        if (i == n_fp) {
+            /* i_fp = N_fp is the same surface point as i_fp = 0 (reading:
+             * exact periodicity, phi_o[N_fp] = phi_o[0] + 1) */
+            if (vis0) {
+                F[i] = F[0]; z[i] = z[0]; mu[i] = mu[0]; phio[i] = phio[0] + 1.0;
+            } else {
+                F[i] = 0.0; mu[i] = 0.0; z[i] = 0.0; phio[i] = 0.0;
+            }
+            break;
+        }
+        double phi = 2.0 * ORC_PI * (double)i / (double)n_fp;
+        double cphi = cos(phi), sphi = sin(phi);
+        /* step 2: cos psi */
+        double cpsi = s->sini * st * cphi + s->cosi * ct;
+        int visible = 0;
+        double ca, lf;
+        /* step 3: lens lookup; points beyond the cos psi grid are invisible */
+        if (cpsi >= ls->cpsi_min && orc_lens_lookup(L, rg->u, cpsi, &ca, &lf)) {
+            double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
+            double sp = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
+            /* sin(alpha)/sin(psi); limit sqrt(LF) as psi -> 0 (reading) */
+            double ratio = sp > 1e-12 ? sa / sp : sqrt(lf);
+            /* step 4: Eq. sigma_relation */
+            double csig = ca * rg->cos_eta +
+                          ratio * rg->sin_eta * (s->cosi * st - s->sini * ct * cphi);
+            /* step 5 */
+            if (csig >= 0.0) {
+                visible = 1;
+                double cxi = -ratio * s->sini * sphi;          /* Table tab:angles */
+                double delta = 1.0 / (rg->gamma * (1.0 - rg->beta * cxi));
+                double m = delta * csig;                        /* mu = cos sigma' */
+                F[i] = sq * delta * delta * delta * m * lf * rg->gamma * area;
+                z[i] = 1.0 / (delta * sq);
+                double dt = rg->R / C_MS * orc_td_lookup(L, rg->u, ca) + dt_obl;
+                phio[i] = (double)i / (double)n_fp + s->nu * dt;
+                mu[i] = m;
+            }
+        }
+        if (i == 0) vis0 = visible;
+        if (!visible) {
+            if (i < inv_min) inv_min = i;
+            if (i > inv_max) inv_max = i;
+            F[i] = 0.0; mu[i] = 0.0; z[i] = 0.0; phio[i] = 0.0;
+        }
+    }
+    if (!vis0) return 0;
+    if (inv_min <= inv_max) {
+        int a = inv_min - 1, b = inv_max + 1;
+        for (int i = inv_min; i <= inv_max; i++) {
+            double t = (double)(i - a) / (double)(b - a);
+            F[i] = 0.0;
+            mu[i] = 0.0;
+            z[i] = z[a] + (z[b] - z[a]) * t;
+            phio[i] = phio[a] + (phio[b] - phio[a]) * t;
+        }
+    }
+    return 1;
+}
+
+/* =====================================================================
+ * Forward profile F_t (Sect. 2.8.3 shift-and-add, Eq. add_Ft)
+ * ===================================================================== */
+
+/* floor-mod into [0, 1) */
+static double frac1(double x) { return x - floor(x); }
+
+/* Linear interpolation of the template at phase phip (reading: linear,
+ * binary search on the monotone phi_o). */
+static void template_at(const double *phio, const double *F, const double *z,
+                        const double *mu, int n_fp, double phip,
+                        double *Fp, double *zp, double *mup)
+{
+    int lo = 0, hi = n_fp;
+    if (phip <= phio[0]) hi = 1;
+    else if (phip >= phio[n_fp]) lo = n_fp - 1;
+    else {
+        while (hi - lo > 1) {
+            int mid = (lo + hi) / 2;
+            if (phio[mid] <= phip) lo = mid; else hi = mid;
+        }
+    }
+    double w = (phip - phio[lo]) / (phio[lo + 1] - phio[lo]);
+    if (w < 0.0) w = 0.0;
+    if (w > 1.0) w = 1.0;
+    *Fp = F[lo] + (F[lo + 1] - F[lo]) * w;
+    *zp = z[lo] + (z[lo + 1] - z[lo]) * w;
+    *mup = mu[lo] + (mu[lo + 1] - mu[lo]) * w;
+}
+
+/* Status codes of the oracle */
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ERANGE = 2 };
+
+/* F_t[j][k] for the selected output phases jsel (indices into
+ * phi_out = j / n_phase) and energies ksel (indices into E_keV); NULL
+ * selects all.  ring_stride > 1 evaluates every ring_stride-th ring only
+ * (used to time a bounded sample).  Ft has n_j * n_k entries, row-major. */
+int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
+                const double *E_keV, int nE, const int *jsel, int nj,
+                const int *ksel, int nk, int ring_stride, double *Ft)
+{
+    if (in->n_spots < 1 || in->n_spots > 2 || in->n_theta < 1 || in->n_phi < 1 ||
+        in->n_phase < 1 || in->n_fp < 2 || nE < 1)
+        return ORC_EINVAL;
+    if (in->emission == 1 && A == NULL) return ORC_EINVAL;
+    if (ring_stride < 1) ring_stride = 1;
+    int NJ = jsel ? nj : in->n_phase;
+    int NK = ksel ? nk : nE;
+    memset(Ft, 0, sizeof(double) * (size_t)NJ * NK);
+    orc_star s;
+    star_init(in, &s);
+    int n_fp = in->n_fp;
+    double *F = (double *)malloc(sizeof(double) * (n_fp + 1));
+    double *z = (double *)malloc(sizeof(double) * (n_fp + 1));
+    double *ph = (double *)malloc(sizeof(double) * (n_fp + 1));
+    double *mu = (double *)malloc(sizeof(double) * (n_fp + 1));
+    int status = ORC_OK;
+    for (int sp = 0; sp < in->n_spots && status == ORC_OK; sp++) {
+        double logT = in->logT[sp];
+        double kT = KB_KEVK * pow(10.0, logT);
+        if (in->emission == 1 && (logT < A->logT[0] || logT > A->logT[A->nT - 1])) {
+            status = ORC_ERANGE;
+            break;
+        }
+        for (int r = 0; r < in->n_theta; r += ring_stride) {
+            double theta, dcos, half;
+            ring_of_spot(in, sp, r, &theta, &dcos, &half);
+            if (!(half > 0.0)) continue;
+            orc_ring rg;
+            ring_geom(&s, theta, dcos, &rg);
+            if (in->emission == 1 && (rg.logg < A->logg[0] || rg.logg > A->logg[A->ng - 1])) {
+                status = ORC_ERANGE;
+                break;
+            }
+            double dphi = 2.0 * half / in->n_phi;
+            int tv = ring_template(&s, &rg, dphi, L, n_fp, F, z, ph, mu);
+            if (tv < 0) { status = ORC_ERANGE; break; }
+            if (tv == 0) continue;
+            for (int m = 0; m < in->n_phi; m++) {
+                double phia = in->azim[sp] - half + (m + 0.5) * dphi;
+                if (!element_active(in, sp, theta, phia)) continue;
+                double sm = phia / (2.0 * ORC_PI);
+                for (int jj = 0; jj < NJ; jj++) {
+                    int j = jsel ? jsel[jj] : jj;
+                    double phi_out = (double)j / (double)in->n_phase;
+                    double phip = frac1(phi_out + sm + 1.0 - ph[0]) + ph[0];
+                    double Fp, zp, mup;
+                    template_at(ph, F, z, mu, n_fp, phip, &Fp, &zp, &mup);
+                    if (Fp == 0.0) continue;
+                    for (int kk = 0; kk < NK; kk++) {
+                        int k = ksel ? ksel[kk] : kk;
+                        double E = E_keV[k];
+                        double Ep = zp * E;
+                        double I = (in->emission == 1)
+                                       ? orc_atm_interp(A, logT, rg.logg, mup, Ep)
+                                       : orc_bb_intensity(Ep, kT);
+                        Ft[(size_t)jj * NK + kk] += Fp * I / E;
+                    }
+                }
+            }
+        }
+    }
+    free(F); free(z); free(ph); free(mu);
+    return status;
+}
+
+/* Ring quantities and template for tests: fills info[0..15] =
+ * {theta, dcos, half_width, R, u, f, cos_eta, sin_eta, logg, beta, gamma,
+ *  area_dphi, n_active, status} and the four template arrays. */
+int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
+                      double *info, double *F, double *z, double *phio, double *mu)
+{
+    orc_star s;
+    star_init(in, &s);
+    double theta, dcos, half;
+    ring_of_spot(in, spot, r, &theta, &dcos, &half);
+    orc_ring rg;
+    ring_geom(&s, theta, dcos, &rg);
+    double dphi = 2.0 * half / in->n_phi;
+    int nact = 0;
+    for (int m = 0; m < in->n_phi; m++)
+        nact += element_active(in, spot, theta, in->azim[spot] - half + (m + 0.5) * dphi);
+    int st = half > 0.0 ? ring_template(&s, &rg, dphi, L, in->n_fp, F, z, phio, mu) : 0;
+    double v[14] = {rg.theta, rg.dcos, half, rg.R, rg.u, rg.f, rg.cos_eta, rg.sin_eta,
+                    rg.logg, rg.beta, rg.gamma, dphi, (double)nact, (double)st};
+    memcpy(info, v, sizeof(v));
+    return st;
+}
+
+/* =====================================================================
+ * ISM, response and Poisson likelihood (Sect. 2.7, 2.8.4, 6)
+ * ===================================================================== */
+
+/* C[j][c] = sum_k Ft[j][k] ATT_k R[k][c], ATT_k = exp(-N_H sigma_k) */
+void orc_counts(const double *Ft, int n_phase, int nE, const float *R, int nc,
+                const float *sigma, double nh_1e20, double *C)
+{
+    double nh = nh_1e20 * 1e20;
+    for (int j = 0; j < n_phase; j++)
+        for (int c = 0; c < nc; c++) {
+            double s = 0.0;
+            for (int k = 0; k < nE; k++)
+                s += Ft[(size_t)j * nE + k] * exp(-nh * (double)sigma[k]) * (double)R[(size_t)k * nc + c];
+            C[(size_t)j * nc + c] = s;
+        }
+}
+
+/* logL = sum d ln(lambda) - lambda - ln Gamma(d + 1), lambda = tau C + b.
+ * (reading: the Poisson log-likelihood; lambda = 0 gives 0 for d = 0 and
+ * -inf for d > 0). */
+double orc_loglike(const double *C, int n, const int *d, const float *bkg, double tau)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; i++) {
+        double lam = tau * C[i] + (bkg ? (double)bkg[i] : 0.0);
+        if (lam <= 0.0) {
+            if (d[i] > 0) return -INFINITY;
+            continue;
+        }
+        s += (double)d[i] * log(lam) - lam - lgamma((double)d[i] + 1.0);
+    }
+    return s;
+}

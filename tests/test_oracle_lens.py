@@ -1,0 +1,191 @@
+"""Pins of the oracle's light bending and time delay (Sect. 2.3, 2.8.2).
+
+Each check compares the oracle (Salmi-substitution integrals, Eqs. salmi_lf,
+salmi_td, evaluated by its own adaptive Gauss-Kronrod rule) with something
+computed independently here: the geodesic forms Eq. psi_integral and
+Eq. tp_direct integrated by scipy, brute-force RK4 integration of the
+Schwarzschild orbit equation, the cubic for the periastron, and the photon
+coordinate time along inward rays.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+U_VALUES = [0.2, 0.3445, 0.5, 0.537]
+A_OUT = [0.05, 0.4, 0.9, 1.2, 1.45, 1.55, 1.5702]
+
+
+def psi_geodesic(u, alpha):
+    """Eq. psi_integral with w = R/r, then w = 1 - t^2 (removes the grazing endpoint)."""
+    s2 = math.sin(alpha) ** 2
+
+    def f(t):
+        w = 1.0 - t * t
+        return 2.0 * t / math.sqrt((1.0 - u) / s2 - w * w * (1.0 - u * w))
+    return quad(f, 0.0, 1.0, epsabs=1e-15, epsrel=1e-14, limit=400)[0]
+
+
+def td_geodesic(u, alpha):
+    """Eq. tp_direct (units of R) with w = R/r, w = 1 - t^2."""
+    b2 = math.sin(alpha) ** 2 / (1.0 - u)
+
+    def f(t):
+        w = 1.0 - t * t
+        if w == 0.0:
+            return 0.0
+        inner = 1.0 - b2 * w * w * (1.0 - u * w)
+        return 2.0 * t / (w * w * (1.0 - u * w)) * (1.0 / math.sqrt(inner) - 1.0)
+    return quad(f, 0.0, 1.0, epsabs=1e-13, epsrel=1e-11, limit=400)[0]
+
+
+def rk4_psi(u, alpha, h=1e-3):
+    """Brute-force bending angle: integrate w'' = -w + 1.5 u w^2 (w = R/r) from
+    w = 1, w' = -sqrt(1-u) cot(alpha) until w = 0."""
+    def acc(w):
+        return -w + 1.5 * u * w * w
+    w, v, phi = 1.0, -math.sqrt(1.0 - u) * math.cos(alpha) / math.sin(alpha), 0.0
+
+    def step(w, v, hh):
+        k1w, k1v = v, acc(w)
+        k2w, k2v = v + 0.5 * hh * k1v, acc(w + 0.5 * hh * k1w)
+        k3w, k3v = v + 0.5 * hh * k2v, acc(w + 0.5 * hh * k2w)
+        k4w, k4v = v + hh * k3v, acc(w + hh * k3w)
+        return (w + hh / 6 * (k1w + 2 * k2w + 2 * k3w + k4w),
+                v + hh / 6 * (k1v + 2 * k2v + 2 * k3v + k4v))
+    while True:
+        w1, v1 = step(w, v, h)
+        if w1 <= 0.0:
+            break
+        w, v, phi = w1, v1, phi + h
+    lo, hi = 0.0, h   # bisection on the last step length
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if step(w, v, mid)[0] > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return phi + 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("u", U_VALUES)
+def test_psi_matches_geodesic_integral(orc, u):
+    for a in A_OUT:
+        assert orc.psi(u, a) == pytest.approx(psi_geodesic(u, a), rel=1e-11, abs=1e-12)
+
+
+@pytest.mark.parametrize("u", U_VALUES)
+def test_psi_matches_orbit_integration(orc, u):
+    # outgoing and inward rays (alpha > pi/2 passes through the periastron)
+    for a in [0.3, 1.0, 1.5, 1.62, 1.7, 1.8]:
+        if math.isnan(orc.rho(u, a)) and a > math.pi / 2:
+            continue
+        assert orc.psi(u, a) == pytest.approx(rk4_psi(u, a), abs=2e-9)
+
+
+@pytest.mark.parametrize("u", U_VALUES)
+def test_td_matches_geodesic_integral(orc, u):
+    for a in A_OUT:
+        assert orc.td(u, a) == pytest.approx(td_geodesic(u, a), rel=1e-10, abs=1e-12)
+
+
+def test_rho_is_root_of_periastron_cubic(orc):
+    # b^2 = r^2 / (1 - R_S / r) at the turning point: rho^3 - K rho + K u = 0, K = sin^2/(1-u)
+    for u in U_VALUES + [0.15, 0.6]:
+        for a in np.linspace(1.58, 3.0, 25):
+            s = math.sin(a)
+            K = s * s / (1.0 - u)
+            captured = s < 1.5 * math.sqrt(3.0) * u * math.sqrt(1.0 - u)   # b < b_crit
+            r = orc.rho(u, a)
+            if captured:
+                assert math.isnan(r)
+                continue
+            roots = np.roots([1.0, 0.0, -K, K * u])
+            real = sorted(x.real for x in roots if abs(x.imag) < 1e-9)
+            assert r == pytest.approx(real[-1], rel=1e-12)
+            assert r <= 1.0 + 1e-12 and r >= 1.5 * u - 1e-12
+    assert orc.rho(0.3, math.pi / 2) == pytest.approx(1.0, abs=1e-14)
+
+
+def test_inward_delay_equals_coordinate_time(orc):
+    """The inward-ray delay reading (Eq. tot_time_delay with the periastron leg
+    in units of R_p and the radial-delay difference folded in) equals the excess
+    coordinate time of the ray over a radial ray, integrated directly:
+    2 int_{R_p}^{R} dt/dr dr + (Eq. tp_direct for the outgoing leg)."""
+    for u in [0.2, 0.3445, 0.5]:
+        for a in [1.6, 1.7, 1.8]:
+            rho = orc.rho(u, a)
+            if math.isnan(rho):
+                continue
+            b2 = math.sin(a) ** 2 / (1.0 - u)
+
+            def g(s):   # r = rho + (1 - rho) s^2 removes the turning-point singularity
+                r = rho + (1.0 - rho) * s * s
+                inner = 1.0 - b2 * (1.0 - u / r) / (r * r)
+                return 2.0 * (1.0 - rho) * s / ((1.0 - u / r) * math.sqrt(max(inner, 0.0))) \
+                    if inner > 0 else 0.0
+            leg = quad(g, 0.0, 1.0, epsabs=1e-13, epsrel=1e-11, limit=400)[0]
+            direct = 2.0 * leg + td_geodesic(u, math.pi - a)
+            assert orc.td(u, a) == pytest.approx(direct, rel=1e-9)
+
+
+def test_flat_space_limits(orc):
+    # u -> 0: straight lines, psi = alpha and c Delta t / R = 1 - cos(alpha)
+    for a in [0.1, 0.8, 1.5]:
+        assert orc.psi(0.0, a) == pytest.approx(a, rel=1e-13)
+        assert orc.td(0.0, a) == pytest.approx(1.0 - math.cos(a), rel=1e-12)
+
+
+def test_limb_of_crescent_star(orc, synth):
+    # the crescent workload's colatitude assumes psi_limb(u = 0.537) = 165.5 deg
+    psi_limb = orc.psi(0.537, math.pi / 2) * 180 / math.pi
+    assert psi_limb == pytest.approx(165.5, abs=0.05)
+    assert synth.CRESCENT_COLAT * 180 / math.pi == pytest.approx(psi_limb - 5 - 85, abs=0.05)
+
+
+def test_lens_table_inverts_bending(orc, small_lens):
+    """Every tabulated cos(alpha) bends to its grid cos(psi) within the march
+    interpolation error (linear interpolation over d alpha = pi/2048)."""
+    L = orc.lens(small_lens)
+    sp = small_lens
+    us = np.linspace(sp.u_min, sp.u_max, sp.n_u)
+    cps = np.linspace(sp.cpsi_min, sp.cpsi_max, sp.n_cpsi)
+    rng = np.random.default_rng(1)
+    for _ in range(60):
+        iu, ic = rng.integers(sp.n_u), rng.integers(sp.n_cpsi)
+        ca = L.Ca[iu, ic]
+        assert np.isfinite(ca)
+        back = math.cos(orc.psi(us[iu], math.acos(ca)))
+        assert back == pytest.approx(cps[ic], abs=2e-6)
+
+
+def test_lens_factor_is_derivative(orc, small_lens):
+    """LF = d cos(alpha)/d cos(psi): compare with the exact derivative
+    sin(alpha) / (sin(psi) dpsi/dalpha) from the oracle's psi."""
+    L = orc.lens(small_lens)
+    sp = small_lens
+    us = np.linspace(sp.u_min, sp.u_max, sp.n_u)
+    cps = np.linspace(sp.cpsi_min, sp.cpsi_max, sp.n_cpsi)
+    for iu in [0, 40, 128]:
+        for ic in [5, 100, 300, 480]:
+            a = math.acos(L.Ca[iu, ic])
+            h = 1e-6
+            dpsi = (orc.psi(us[iu], a + h) - orc.psi(us[iu], a - h)) / (2 * h)
+            exact = math.sin(a) / (math.sin(orc.psi(us[iu], a)) * dpsi)
+            assert L.LF[iu, ic] == pytest.approx(exact, rel=2e-4)
+
+
+def test_lens_table_coverage(orc, synth):
+    """The default grid reaches cos(psi) = -0.995 on every row; TD is NaN only
+    for captured rays."""
+    sp = synth.LensSpec(n_u=10, n_cpsi=64, n_calpha=64)
+    L = orc.Lens(sp)
+    assert np.isfinite(L.Ca).all() and np.isfinite(L.LF).all()
+    us = np.linspace(sp.u_min, sp.u_max, sp.n_u)
+    cas = np.linspace(sp.calpha_min, sp.calpha_max, sp.n_calpha)
+    for iu, u in enumerate(us):
+        for ia, ca in enumerate(cas):
+            s = math.sqrt(1 - ca * ca)
+            captured = ca < 0 and s < 1.5 * math.sqrt(3.0) * u * math.sqrt(1.0 - u)
+            assert np.isnan(L.TD[iu, ia]) == captured
