@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the pulse-profile likelihood on GB300.
+
+One step = one full likelihood evaluation (ring templates, shift-and-add with
+atmosphere interpolation, ISM, response contraction, Poisson logL) of the
+workload's parameter vectors.  Default workload: two hotspots (cap + ring)
+x 128x128 elements, 128 phases, 256 energies, 300 channels, synthetic
+35x11x67x166 atmosphere table, oblate Schwarzschild, one parameter vector.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank evaluates
+its own copies of the workload (replicas, weak scaling; no collective on the
+data path).  ``--impl reference`` times the FP64 CPU oracle on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PPM likelihood evals/s (ms/eval) at 1e-3 rel. accuracy; batched & grad evals/s"
+FLOP_PER_TRIPLE = 14          # algorithmic FP32 flops per (element, phase, energy) triple
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_shift_add_atm_two_spot.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2510_07764_gb300", "csrc", "shift_add.cu")
+REF_RING_STRIDE = 64
+CPU_RING_STRIDE = 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="atm_two_spot")
+    ap.add_argument("--flush-mib", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(w):
+    inst = w.inst
+    return {
+        "workload": w.name,
+        "B": int(inst.B),
+        "spots": int(inst.n_spots),
+        "elements_per_spot": "%dx%d" % (int(inst.n_theta[0]), int(inst.n_phi[0])),
+        "phases": int(inst.n_phase[0]),
+        "energies": int(len(w.E_keV)),
+        "channels": int(w.nc),
+        "n_fp": int(inst.n_fp),
+        "spacetime": "oblate Schwarzschild" if inst.oblate else "Schwarzschild+Doppler",
+        "emission": "atmosphere table 35x11x67x166" if inst.emission else "analytic blackbody",
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = os.path.join("/tmp", "ppm_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def profile_traffic():
+    """dram bytes per launch of the shift-and-add kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    txt = open(PROFILE_SUMMARY).read()
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m and t):
+        return None
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    return float(t.group(1)) if m.group(1) == sha else None
+
+
+def cpu_baseline(w):
+    """The FP64 oracle on every CPU_RING_STRIDE-th ring, extrapolated to one evaluation."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    oracle.lens(w.lens)   # table build is not part of an evaluation
+    t0 = time.perf_counter()
+    Ft = oracle.profile(w, ring_stride=CPU_RING_STRIDE)
+    C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
+    oracle.loglike(C, w.counts, w.tau)
+    dt = time.perf_counter() - t0
+    per_eval = dt * CPU_RING_STRIDE
+    rings = int(np.sum(w.inst.n_theta)) * w.inst.n_spots
+    return {"value": 1.0 / per_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "sample": "every %dth ring (%d of %d rings), all phases x energies, response and logL; "
+                      "%.1f s measured, extrapolated x%d" % (CPU_RING_STRIDE,
+                                                              rings // CPU_RING_STRIDE, rings, dt,
+                                                              CPU_RING_STRIDE)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2510_07764_gb300 import synth
+    import oracle
+    w = synth.WORKLOADS[args.workload]()
+    oracle.build()
+    oracle.lens(w.lens)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        Ft = oracle.profile(w, ring_stride=REF_RING_STRIDE)
+        C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
+        oracle.loglike(C, w.counts, w.tau)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt * REF_RING_STRIDE)
+    per_eval = sum(times) / len(times)
+    value = 1.0 / per_eval
+    sample = ("every %dth ring per step, extrapolated x%d to one evaluation"
+              % (REF_RING_STRIDE, REF_RING_STRIDE))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_eval * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(w),
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from paper_2510_07764_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.WORKLOADS[args.workload]()
+    ctx = ppm.Context(local_rank)
+    t0 = time.perf_counter()
+    ctx.setup(w)
+    setup_s = time.perf_counter() - t0
+    dp = ppm.DeviceParams(w.inst, device=dev)
+    B = dp.B
+    counts = torch.from_numpy(w.counts).to(dev)
+    logL = torch.empty(B, dtype=torch.float64, device=dev)
+    flush = torch.empty(args.flush_mib * (1 << 20) // 4, dtype=torch.float32, device=dev)
+    dist = world > 1
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        ctx.loglike(dp, counts, w.tau, out=logL)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM; L2 flushed before each)
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = Clocks(gpu_id)
+    clocks.start()
+    ctx.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs[k][0].record()
+        ctx.loglike(dp, counts, w.tau, out=logL)
+        evs[k][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    timing = ctx.get_timing()
+    ctx.set_timing(False)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    assert np.isfinite(logL.cpu().numpy()).all()
+
+    # ---- end to end through host buffers (params + counts in, logL out)
+    pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(w.inst, f), dtype=np.float64)
+                               .reshape(-1)).pin_memory() for f in ppm._abi.PARAM_FIELDS}
+    host_inst = w.inst.replace()
+    for f, t in pin.items():
+        setattr(host_inst, f, t)
+    counts_pin = torch.from_numpy(w.counts).pin_memory()
+    out_pin = torch.empty(B, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 8 for t in pin.values()) + counts_pin.numel() * 4
+    d2h = B * 8
+    evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        evs2[k][0].record()
+        dp.upload(host_inst, non_blocking=True)
+        counts.copy_(counts_pin, non_blocking=True)
+        ctx.loglike(dp, counts, w.tau, out=logL)
+        out_pin.copy_(logL, non_blocking=True)
+        evs2[k][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in evs2)
+
+    if dist:
+        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    units = world * args.steps * B
+    value = units / (dev_ms / 1e3)
+    e2e_value = units / (e2e_ms / 1e3)
+
+    calls = max(timing["calls"], 1)
+    k_ms = timing["ms_shift_add"] / calls
+    triples = timing["triples"] / calls
+    achieved = triples * FLOP_PER_TRIPLE / (k_ms / 1e3) / 1e12
+    traffic = profile_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "k_shift_add<atmosphere>", "kernel_ms": k_ms,
+                "triples_per_launch": triples, "flop_per_triple": FLOP_PER_TRIPLE,
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
+                "stage_ms_per_eval": {"ring_template": timing["ms_ring"] / calls,
+                                      "shift_add": k_ms,
+                                      "reduce": timing["ms_reduce"] / calls,
+                                      "response_loglike": timing["ms_loglike"] / calls}}
+    cfg = workload_desc(w)
+    cfg["l2"] = "flushed before every timed step (%d MiB write)" % args.flush_mib
+    cfg["parallelism"] = "replicas x%d" % world
+    cfg["setup_s"] = round(setup_s, 3)
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg,
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
+            "gpu_launches": int(timing["launches"]),
+            "roofline": roofline, "clocks": clk}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

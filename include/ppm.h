@@ -1,0 +1,223 @@
+/*
+ * ppm.h -- C ABI of the GB300 pulse-profile likelihood library (libppm.so).
+ *
+ * The library evaluates the energy-resolved X-ray pulse-profile forward model
+ * of Zhou & Huang, "GPU-accelerated X-ray pulse profile modeling"
+ * (arXiv 2510.07764), and its Poisson likelihood, entirely in CUDA kernels
+ * for sm_103a:
+ *
+ *   parameters --(light bending, Doppler, atmosphere, shift-and-add)--> F_t
+ *   F_t --(ISM attenuation, response contraction)--> expected counts
+ *   expected counts, data --> Poisson log-likelihood
+ *
+ * Conventions
+ * -----------
+ * - Every entry point returns a ppm_status; nothing throws across the ABI.
+ *   On error ppm_last_error() returns a message for the calling thread's last
+ *   failed call on that context.
+ * - "device" pointers are CUDA global-memory pointers on the context's device;
+ *   "host" pointers are ordinary process memory.  The caller owns every
+ *   pointer it passes; the library never frees caller memory and keeps no
+ *   pointer to it after the call returns (table setters copy their inputs).
+ * - `stream` is a cudaStream_t (NULL = the legacy default stream).  Compute
+ *   calls enqueue work on that stream and return without waiting; outputs are
+ *   valid once the stream has completed (see ppm_sync).
+ * - Argument errors are detected on the host before any work is enqueued and
+ *   return PPM_EINVAL.  Per-instance physics range errors (compactness outside
+ *   the lens table, temperature or gravity outside the atmosphere table) are
+ *   reported through `inst_status` and do not fail the call.
+ * - Angles are radians, masses solar masses, radii km, distances kpc,
+ *   energies keV, hydrogen columns 1e20 cm^-2, temperatures log10(T / K).
+ * - A context is not thread-safe: calls on one context must be serialised
+ *   (they may use different streams; the context's workspace is reused, so
+ *   two compute calls on one context must not overlap on the GPU).
+ */
+#ifndef PPM_H
+#define PPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PPM_OK = 0,
+    PPM_EINVAL = 1,    /* bad argument, missing table, unsupported size */
+    PPM_ERANGE = 2,    /* per-instance: parameters outside the tables */
+    PPM_ENOMEM = 3,    /* device or pinned-host allocation failed */
+    PPM_ECUDA = 4,     /* a CUDA runtime call failed */
+    PPM_ETIMEOUT = 5,  /* ppm_sync gave up waiting */
+    PPM_ENOTREADY = 6  /* a device-side invariant failed (see ppm_sync) */
+} ppm_status;
+
+typedef struct ppm_ctx ppm_ctx;
+
+/* Create a context on CUDA device `device`.  The context owns the lens,
+ * atmosphere, energy and response tables and a workspace that grows on first
+ * use of a larger problem (no allocation on later calls of the same size). */
+ppm_status ppm_create(ppm_ctx **out, int device);
+
+/* Destroy a context and free everything it owns.  NULL is ignored. */
+void ppm_destroy(ppm_ctx *ctx);
+
+/* Message describing the last failed call on this context ("" if none). */
+const char *ppm_last_error(const ppm_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Light-bending tables (Sect. 2.3 and 2.8.2 of the paper; grids: Eq.
+ * grids_def; bending: Eqs. salmi_lf and rho; delays: Eqs. salmi_td and
+ * tot_time_delay).
+ *
+ * Builds, in FP64 on the GPU, three tables on linear grids:
+ *   C_alpha[u][cos psi]  cos(alpha) of the ray that reaches the observer,
+ *   LF[u][cos psi]       lensing factor d cos(alpha) / d cos(psi),
+ *   TD[u][cos alpha]     c Delta t / R (the run-time delay is
+ *                        (R/c) TD + delta t(R), Eq. delta_t_oblate).
+ * The alpha march uses steps of `dalpha` (the paper: pi/2048) and stops when
+ * psi exceeds arccos(cpsi_min), when the ray is captured, or when psi would
+ * pass pi; grid cells beyond the march are marked invalid (treated as
+ * invisible).  Requires n_u, n_cpsi, n_calpha >= 2, 0 <= u_min < u_max < 2/3,
+ * -1 <= cpsi_min < cpsi_max <= 1, -1 <= calpha_min < calpha_max <= 1,
+ * pi/16384 <= dalpha <= 0.05, cpsi_max = 1.  The call waits for `stream`,
+ * builds the tables on it and blocks until they are complete.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double u_min, u_max;
+    int n_u;
+    double cpsi_min, cpsi_max;
+    int n_cpsi;
+    double calpha_min, calpha_max;
+    int n_calpha;
+    double dalpha;
+} ppm_lens_spec;
+
+ppm_status ppm_build_lens(ppm_ctx *ctx, const ppm_lens_spec *spec, void *stream);
+
+/* Copy the lens tables to host arrays (row-major [n_u][n_cpsi] for Ca and LF,
+ * [n_u][n_calpha] for TD; invalid cells are NaN).  Any pointer may be NULL.
+ * Blocks until the tables are built. */
+ppm_status ppm_get_lens(ppm_ctx *ctx, double *Ca, double *LF, double *TD);
+
+/* ------------------------------------------------------------------------
+ * Atmosphere table (Sect. 2.5 and 4): specific intensity I(E', mu; T, g) in
+ * keV cm^-2 s^-1 keV^-1 sr^-1, host array I[nT][ng][nmu][nE] (float32,
+ * linear intensity), with node positions logT[nT], logg[ng] (uniform grids),
+ * mu[nmu] (increasing, any spacing) and lnE[nE] (natural log of keV, uniform
+ * spacing).  Interpolation is mixed order: linear in logT and logg, cubic
+ * Lagrange in mu and ln E, linear on the intervals among the first
+ * `n_protect` (>= 2) small-mu nodes and wherever the four-node stencil would
+ * leave the grid; queries outside the mu and E ranges clamp to the edge node.
+ * Limits: nmu <= 128, nE <= 512, nmu >= 4, nE >= 4, nT, ng >= 2.
+ * The table is copied; the call is synchronous.
+ * ------------------------------------------------------------------------ */
+ppm_status ppm_set_atmosphere(ppm_ctx *ctx, const float *I,
+                              const double *logT, int nT, const double *logg, int ng,
+                              const double *mu, int nmu, const double *lnE, int nE,
+                              int n_protect);
+
+/* Model (observed) energy grid E_keV[nE] (host, strictly increasing,
+ * 1 <= nE <= 1024).  Copied; synchronous.  Resets any response matrix whose
+ * energy count differs. */
+ppm_status ppm_set_energies(ppm_ctx *ctx, const double *E_keV, int nE);
+
+/* Response on the model energy grid (Sect. 2.7, 2.8.4): R[nE][nc] host
+ * row-major float32 (effective area x redistribution x energy width, so
+ * that counts/s = F_t diag(ATT) R), and the ISM cross-section sigma_ism[nE]
+ * in cm^2 (ATT_k = exp(-N_H sigma_k)).  nE must equal the energy grid size;
+ * 1 <= nc <= 4096.  Copied; synchronous. */
+ppm_status ppm_set_response(ppm_ctx *ctx, const float *R, int nE, int nc,
+                            const float *sigma_ism);
+
+/* ------------------------------------------------------------------------
+ * Parameter vectors: structure of arrays of DEVICE pointers, B instances.
+ * Per instance (length B): mass_msun, radius_km (equatorial), spin_hz,
+ * incl_rad, dist_kpc, nh_1e20.  Per instance and spot (length B * n_spots,
+ * index b * n_spots + s): colat, azim, zeta (angular radius), logT, and a
+ * masking cap mask_colat, mask_azim, mask_zeta (mask_zeta <= 0: no mask).
+ * An element of a spot is active when its centre is not inside the mask cap
+ * (a concentric mask makes a ring, an offset one a crescent).
+ * oblate: 0 = Schwarzschild+Doppler sphere, 1 = oblate Schwarzschild.
+ * emission: 0 = isotropic blackbody (analytic), 1 = atmosphere table.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int B;
+    int n_spots;   /* 1 or 2 */
+    int oblate;
+    int emission;
+    const double *mass_msun, *radius_km, *spin_hz, *incl_rad, *dist_kpc, *nh_1e20;
+    const double *colat, *azim, *zeta, *logT;
+    const double *mask_colat, *mask_azim, *mask_zeta;
+} ppm_params;
+
+/* Per-instance resolution: HOST arrays of length B.  Each spot is covered by
+ * n_theta rings uniform in colatitude over its angular extent, each ring by
+ * n_phi elements uniform over the spot's azimuthal width (1 <= n_theta <=
+ * 4096, 1 <= n_phi <= 4096); n_phase output phases j / n_phase (1 <= n_phase
+ * <= 4096).  n_fp fine template phases per ring (8 <= n_fp <= 1024; the
+ * paper uses 192). */
+typedef struct {
+    const int *n_theta, *n_phi, *n_phase;
+    int n_fp;
+} ppm_res;
+
+/* ------------------------------------------------------------------------
+ * Forward profile (Sect. 2.8.3, Eq. add_Ft; flux formula of Sect. 2.5 / App.
+ * C).  Writes the photon number flux F_t (photons cm^-2 s^-1 keV^-1) to the
+ * DEVICE array Ft, float32, rows of instance b at row offset
+ * sum_{b' < b} n_phase[b'], each row nE energies.  inst_status (DEVICE int
+ * [B], may be NULL) receives PPM_OK or PPM_ERANGE per instance; rows of an
+ * out-of-range instance are zero.  Requires ppm_build_lens, ppm_set_energies
+ * and, for emission = 1, ppm_set_atmosphere.
+ * ------------------------------------------------------------------------ */
+ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                       float *Ft, int *inst_status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Poisson log-likelihood (Sect. 2.7, 2.8.4; the paper states the likelihood
+ * only through -2 Delta ln L ~ chi^2, Eq. chi2_def context, and its GPU-side
+ * accumulation in Sect. 6): the profile of ppm_profile, attenuated,
+ * contracted with the response, lambda = tau * C + bkg, and
+ *   logL[b] = sum_{j,c} d ln(lambda) - lambda - ln Gamma(d + 1)
+ * accumulated in FP64 (lambda = 0 contributes 0 if d = 0, -inf otherwise).
+ * counts: DEVICE int32 [rows][nc] with the row layout of Ft, or, if
+ * counts_shared != 0, one [n_phase][nc] block used by every instance (all
+ * instances must then have the same n_phase).  bkg: DEVICE float32 with the
+ * layout of counts, or NULL.  logL: DEVICE double [B].  model_counts: DEVICE
+ * float32 [rows][nc] receiving lambda, or NULL.  Out-of-range instances get
+ * logL = -inf and PPM_ERANGE in inst_status.
+ * ------------------------------------------------------------------------ */
+ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                       const int *counts, int counts_shared, const float *bkg,
+                       double tau, double *logL, float *model_counts,
+                       int *inst_status, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Stage timing (no counterpart in the paper; tracing support).  When enabled,
+ * every compute call records CUDA events around its stages on the call's
+ * stream and counts its kernel launches and the (active element, output
+ * phase, energy) triples its shift-and-add evaluates.  ppm_get_timing waits
+ * for the recorded events and returns the totals accumulated since
+ * ppm_set_timing; ppm_set_timing(ctx, enable) resets the totals.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double ms_ring;        /* per-ring setup + template kernel */
+    double ms_shift_add;   /* shift-and-add + atmosphere interpolation kernel */
+    double ms_reduce;      /* partial-sum reduction kernel */
+    double ms_loglike;     /* response contraction + likelihood kernels */
+    long long calls;       /* compute calls timed */
+    long long launches;    /* kernels launched by those calls */
+    double triples;        /* element x phase x energy triples evaluated */
+} ppm_timing;
+
+ppm_status ppm_set_timing(ppm_ctx *ctx, int enable);
+ppm_status ppm_get_timing(ppm_ctx *ctx, ppm_timing *out);
+
+/* Wait for `stream` with a bounded host-side poll (timeout_s > 0), then report
+ * any device-side invariant failure recorded since the last ppm_sync
+ * (PPM_ENOTREADY, with a message) and clear it.  Returns PPM_ETIMEOUT if the
+ * stream has not completed within timeout_s seconds. */
+ppm_status ppm_sync(ppm_ctx *ctx, void *stream, double timeout_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPM_H */

@@ -1,0 +1,194 @@
+"""GB300-native pulse-profile likelihood (arXiv 2510.07764).
+
+Python front end of libppm.so.  PyTorch provides device memory and streams;
+every step of the forward model and the likelihood runs in the library's CUDA
+kernels.  ``Context`` wraps one library context; ``DeviceParams`` holds the
+structure-of-arrays parameter vectors as CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import (PPM_EINVAL, PPM_ENOMEM, PPM_ENOTREADY, PPM_ERANGE, PPM_ETIMEOUT, PPM_OK,
+                   LibraryMissing)
+
+__all__ = ["Context", "DeviceParams", "PPMError", "LibraryMissing", "PPM_OK", "PPM_ERANGE",
+           "PPM_EINVAL", "PPM_ENOMEM", "PPM_ETIMEOUT", "PPM_ENOTREADY"]
+
+
+class PPMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_abi.STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+        self.status = status
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+class DeviceParams:
+    """SoA parameter vectors on the GPU (float64 CUDA tensors)."""
+
+    def __init__(self, inst, device="cuda"):
+        import torch
+        self.inst = inst
+        self.B = inst.B
+        self.n_spots = inst.n_spots
+        self.oblate = int(inst.oblate)
+        self.emission = int(inst.emission)
+        self.t = {f: torch.empty(getattr(inst, f).size, dtype=torch.float64, device=device)
+                  for f in _abi.PARAM_FIELDS}
+        self.upload(inst)
+        self._res_arrays(inst)
+
+    def _res_arrays(self, inst):
+        self.n_theta = np.ascontiguousarray(inst.n_theta, dtype=np.int32)
+        self.n_phi = np.ascontiguousarray(inst.n_phi, dtype=np.int32)
+        self.n_phase = np.ascontiguousarray(inst.n_phase, dtype=np.int32)
+        self.n_fp = int(inst.n_fp)
+        ip = C.POINTER(C.c_int)
+        self.res = _abi.ppm_res(self.n_theta.ctypes.data_as(ip), self.n_phi.ctypes.data_as(ip),
+                                self.n_phase.ctypes.data_as(ip), self.n_fp)
+        self.rows = int(self.n_phase.sum())
+
+    def upload(self, inst, non_blocking: bool = False):
+        """Copy parameter values (host numpy or pinned tensors) into the device arrays."""
+        import torch
+        for f in _abi.PARAM_FIELDS:
+            src = getattr(inst, f)
+            if isinstance(src, torch.Tensor):
+                self.t[f].copy_(src.reshape(-1), non_blocking=non_blocking)
+            else:
+                self.t[f].copy_(torch.from_numpy(np.ascontiguousarray(src, dtype=np.float64).reshape(-1)),
+                                non_blocking=non_blocking)
+
+    def struct(self) -> _abi.ppm_params:
+        p = _abi.ppm_params()
+        p.B, p.n_spots, p.oblate, p.emission = self.B, self.n_spots, self.oblate, self.emission
+        for f in _abi.PARAM_FIELDS:
+            setattr(p, f, self.t[f].data_ptr())
+        return p
+
+
+class Context:
+    """One libppm context (tables + workspace) on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        st, h = _abi.ppm_create(device)
+        if st != PPM_OK:
+            raise PPMError(st, "ppm_create failed on device %d" % device)
+        self.h = h
+        self.device = device
+        self.nE = 0
+        self.nc = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            _abi.ppm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != PPM_OK:
+            raise PPMError(st, _abi.ppm_last_error(self.h))
+
+    # ---- tables -------------------------------------------------------------
+    def build_lens(self, spec, stream=None):
+        s = _abi.ppm_lens_spec(spec.u_min, spec.u_max, spec.n_u, spec.cpsi_min, spec.cpsi_max,
+                               spec.n_cpsi, spec.calpha_min, spec.calpha_max, spec.n_calpha,
+                               spec.dalpha)
+        self._check(_abi.ppm_build_lens(self.h, s, _stream_handle(stream)))
+        self.lens_spec = spec
+
+    def get_lens(self):
+        s = self.lens_spec
+        Ca = np.empty((s.n_u, s.n_cpsi))
+        LF = np.empty((s.n_u, s.n_cpsi))
+        TD = np.empty((s.n_u, s.n_calpha))
+        self._check(_abi.ppm_get_lens(self.h, _dp(Ca), _dp(LF), _dp(TD)))
+        return Ca, LF, TD
+
+    def set_atmosphere(self, t):
+        arrs = [np.ascontiguousarray(t.I, dtype=np.float32)] + \
+               [np.ascontiguousarray(a, dtype=np.float64) for a in (t.logT, t.logg, t.mu, t.lnE)]
+        I, lT, lg, mu, lnE = arrs
+        self._check(_abi.ppm_set_atmosphere(self.h, _dp(I), _dp(lT), len(lT), _dp(lg), len(lg),
+                                            _dp(mu), len(mu), _dp(lnE), len(lnE),
+                                            int(t.n_protect)))
+
+    def set_energies(self, E_keV):
+        E = np.ascontiguousarray(E_keV, dtype=np.float64)
+        self._check(_abi.ppm_set_energies(self.h, _dp(E), len(E)))
+        self.nE = len(E)
+
+    def set_response(self, R, sigma):
+        R = np.ascontiguousarray(R, dtype=np.float32)
+        sg = np.ascontiguousarray(sigma, dtype=np.float32)
+        self._check(_abi.ppm_set_response(self.h, _dp(R), R.shape[0], R.shape[1], _dp(sg)))
+        self.nc = R.shape[1]
+
+    def setup(self, w, build_lens: bool = True):
+        """Load every table of a synthetic workload (``synth.Workload``)."""
+        if build_lens:
+            self.build_lens(w.lens)
+        if w.atm is not None:
+            self.set_atmosphere(w.atm)
+        self.set_energies(w.E_keV)
+        if w.R is not None:
+            self.set_response(w.R, w.sigma_ism)
+
+    # ---- compute ------------------------------------------------------------
+    def profile(self, dp: DeviceParams, out=None, status=None, stream=None):
+        """F_t [sum_b n_phase_b, nE] float32 (CUDA tensor)."""
+        import torch
+        if out is None:
+            out = torch.empty((dp.rows, self.nE), dtype=torch.float32, device="cuda:%d" % self.device)
+        if status is None:
+            status = torch.empty(dp.B, dtype=torch.int32, device=out.device)
+        self._check(_abi.ppm_profile(self.h, dp.struct(), dp.res, C.c_void_p(out.data_ptr()),
+                                     C.c_void_p(status.data_ptr()), _stream_handle(stream)))
+        self.last_status = status
+        return out
+
+    def loglike(self, dp: DeviceParams, counts, tau: float, bkg=None, counts_shared=False,
+                out=None, model_counts=None, status=None, stream=None):
+        """Poisson log-likelihood per instance, float64 CUDA tensor [B]."""
+        import torch
+        dev = counts.device
+        if out is None:
+            out = torch.empty(dp.B, dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(dp.B, dtype=torch.int32, device=dev)
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(_abi.ppm_loglike(self.h, dp.struct(), dp.res, ptr(counts), int(counts_shared),
+                                     ptr(bkg), float(tau), ptr(out), ptr(model_counts),
+                                     ptr(status), _stream_handle(stream)))
+        self.last_status = status
+        return out
+
+    def set_timing(self, enable: bool = True):
+        self._check(_abi.ppm_set_timing(self.h, int(enable)))
+
+    def get_timing(self) -> dict:
+        t = _abi.ppm_timing()
+        self._check(_abi.ppm_get_timing(self.h, t))
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def sync(self, stream=None, timeout: float = 30.0):
+        self._check(_abi.ppm_sync(self.h, _stream_handle(stream), timeout))

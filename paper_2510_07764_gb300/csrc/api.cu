@@ -1,0 +1,728 @@
+// C ABI of libppm.so: contexts, tables, planning, workspace and launches.
+#include <algorithm>
+#include <cstdarg>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "ppm_internal.cuh"
+
+using namespace ppm;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    // grow-only; the caller must make sure the old contents are no longer in use
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= n && p) return cudaSuccess;
+        release();
+        size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        n = want;
+        return cudaSuccess;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct HostPlan {
+    std::vector<InstPlan> inst;
+    std::vector<Item> items;
+    std::vector<int2> tiles;
+    int total_rings = 0, total_rows = 0, n_phi_max = 0;
+    size_t total_elems = 0;
+};
+
+struct DeviceGuard {
+    int prev = -1, dev;
+    explicit DeviceGuard(int d) : dev(d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct ppm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    // lens
+    bool lens_ready = false;
+    ppm_lens_spec lens{};
+    DevBuf d_Ca, d_LF, d_TD;
+    // atmosphere
+    bool atm_ready = false;
+    int nT = 0, ng = 0, nmu = 0, nEt = 0, n_protect = 0, nmu_pad = 0;
+    double lnE0_t = 0.0, dlnE_t = 0.0;
+    DevBuf d_I, d_logT, d_logg, d_mu;
+    // energies
+    std::vector<double> E;
+    DevBuf d_E, d_E2, d_pk, d_invE;
+    bool energy_dirty = true;
+    int nEpad = 0, sliding = 0;
+    // response
+    int nc = 0;
+    DevBuf d_R, d_sigma;
+    // plan
+    std::vector<int> plan_key;
+    HostPlan plan;
+    DevBuf d_plan;
+    void *h_pinned = nullptr;
+    size_t h_pinned_n = 0;
+    cudaEvent_t plan_ev = nullptr;
+    // workspace
+    DevBuf ws;
+    unsigned *d_err = nullptr;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    ppm_timing acc{};
+    unsigned long long *d_triples = nullptr;
+};
+
+namespace {
+// records an event pair around one stage when timing is enabled
+struct StageTimer {
+    ppm_ctx *c;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageTimer(ppm_ctx *c_, int stage_, cudaStream_t st_) : c(c_), stage(stage_), st(st_)
+    {
+        if (!c->timing) return;
+        a = take();
+        if (a) cudaEventRecord(a, st);
+    }
+    cudaEvent_t take()
+    {
+        if (!c->ev_pool.empty()) {
+            cudaEvent_t e = c->ev_pool.back();
+            c->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    void done(int kernels)
+    {
+        if (!c->timing) return;
+        c->acc.launches += kernels;
+        if (!a) return;
+        cudaEvent_t b = take();
+        if (!b) { c->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, st);
+        c->pending.push_back({stage, a, b});
+    }
+};
+}  // namespace
+
+static ppm_status fail(ppm_ctx *c, ppm_status s, const char *fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+static ppm_status cuda_fail(ppm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? PPM_ENOMEM : PPM_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define PPM_CUDA(call, what)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+extern "C" {
+
+ppm_status ppm_create(ppm_ctx **out, int device)
+{
+    if (!out) return PPM_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return PPM_EINVAL;
+    ppm_ctx *ctx = new ppm_ctx();
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return PPM_ECUDA;
+    }
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->plan_ev, cudaEventDisableTiming) != cudaSuccess) {
+        ppm_destroy(ctx);
+        return PPM_ENOMEM;
+    }
+    *out = ctx;
+    return PPM_OK;
+}
+
+void ppm_destroy(ppm_ctx *ctx)
+{
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    for (DevBuf *b : {&ctx->d_Ca, &ctx->d_LF, &ctx->d_TD, &ctx->d_I, &ctx->d_logT, &ctx->d_logg,
+                      &ctx->d_mu, &ctx->d_E, &ctx->d_E2, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
+                      &ctx->d_sigma, &ctx->d_plan, &ctx->ws})
+        b->release();
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_triples) cudaFree(ctx->d_triples);
+    for (auto &pd : ctx->pending) ctx->ev_pool.push_back(pd.a), ctx->ev_pool.push_back(pd.b);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->plan_ev) cudaEventDestroy(ctx->plan_ev);
+    delete ctx;
+}
+
+const char *ppm_last_error(const ppm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------------------
+// lens tables
+// ---------------------------------------------------------------------------
+ppm_status ppm_build_lens(ppm_ctx *ctx, const ppm_lens_spec *s, void *stream)
+{
+    if (!ctx || !s) return fail(ctx, PPM_EINVAL, "null argument");
+    if (s->n_u < 2 || s->n_cpsi < 2 || s->n_calpha < 2 || s->n_u > 8192 || s->n_cpsi > 65536 ||
+        s->n_calpha > 65536)
+        return fail(ctx, PPM_EINVAL, "lens grid sizes must be in [2, 8192/65536]");
+    if (!(s->u_min >= 0.0 && s->u_min < s->u_max && s->u_max < 2.0 / 3.0))
+        return fail(ctx, PPM_EINVAL, "need 0 <= u_min < u_max < 2/3");
+    if (!(s->cpsi_min >= -1.0 && s->cpsi_min < s->cpsi_max && s->cpsi_max == 1.0))
+        return fail(ctx, PPM_EINVAL, "need -1 <= cpsi_min < cpsi_max = 1");
+    if (!(s->calpha_min >= -1.0 && s->calpha_min < s->calpha_max && s->calpha_max <= 1.0))
+        return fail(ctx, PPM_EINVAL, "need -1 <= calpha_min < calpha_max <= 1");
+    if (!(s->dalpha >= kPI / 16384.0 && s->dalpha <= 0.05))
+        return fail(ctx, PPM_EINVAL, "need pi/16384 <= dalpha <= 0.05");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    PPM_CUDA(cudaStreamSynchronize(st), "sync before lens build");
+    const size_t ncp = (size_t)s->n_u * s->n_cpsi, nca = (size_t)s->n_u * s->n_calpha;
+    PPM_CUDA(ctx->d_Ca.ensure(ncp * 8), "alloc Ca");
+    PPM_CUDA(ctx->d_LF.ensure(ncp * 8), "alloc LF");
+    PPM_CUDA(ctx->d_TD.ensure(nca * 8), "alloc TD");
+    const int j_cap = (int)std::floor(kPI / s->dalpha) + 2;
+    DevBuf scratch;
+    PPM_CUDA(scratch.ensure((size_t)s->n_u * j_cap * 4 * sizeof(double)), "alloc lens scratch");
+    LensDev L;
+    L.u_min = s->u_min; L.u_max = s->u_max; L.n_u = s->n_u;
+    L.cpsi_min = s->cpsi_min; L.cpsi_max = s->cpsi_max; L.n_cpsi = s->n_cpsi;
+    L.ca_min = s->calpha_min; L.ca_max = s->calpha_max; L.n_calpha = s->n_calpha;
+    L.Ca = ctx->d_Ca.as<double>(); L.LF = ctx->d_LF.as<double>(); L.TD = ctx->d_TD.as<double>();
+    double *psi = scratch.as<double>();
+    cudaError_t e = launch_lens_build(L, s->dalpha, psi, psi + (size_t)s->n_u * j_cap, j_cap, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    scratch.release();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "lens build");
+    ctx->lens = *s;
+    ctx->lens_ready = true;
+    return PPM_OK;
+}
+
+ppm_status ppm_get_lens(ppm_ctx *ctx, double *Ca, double *LF, double *TD)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (!ctx->lens_ready) return fail(ctx, PPM_EINVAL, "lens tables not built");
+    DeviceGuard g(ctx->device);
+    const size_t ncp = (size_t)ctx->lens.n_u * ctx->lens.n_cpsi;
+    const size_t nca = (size_t)ctx->lens.n_u * ctx->lens.n_calpha;
+    PPM_CUDA(cudaDeviceSynchronize(), "sync");
+    if (Ca) PPM_CUDA(cudaMemcpy(Ca, ctx->d_Ca.p, ncp * 8, cudaMemcpyDeviceToHost), "copy Ca");
+    if (LF) PPM_CUDA(cudaMemcpy(LF, ctx->d_LF.p, ncp * 8, cudaMemcpyDeviceToHost), "copy LF");
+    if (TD) PPM_CUDA(cudaMemcpy(TD, ctx->d_TD.p, nca * 8, cudaMemcpyDeviceToHost), "copy TD");
+    return PPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// atmosphere, energies, response
+// ---------------------------------------------------------------------------
+static bool increasing(const double *x, int n)
+{
+    for (int i = 0; i + 1 < n; ++i)
+        if (!(x[i + 1] > x[i]) || !std::isfinite(x[i])) return false;
+    return std::isfinite(x[n - 1]);
+}
+
+ppm_status ppm_set_atmosphere(ppm_ctx *ctx, const float *I, const double *logT, int nT,
+                              const double *logg, int ng, const double *mu, int nmu,
+                              const double *lnE, int nE, int n_protect)
+{
+    if (!ctx || !I || !logT || !logg || !mu || !lnE) return fail(ctx, PPM_EINVAL, "null argument");
+    if (nT < 2 || ng < 2 || nmu < 4 || nmu > 128 || nE < 4 || nE > 512)
+        return fail(ctx, PPM_EINVAL, "atmosphere sizes out of range");
+    if (n_protect < 2 || n_protect > nmu) return fail(ctx, PPM_EINVAL, "bad n_protect");
+    if (!increasing(logT, nT) || !increasing(logg, ng) || !increasing(mu, nmu) ||
+        !increasing(lnE, nE))
+        return fail(ctx, PPM_EINVAL, "table axes must be strictly increasing");
+    const double d = (lnE[nE - 1] - lnE[0]) / (nE - 1);
+    for (int i = 0; i < nE; ++i)
+        if (std::fabs(lnE[i] - (lnE[0] + i * d)) > 1e-9 * std::fabs(lnE[nE - 1] - lnE[0]))
+            return fail(ctx, PPM_EINVAL, "ln E axis must be uniformly spaced");
+    const int pad = nmu | 1;
+    if ((size_t)nE * pad * 4 > 160 * 1024)
+        return fail(ctx, PPM_EINVAL, "atmosphere slab (nE x nmu) exceeds 160 KB of shared memory");
+    DeviceGuard g(ctx->device);
+    PPM_CUDA(cudaDeviceSynchronize(), "sync");
+    const size_t n = (size_t)nT * ng * nmu * nE;
+    PPM_CUDA(ctx->d_I.ensure(n * 4), "alloc table");
+    PPM_CUDA(ctx->d_logT.ensure(nT * 8), "alloc");
+    PPM_CUDA(ctx->d_logg.ensure(ng * 8), "alloc");
+    PPM_CUDA(ctx->d_mu.ensure(nmu * 4), "alloc");
+    PPM_CUDA(cudaMemcpy(ctx->d_I.p, I, n * 4, cudaMemcpyHostToDevice), "copy table");
+    PPM_CUDA(cudaMemcpy(ctx->d_logT.p, logT, nT * 8, cudaMemcpyHostToDevice), "copy");
+    PPM_CUDA(cudaMemcpy(ctx->d_logg.p, logg, ng * 8, cudaMemcpyHostToDevice), "copy");
+    std::vector<float> muf(mu, mu + nmu);
+    PPM_CUDA(cudaMemcpy(ctx->d_mu.p, muf.data(), nmu * 4, cudaMemcpyHostToDevice), "copy");
+    ctx->nT = nT; ctx->ng = ng; ctx->nmu = nmu; ctx->nEt = nE; ctx->n_protect = n_protect;
+    ctx->nmu_pad = pad; ctx->lnE0_t = lnE[0]; ctx->dlnE_t = d;
+    ctx->atm_ready = true;
+    ctx->energy_dirty = true;
+    return PPM_OK;
+}
+
+ppm_status ppm_set_energies(ppm_ctx *ctx, const double *E_keV, int nE)
+{
+    if (!ctx || !E_keV) return fail(ctx, PPM_EINVAL, "null argument");
+    if (nE < 1 || nE > 1024) return fail(ctx, PPM_EINVAL, "need 1 <= nE <= 1024");
+    for (int i = 0; i < nE; ++i)
+        if (!(E_keV[i] > 0.0) || !std::isfinite(E_keV[i]) || (i && !(E_keV[i] > E_keV[i - 1])))
+            return fail(ctx, PPM_EINVAL, "energies must be positive and strictly increasing");
+    if (ctx->nc && (int)ctx->E.size() != nE) ctx->nc = 0;  // response no longer matches
+    ctx->E.assign(E_keV, E_keV + nE);
+    ctx->energy_dirty = true;
+    return PPM_OK;
+}
+
+ppm_status ppm_set_response(ppm_ctx *ctx, const float *R, int nE, int nc, const float *sigma)
+{
+    if (!ctx || !R || !sigma) return fail(ctx, PPM_EINVAL, "null argument");
+    if (nE != (int)ctx->E.size() || nE < 1) return fail(ctx, PPM_EINVAL, "response nE must match the energy grid");
+    if (nc < 1 || nc > 4096) return fail(ctx, PPM_EINVAL, "need 1 <= nc <= 4096");
+    DeviceGuard g(ctx->device);
+    PPM_CUDA(cudaDeviceSynchronize(), "sync");
+    PPM_CUDA(ctx->d_R.ensure((size_t)nE * nc * 4), "alloc R");
+    PPM_CUDA(ctx->d_sigma.ensure((size_t)nE * 4), "alloc sigma");
+    PPM_CUDA(cudaMemcpy(ctx->d_R.p, R, (size_t)nE * nc * 4, cudaMemcpyHostToDevice), "copy R");
+    PPM_CUDA(cudaMemcpy(ctx->d_sigma.p, sigma, (size_t)nE * 4, cudaMemcpyHostToDevice), "copy sigma");
+    ctx->nc = nc;
+    return PPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// planning and launch
+// ---------------------------------------------------------------------------
+static ppm_status refresh_energies(ppm_ctx *ctx)
+{
+    if (!ctx->energy_dirty) return PPM_OK;
+    const int nE = (int)ctx->E.size();
+    const int nEpad = (nE + kEC - 1) / kEC * kEC;
+    std::vector<float> E(nEpad), E2(nEpad), pk(nEpad), invE(nEpad);
+    for (int k = 0; k < nEpad; ++k) {
+        const double e = ctx->E[std::min(k, nE - 1)];
+        E[k] = (float)e;
+        E2[k] = (float)(e * e);
+        invE[k] = (float)(1.0 / e);
+        pk[k] = ctx->atm_ready ? (float)((std::log(e) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
+    }
+    int sliding = ctx->atm_ready ? 1 : 0;
+    if (sliding) {
+        for (int k = 0; k + 1 < nE; ++k)
+            if (!((double)pk[k + 1] - pk[k] < 0.999)) sliding = 0;
+        if (!((double)pk[nE - 1] - pk[0] < ctx->nEt - 3.5)) sliding = 0;
+    }
+    DeviceGuard g(ctx->device);
+    PPM_CUDA(cudaDeviceSynchronize(), "sync");
+    for (DevBuf *b : {&ctx->d_E, &ctx->d_E2, &ctx->d_pk, &ctx->d_invE})
+        PPM_CUDA(b->ensure((size_t)nEpad * 4), "alloc energies");
+    PPM_CUDA(cudaMemcpy(ctx->d_E.p, E.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
+    PPM_CUDA(cudaMemcpy(ctx->d_E2.p, E2.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
+    PPM_CUDA(cudaMemcpy(ctx->d_pk.p, pk.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
+    PPM_CUDA(cudaMemcpy(ctx->d_invE.p, invE.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
+    ctx->nEpad = nEpad;
+    ctx->sliding = sliding;
+    ctx->energy_dirty = false;
+    return PPM_OK;
+}
+
+static ppm_status check_params(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res)
+{
+    if (!p || !res) return fail(ctx, PPM_EINVAL, "null params or res");
+    if (p->B < 1 || p->B > (1 << 22)) return fail(ctx, PPM_EINVAL, "need 1 <= B <= 4194304");
+    if (p->n_spots < 1 || p->n_spots > 2) return fail(ctx, PPM_EINVAL, "n_spots must be 1 or 2");
+    if (p->oblate != 0 && p->oblate != 1) return fail(ctx, PPM_EINVAL, "oblate must be 0 or 1");
+    if (p->emission != 0 && p->emission != 1) return fail(ctx, PPM_EINVAL, "emission must be 0 or 1");
+    const void *ptrs[] = {p->mass_msun, p->radius_km, p->spin_hz, p->incl_rad, p->dist_kpc,
+                          p->nh_1e20, p->colat, p->azim, p->zeta, p->logT,
+                          p->mask_colat, p->mask_azim, p->mask_zeta};
+    for (const void *q : ptrs)
+        if (!q) return fail(ctx, PPM_EINVAL, "null parameter array");
+    if (!res->n_theta || !res->n_phi || !res->n_phase)
+        return fail(ctx, PPM_EINVAL, "null resolution array");
+    if (res->n_fp < 8 || res->n_fp > kMaxFp) return fail(ctx, PPM_EINVAL, "need 8 <= n_fp <= 1024");
+    for (int b = 0; b < p->B; ++b) {
+        if (res->n_theta[b] < 1 || res->n_theta[b] > 4096 || res->n_phi[b] < 1 ||
+            res->n_phi[b] > 4096 || res->n_phase[b] < 1 || res->n_phase[b] > 4096)
+            return fail(ctx, PPM_EINVAL, "instance %d: resolution out of range", b);
+    }
+    if (!ctx->lens_ready) return fail(ctx, PPM_EINVAL, "lens tables not built");
+    if (ctx->E.empty()) return fail(ctx, PPM_EINVAL, "energy grid not set");
+    if (p->emission == 1 && !ctx->atm_ready) return fail(ctx, PPM_EINVAL, "atmosphere table not set");
+    return PPM_OK;
+}
+
+static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                            cudaStream_t st)
+{
+    const int B = p->B;
+    std::vector<int> key;
+    key.reserve(3 * B + 4);
+    key.push_back(B);
+    key.push_back(p->n_spots);
+    key.push_back(res->n_fp);
+    key.push_back(ctx->sm_count);
+    for (int b = 0; b < B; ++b) {
+        key.push_back(res->n_theta[b]);
+        key.push_back(res->n_phi[b]);
+        key.push_back(res->n_phase[b]);
+    }
+    if (key == ctx->plan_key && ctx->d_plan.p) return PPM_OK;
+
+    HostPlan hp;
+    long long T = 0;
+    for (int b = 0; b < B; ++b)
+        T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + kPT - 1) / kPT);
+    const long long D = (long long)ctx->sm_count * 12;
+    const int g = (int)std::max<long long>(1, T / std::max<long long>(D, 1));
+    hp.inst.resize(B);
+    for (int b = 0; b < B; ++b) {
+        InstPlan &ip = hp.inst[b];
+        ip.n_theta = res->n_theta[b];
+        ip.n_phi = res->n_phi[b];
+        ip.n_phase = res->n_phase[b];
+        ip.ring0 = hp.total_rings;
+        ip.elem0 = (int)hp.total_elems;
+        ip.row0 = hp.total_rows;
+        ip.tiles = (ip.n_phase + kPT - 1) / kPT;
+        ip.tile0 = (int)hp.tiles.size();
+        hp.total_rings += p->n_spots * ip.n_theta;
+        hp.total_elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
+        hp.total_rows += ip.n_phase;
+        hp.n_phi_max = std::max(hp.n_phi_max, ip.n_phi);
+        const int gb = std::min(g, ip.n_theta);
+        for (int t = 0; t < ip.tiles; ++t) {
+            const int begin = (int)hp.items.size();
+            for (int s = 0; s < p->n_spots; ++s)
+                for (int r0 = 0; r0 < ip.n_theta; r0 += gb) {
+                    Item it;
+                    it.b = b; it.spot = s; it.r0 = r0; it.r1 = std::min(r0 + gb, ip.n_theta);
+                    it.j0 = t * kPT; it.nj = std::min(kPT, ip.n_phase - t * kPT);
+                    hp.items.push_back(it);
+                }
+            hp.tiles.push_back(make_int2(begin, (int)hp.items.size()));
+        }
+    }
+    if (hp.total_elems > (size_t)INT32_MAX) return fail(ctx, PPM_EINVAL, "problem too large");
+    const size_t b_inst = align256(hp.inst.size() * sizeof(InstPlan));
+    const size_t b_items = align256(hp.items.size() * sizeof(Item));
+    const size_t b_tiles = align256(hp.tiles.size() * sizeof(int2));
+    const size_t bytes = b_inst + b_items + b_tiles;
+    // the pinned staging buffer may still feed the previous upload
+    PPM_CUDA(cudaEventSynchronize(ctx->plan_ev), "plan event");
+    if (ctx->h_pinned_n < bytes) {
+        if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+        ctx->h_pinned = nullptr;
+        ctx->h_pinned_n = 0;
+        PPM_CUDA(cudaMallocHost(&ctx->h_pinned, bytes), "pinned plan buffer");
+        ctx->h_pinned_n = bytes;
+    }
+    char *h = static_cast<char *>(ctx->h_pinned);
+    memcpy(h, hp.inst.data(), hp.inst.size() * sizeof(InstPlan));
+    memcpy(h + b_inst, hp.items.data(), hp.items.size() * sizeof(Item));
+    memcpy(h + b_inst + b_items, hp.tiles.data(), hp.tiles.size() * sizeof(int2));
+    if (ctx->d_plan.n < bytes) {
+        PPM_CUDA(cudaDeviceSynchronize(), "sync");
+        PPM_CUDA(ctx->d_plan.ensure(bytes), "alloc plan");
+    }
+    PPM_CUDA(cudaMemcpyAsync(ctx->d_plan.p, h, bytes, cudaMemcpyHostToDevice, st), "upload plan");
+    PPM_CUDA(cudaEventRecord(ctx->plan_ev, st), "plan event");
+    ctx->plan = std::move(hp);
+    ctx->plan_key = std::move(key);
+    return PPM_OK;
+}
+
+namespace {
+struct Work {
+    int *status;
+    RingRec *recs;
+    float *tmpl, *elems, *partials, *Ft;
+    double *row_ll;
+};
+}  // namespace
+
+static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, bool need_ft,
+                                   Work *w)
+{
+    const HostPlan &hp = ctx->plan;
+    const int ct = ctx->nc ? (ctx->nc + 63) / 64 : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+    const size_t o_status = take((size_t)p->B * sizeof(int));
+    const size_t o_recs = take((size_t)hp.total_rings * sizeof(RingRec));
+    const size_t o_tmpl = take((size_t)hp.total_rings * 4 * (n_fp + 1) * sizeof(float));
+    const size_t o_elems = take(hp.total_elems * sizeof(float));
+    const size_t o_part = take((size_t)hp.items.size() * kPT * ctx->nEpad * sizeof(float));
+    const size_t o_ft = take(need_ft ? (size_t)hp.total_rows * ctx->E.size() * sizeof(float) : 0);
+    const size_t o_ll = take(need_ft ? (size_t)hp.total_rows * ct * sizeof(double) : 0);
+    if (off > ctx->ws.n) {
+        PPM_CUDA(cudaDeviceSynchronize(), "sync");
+        PPM_CUDA(ctx->ws.ensure(off), "alloc workspace");
+    }
+    char *base = ctx->ws.as<char>();
+    w->status = reinterpret_cast<int *>(base + o_status);
+    w->recs = reinterpret_cast<RingRec *>(base + o_recs);
+    w->tmpl = reinterpret_cast<float *>(base + o_tmpl);
+    w->elems = reinterpret_cast<float *>(base + o_elems);
+    w->partials = reinterpret_cast<float *>(base + o_part);
+    w->Ft = reinterpret_cast<float *>(base + o_ft);
+    w->row_ll = reinterpret_cast<double *>(base + o_ll);
+    return PPM_OK;
+}
+
+static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, PlanDev *plan,
+                      LensDev *L, AtmDev *A, EnergyDev *en)
+{
+    P->B = p->B; P->n_spots = p->n_spots; P->oblate = p->oblate; P->emission = p->emission;
+    P->mass_msun = p->mass_msun; P->radius_km = p->radius_km; P->spin_hz = p->spin_hz;
+    P->incl_rad = p->incl_rad; P->dist_kpc = p->dist_kpc; P->nh_1e20 = p->nh_1e20;
+    P->colat = p->colat; P->azim = p->azim; P->zeta = p->zeta; P->logT = p->logT;
+    P->mask_colat = p->mask_colat; P->mask_azim = p->mask_azim; P->mask_zeta = p->mask_zeta;
+    const HostPlan &hp = ctx->plan;
+    const size_t b_inst = align256(hp.inst.size() * sizeof(InstPlan));
+    const size_t b_items = align256(hp.items.size() * sizeof(Item));
+    char *d = ctx->d_plan.as<char>();
+    plan->B = p->B; plan->n_fp = n_fp; plan->n_items = (int)hp.items.size();
+    plan->total_rings = hp.total_rings;
+    plan->inst = reinterpret_cast<const InstPlan *>(d);
+    plan->items = reinterpret_cast<const Item *>(d + b_inst);
+    plan->tile_items = reinterpret_cast<const int2 *>(d + b_inst + b_items);
+    const ppm_lens_spec &s = ctx->lens;
+    L->u_min = s.u_min; L->u_max = s.u_max; L->n_u = s.n_u;
+    L->cpsi_min = s.cpsi_min; L->cpsi_max = s.cpsi_max; L->n_cpsi = s.n_cpsi;
+    L->ca_min = s.calpha_min; L->ca_max = s.calpha_max; L->n_calpha = s.n_calpha;
+    L->Ca = ctx->d_Ca.as<double>(); L->LF = ctx->d_LF.as<double>(); L->TD = ctx->d_TD.as<double>();
+    A->nT = ctx->nT; A->ng = ctx->ng; A->nmu = ctx->nmu; A->nE = ctx->nEt;
+    A->n_protect = ctx->n_protect; A->nmu_pad = ctx->nmu_pad;
+    A->I = ctx->d_I.as<float>(); A->logT = ctx->d_logT.as<double>();
+    A->logg = ctx->d_logg.as<double>(); A->mu = ctx->d_mu.as<float>();
+    A->lnE0 = ctx->lnE0_t; A->dlnE = ctx->dlnE_t;
+    en->nE = (int)ctx->E.size(); en->nEpad = ctx->nEpad;
+    en->E = ctx->d_E.as<float>(); en->E2 = ctx->d_E2.as<float>();
+    en->pk = ctx->d_pk.as<float>(); en->invE = ctx->d_invE.as<float>();
+    en->sliding = ctx->sliding;
+}
+
+static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
+                              bool internal_ft, cudaStream_t st, Work *w)
+{
+    ppm_status s = check_params(ctx, p, res);
+    if (s != PPM_OK) return s;
+    if ((s = refresh_energies(ctx)) != PPM_OK) return s;
+    if ((s = make_plan(ctx, p, res, st)) != PPM_OK) return s;
+    if ((s = ensure_workspace(ctx, p, res->n_fp, internal_ft, w)) != PPM_OK) return s;
+    Params P;
+    PlanDev plan;
+    LensDev L;
+    AtmDev A;
+    EnergyDev en;
+    fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
+    // shared-memory budget of the shift-and-add kernel
+    size_t smem = 4 * (size_t)(4 * (res->n_fp + 1) + ctx->plan.n_phi_max + 3 * ctx->nEpad +
+                               kPT * ctx->nEpad + 64);
+    if (p->emission == 1) smem += 4 * (size_t)(ctx->nmu + ctx->nEt * ctx->nmu_pad + 8);
+    if (smem > ctx->smem_optin)
+        return fail(ctx, PPM_EINVAL, "shared memory need %zu B exceeds %zu B (n_phi, nE too large)",
+                    smem, ctx->smem_optin);
+    if (internal_ft) Ft = w->Ft;
+    PPM_CUDA(cudaMemsetAsync(w->status, 0, sizeof(int) * p->B, st), "memset status");
+    {
+        StageTimer t(ctx, 0, st);
+        PPM_CUDA(launch_ring(P, plan, L, A, w->recs, w->tmpl, w->elems, w->status, ctx->d_err,
+                             ctx->timing ? ctx->d_triples : nullptr, (int)ctx->E.size(), st),
+                 "ring kernel");
+        t.done(1);
+    }
+    {
+        StageTimer t(ctx, 1, st);
+        PPM_CUDA(launch_shift_add(P, plan, A, en, w->recs, w->tmpl, w->elems, w->status,
+                                  w->partials, ctx->plan.n_phi_max, st),
+                 "shift-and-add kernel");
+        t.done(1);
+    }
+    {
+        StageTimer t(ctx, 2, st);
+        PPM_CUDA(launch_reduce(plan, en, w->partials, w->status, ctx->plan.total_rows, Ft, st),
+                 "reduce kernel");
+        t.done(1);
+    }
+    if (ctx->timing) ctx->acc.calls += 1;
+    return PPM_OK;
+}
+
+ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
+                       int *inst_status, void *stream)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (!Ft) return fail(ctx, PPM_EINVAL, "null Ft");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    ppm_status s = run_profile(ctx, p, res, Ft, false, st, &w);
+    if (s != PPM_OK) return s;
+    if (inst_status)
+        PPM_CUDA(cudaMemcpyAsync(inst_status, w.status, sizeof(int) * p->B,
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy status");
+    ctx->err.clear();
+    return PPM_OK;
+}
+
+ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, const int *counts,
+                       int counts_shared, const float *bkg, double tau, double *logL,
+                       float *model_counts, int *inst_status, void *stream)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (!counts || !logL) return fail(ctx, PPM_EINVAL, "null counts or logL");
+    if (!ctx->nc) return fail(ctx, PPM_EINVAL, "response not set");
+    if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ctx, PPM_EINVAL, "tau must be positive");
+    if (p && res && counts_shared && p->B > 0 && res->n_phase)
+        for (int b = 1; b < p->B; ++b)
+            if (res->n_phase[b] != res->n_phase[0])
+                return fail(ctx, PPM_EINVAL, "shared counts need equal n_phase");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    ppm_status s = run_profile(ctx, p, res, nullptr, true, st, &w);
+    if (s != PPM_OK) return s;
+    Params P;
+    PlanDev plan;
+    LensDev L;
+    AtmDev A;
+    EnergyDev en;
+    fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
+    {
+        StageTimer t(ctx, 3, st);
+        PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
+                                ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc, counts,
+                                counts_shared, bkg, tau, w.status, w.row_ll, model_counts, logL,
+                                st),
+                 "likelihood kernels");
+        t.done(2);
+    }
+    if (inst_status)
+        PPM_CUDA(cudaMemcpyAsync(inst_status, w.status, sizeof(int) * p->B,
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy status");
+    ctx->err.clear();
+    return PPM_OK;
+}
+
+ppm_status ppm_set_timing(ppm_ctx *ctx, int enable)
+{
+    if (!ctx) return PPM_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!ctx->d_triples) PPM_CUDA(cudaMalloc(&ctx->d_triples, sizeof(unsigned long long)), "alloc");
+    PPM_CUDA(cudaDeviceSynchronize(), "sync");
+    PPM_CUDA(cudaMemset(ctx->d_triples, 0, sizeof(unsigned long long)), "memset");
+    for (auto &pd : ctx->pending) ctx->ev_pool.push_back(pd.a), ctx->ev_pool.push_back(pd.b);
+    ctx->pending.clear();
+    ctx->acc = ppm_timing{};
+    ctx->timing = enable != 0;
+    return PPM_OK;
+}
+
+ppm_status ppm_get_timing(ppm_ctx *ctx, ppm_timing *out)
+{
+    if (!ctx || !out) return fail(ctx, PPM_EINVAL, "null argument");
+    DeviceGuard g(ctx->device);
+    for (auto &pd : ctx->pending) {
+        PPM_CUDA(cudaEventSynchronize(pd.b), "timing event");
+        float ms = 0.0f;
+        PPM_CUDA(cudaEventElapsedTime(&ms, pd.a, pd.b), "elapsed");
+        double *slot[] = {&ctx->acc.ms_ring, &ctx->acc.ms_shift_add, &ctx->acc.ms_reduce,
+                          &ctx->acc.ms_loglike};
+        *slot[pd.stage] += ms;
+        ctx->ev_pool.push_back(pd.a);
+        ctx->ev_pool.push_back(pd.b);
+    }
+    ctx->pending.clear();
+    unsigned long long tr = 0;
+    if (ctx->d_triples)
+        PPM_CUDA(cudaMemcpy(&tr, ctx->d_triples, sizeof(tr), cudaMemcpyDeviceToHost), "read");
+    ctx->acc.triples = (double)tr;
+    *out = ctx->acc;
+    return PPM_OK;
+}
+
+ppm_status ppm_sync(ppm_ctx *ctx, void *stream, double timeout_s)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (!(timeout_s > 0.0)) return fail(ctx, PPM_EINVAL, "timeout must be positive");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(ctx, e, "stream");
+        const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (el > timeout_s) return fail(ctx, PPM_ETIMEOUT, "stream not complete after %.3f s", el);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    unsigned bits = 0;
+    PPM_CUDA(cudaMemcpy(&bits, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
+    if (bits) {
+        PPM_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)), "clear error word");
+        return fail(ctx, PPM_ENOTREADY, "device invariant failed (bits 0x%x%s)", bits,
+                    (bits & kErrPhaseOrder) ? ": template observed phases not increasing" : "");
+    }
+    return PPM_OK;
+}
+
+}  // extern "C"

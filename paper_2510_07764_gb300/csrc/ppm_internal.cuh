@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of libppm.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ppm.h"
+
+namespace ppm {
+
+// ---- physical constants (CODATA 2018, IAU 2015 nominal GM_sun) -----------
+constexpr double kGM_SUN = 1.32712440018e20;      // m^3 s^-2
+constexpr double kC = 299792458.0;                // m s^-1
+constexpr double kC_CM = 29979245800.0;           // cm s^-1
+constexpr double kH_KEVS = 4.135667696e-18;       // keV s
+constexpr double kKB_KEVK = 8.617333262e-8;       // keV K^-1
+constexpr double kKPC_M = 3.0856775814913673e19;  // m
+constexpr double kPI = 3.141592653589793238462643383279502884;
+
+// Template fluxes are stored as F * kFluxScale so that the FP32 hot loop
+// stays in the normal range for element areas down to ~1e-9 sr (R/D ~ 1e-15).
+constexpr double kFluxScale = 1e30;
+
+// Shift-and-add tiling: output phases per work item and energies per chunk.
+constexpr int kPT = 32;
+constexpr int kEC = 32;
+constexpr int kMaxFp = 1024;
+constexpr int kSABlock = 256;
+
+// device-side invariant failure bits (ctx error word)
+enum : unsigned {
+    kErrPhaseOrder = 1u,  // template observed phases not increasing
+    kErrPlan = 2u,        // inconsistent plan (should not happen)
+};
+
+struct LensDev {
+    double u_min, u_max;
+    int n_u;
+    double cpsi_min, cpsi_max;
+    int n_cpsi;
+    double ca_min, ca_max;
+    int n_calpha;
+    const double *Ca, *LF, *TD;
+};
+
+struct AtmDev {
+    int nT, ng, nmu, nE, n_protect, nmu_pad;
+    const float *I;          // [nT][ng][nmu][nE]
+    const double *logT;      // [nT]
+    const double *logg;      // [ng]
+    const float *mu;         // [nmu]
+    double lnE0, dlnE;       // uniform ln E axis
+};
+
+// Per-instance plan entry (host-built).
+struct InstPlan {
+    int n_theta, n_phi, n_phase;
+    int ring0;   // first global ring index
+    int elem0;   // first element slot (rings of this instance use n_phi slots each)
+    int row0;    // first F_t row
+    int tile0;   // first entry in the tile-range table
+    int tiles;   // ceil(n_phase / kPT)
+};
+
+// One shift-and-add work item: rings [r0, r1) of one spot, phases [j0, j0+nj).
+struct Item {
+    int b, spot, r0, r1, j0, nj;
+};
+
+// Per-ring record written by the ring kernel.
+struct RingRec {
+    int visible;    // 1 if the ring contributes
+    int n_active;   // active elements (compacted at the front of the slots)
+    int iT, ig;     // lower (logT, logg) corner of the atmosphere cell
+    float wT, wg;   // weights of the upper corners
+    float kT;       // keV (blackbody emission)
+    float pad;
+};
+
+struct Params {
+    int B, n_spots, oblate, emission;
+    const double *mass_msun, *radius_km, *spin_hz, *incl_rad, *dist_kpc, *nh_1e20;
+    const double *colat, *azim, *zeta, *logT;
+    const double *mask_colat, *mask_azim, *mask_zeta;
+};
+
+struct PlanDev {
+    int B, n_fp, n_items, total_rings;
+    const InstPlan *inst;
+    const Item *items;
+    const int2 *tile_items;  // [sum tiles] item range of (instance, tile)
+};
+
+// Energy-side arrays (device).
+struct EnergyDev {
+    int nE, nEpad;
+    const float *E;      // [nEpad] keV (padded with the last value)
+    const float *E2;     // [nEpad] E^2
+    const float *pk;     // [nEpad] (ln E - lnE0_table) / dlnE_table
+    const float *invE;   // [nEpad] 1/E
+    int sliding;         // consecutive pk differ by < 1 (one node shift per step)
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_lens_build(const LensDev &L, double dalpha, double *psi_scratch,
+                              double *list_scratch, int j_cap, cudaStream_t st);
+
+cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
+                        const AtmDev &A, RingRec *recs, float *tmpl, float *elems,
+                        int *status, unsigned *err, unsigned long long *triples, int nE,
+                        cudaStream_t st);
+
+cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
+                             const EnergyDev &en, const RingRec *recs, const float *tmpl,
+                             const float *elems, const int *status, float *partials,
+                             int n_phi_max, cudaStream_t st);
+
+cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
+                          const int *status, int total_rows, float *Ft, cudaStream_t st);
+
+cudaError_t launch_loglike(const Params &p, const PlanDev &plan, const float *Ft,
+                           int total_rows, int nE, const float *R, const float *sigma,
+                           int nc, const int *counts, int counts_shared, const float *bkg,
+                           double tau, const int *status, double *row_ll,
+                           float *model_counts, double *logL, cudaStream_t st);
+
+// row -> instance lookup (binary search over InstPlan.row0)
+__device__ __forceinline__ int find_instance_by_row(const InstPlan *ip, int B, int row)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ip[mid].row0 <= row) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_instance_by_ring(const InstPlan *ip, int B, int ring)
+{
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ip[mid].ring0 <= ring) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+}  // namespace ppm

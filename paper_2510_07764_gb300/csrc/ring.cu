@@ -1,0 +1,293 @@
+// Per-ring setup and pseudo-patch template, FP64 (Sect. 2.1-2.6, 2.8.3).
+//
+// One block per ring of one spot of one instance:
+//   - star shape, slope, gravity and surface speed at the ring colatitude
+//     (Eqs. Rtheta, Omega_c_def, def_f, the g(theta) fit of Sect. 2.2, the
+//     beta of Sect. 2.4);
+//   - the template F, z, phi_o, mu at the n_fp + 1 fine phases (the five
+//     steps of Sect. 2.8.3: cos psi, lens lookup, Eq. sigma_relation,
+//     visibility, Doppler factor and aberration, flux of Sect. 2.5) and the
+//     invisible-segment fill;
+//   - the list of active elements of the ring (mask caps removed), compacted;
+//   - the ring's atmosphere cell in (logT, logg).
+// Every visibility and masking decision is taken in FP64, as in the oracle;
+// the template is then stored in FP32 for the shift-and-add kernel.
+#include "ppm_internal.cuh"
+
+namespace ppm {
+namespace {
+
+struct RingGeo {
+    double theta, st, ct, half, dphi, R, u, sq1u, cos_eta, sin_eta, logg, beta, gamma;
+    double area, dt_obl, nu, sini, cosi, phic, mask_c, mask_ct, mask_st, mask_phi;
+    int ok, has_mask;
+};
+
+__device__ bool lens_lookup(const LensDev &L, double u, double cpsi, double *ca, double *lf)
+{
+    double fu = (u - L.u_min) / (L.u_max - L.u_min) * (L.n_u - 1);
+    double fc = (cpsi - L.cpsi_min) / (L.cpsi_max - L.cpsi_min) * (L.n_cpsi - 1);
+    int iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    int ic = min(max((int)floor(fc), 0), L.n_cpsi - 2);
+    double tu = fu - iu, tc = fc - ic;
+    size_t k00 = (size_t)iu * L.n_cpsi + ic, k10 = k00 + L.n_cpsi;
+    double a00 = L.Ca[k00], a01 = L.Ca[k00 + 1], a10 = L.Ca[k10], a11 = L.Ca[k10 + 1];
+    if (isnan(a00) || isnan(a01) || isnan(a10) || isnan(a11)) return false;
+    double d00 = L.LF[k00], d01 = L.LF[k00 + 1], d10 = L.LF[k10], d11 = L.LF[k10 + 1];
+    *ca = (1.0 - tu) * ((1.0 - tc) * a00 + tc * a01) + tu * ((1.0 - tc) * a10 + tc * a11);
+    *lf = (1.0 - tu) * ((1.0 - tc) * d00 + tc * d01) + tu * ((1.0 - tc) * d10 + tc * d11);
+    return true;
+}
+
+__device__ double td_lookup(const LensDev &L, double u, double ca)
+{
+    ca = fmin(fmax(ca, L.ca_min), L.ca_max);
+    double fu = (u - L.u_min) / (L.u_max - L.u_min) * (L.n_u - 1);
+    double fc = (ca - L.ca_min) / (L.ca_max - L.ca_min) * (L.n_calpha - 1);
+    int iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    int ic = min(max((int)floor(fc), 0), L.n_calpha - 2);
+    double tu = fu - iu, tc = fc - ic;
+    size_t k00 = (size_t)iu * L.n_calpha + ic, k10 = k00 + L.n_calpha;
+    return (1.0 - tu) * ((1.0 - tc) * L.TD[k00] + tc * L.TD[k00 + 1]) +
+           tu * ((1.0 - tc) * L.TD[k10] + tc * L.TD[k10 + 1]);
+}
+
+__device__ int axis_cell(const double *x, int n, double q, float *w)
+{
+    int lo = 0, hi = n - 1;
+    if (q <= x[0]) { *w = 0.0f; return 0; }
+    if (q >= x[n - 1]) { *w = 1.0f; return n - 2; }
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (x[mid] <= q) lo = mid; else hi = mid;
+    }
+    *w = (float)((q - x[lo]) / (x[lo + 1] - x[lo]));
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L, AtmDev A,
+                                             RingRec *recs, float *tmpl, float *elems,
+                                             int *status, unsigned *err,
+                                             unsigned long long *triples, int nE)
+{
+    const int g = blockIdx.x;
+    const int b = find_instance_by_ring(plan.inst, plan.B, g);
+    const InstPlan ip = plan.inst[b];
+    const int local = g - ip.ring0;
+    const int spot = local / ip.n_theta, r = local % ip.n_theta;
+    const int sidx = b * p.n_spots + spot;
+    const int n_fp = plan.n_fp;
+
+    __shared__ double sF[kMaxFp + 1], sZ[kMaxFp + 1], sPh[kMaxFp + 1], sMu[kMaxFp + 1];
+    __shared__ RingGeo G;
+    __shared__ int s_inv_min, s_inv_max, s_vis0, s_base, s_wsum[8];
+
+    if (threadIdx.x == 0) {
+        const double GM = p.mass_msun[b] * kGM_SUN;
+        const double Rs = 2.0 * GM / (kC * kC);
+        const double Re = p.radius_km[b] * 1e3;
+        const double nu = p.spin_hz[b];
+        const double D = p.dist_kpc[b] * kKPC_M;
+        const double Obar = 2.0 * kPI * nu * sqrt(Re * Re * Re / GM);
+        const double x = GM / (kC * kC * Re);
+        const double o2 = p.oblate ? Obar * Obar * (-0.788 + 1.030 * x) : 0.0;
+        const double g0 = GM / (Re * Re) / sqrt(1.0 - Rs / Re);
+        // ring of the spot's bounding grid
+        const double tc = p.colat[sidx], zt = p.zeta[sidx];
+        const double lo = fmax(tc - zt, 0.0), hi = fmin(tc + zt, kPI);
+        const double dth = (hi - lo) / ip.n_theta;
+        const double th = lo + (r + 0.5) * dth;
+        const double dcos = cos(lo + r * dth) - cos(lo + (r + 1) * dth);
+        double st, ct;
+        sincos(th, &st, &ct);
+        const double num = cos(zt) - ct * cos(tc), den = st * sin(tc);
+        double half;
+        if (den <= 0.0) half = num <= 0.0 ? kPI : 0.0;
+        else half = acos(fmin(fmax(num / den, -1.0), 1.0));
+        G.theta = th; G.st = st; G.ct = ct; G.half = half;
+        G.dphi = 2.0 * half / ip.n_phi;
+        // shape, slope, gravity, speed
+        const double R = Re * (1.0 + o2 * ct * ct);
+        const double u = Rs / R;
+        const double sq = sqrt(1.0 - u);
+        const double f = -2.0 * o2 * Re * ct * st / (R * sq);
+        G.R = R; G.u = u; G.sq1u = sq;
+        G.cos_eta = 1.0 / sqrt(1.0 + f * f);
+        G.sin_eta = f / sqrt(1.0 + f * f);
+        double gg = g0;
+        if (p.oblate) {
+            const double O2 = Obar * Obar, O4 = O2 * O2, O6 = O4 * O2;
+            const double c2 = ct * ct, s2 = st * st;
+            gg = g0 * (1.0 +
+                       s2 * (O2 * (-0.791 + 0.776 * x) + O4 * (-1.315 * x + 2.431 * x * x) +
+                             O6 * (-1.172 * x)) +
+                       c2 * (O2 * (1.138 - 1.431 * x) + O4 * (0.653 * x - 2.864 * x * x) +
+                             O6 * (0.975 * x) - O4 * (13.47 * x - 27.13 * x * x)) +
+                       fabs(ct) * O4 * (13.47 * x - 27.13 * x * x));
+        }
+        G.logg = log10(gg * 100.0);
+        G.beta = 2.0 * kPI * nu * R * st / (kC * sq);
+        G.gamma = 1.0 / sqrt(1.0 - G.beta * G.beta);
+        G.area = R * R * sqrt(1.0 + f * f) * dcos * G.dphi / (D * D) * kFluxScale;
+        G.dt_obl = (Re - R + Rs * log((Re - Rs) / (R - Rs))) / kC;
+        G.nu = nu;
+        sincos(p.incl_rad[b], &G.sini, &G.cosi);
+        G.phic = p.azim[sidx];
+        const double mz = p.mask_zeta[sidx];
+        G.has_mask = mz > 0.0;
+        G.mask_c = G.has_mask ? cos(mz) : 2.0;
+        G.mask_ct = cos(p.mask_colat[sidx]);
+        G.mask_st = sin(p.mask_colat[sidx]);
+        G.mask_phi = p.mask_azim[sidx];
+        // range checks (per-instance status)
+        bool in_range = u >= L.u_min && u <= L.u_max && zt > 0.0 && zt <= kPI && tc >= 0.0 &&
+                        tc <= kPI && D > 0.0 && nu >= 0.0 && G.beta < 1.0 && Re > Rs &&
+                        p.incl_rad[b] >= 0.0 && p.incl_rad[b] <= kPI && isfinite(G.area);
+        if (p.emission == 1) {
+            const double lt = p.logT[sidx];
+            in_range = in_range && lt >= A.logT[0] && lt <= A.logT[A.nT - 1] &&
+                       G.logg >= A.logg[0] && G.logg <= A.logg[A.ng - 1];
+        }
+        if (!in_range) atomicMax(&status[b], (int)PPM_ERANGE);
+        G.ok = in_range && half > 0.0;
+        s_inv_min = n_fp;
+        s_inv_max = 0;
+        s_vis0 = 0;
+    }
+    __syncthreads();
+
+    const size_t tbase = (size_t)g * 4 * (n_fp + 1);
+    if (G.ok) {
+        const LensDev Lc = L;
+        for (int i = threadIdx.x; i < n_fp; i += blockDim.x) {
+            double sphi, cphi;
+            sincospi(2.0 * (double)i / (double)n_fp, &sphi, &cphi);
+            // step 2: cos psi
+            const double cpsi = G.sini * G.st * cphi + G.cosi * G.ct;
+            bool vis = false;
+            double ca, lf;
+            // step 3: lens table; beyond its cos psi range the point is invisible
+            if (cpsi >= Lc.cpsi_min && lens_lookup(Lc, G.u, cpsi, &ca, &lf)) {
+                const double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
+                const double sp = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
+                const double ratio = sp > 1e-12 ? sa / sp : sqrt(lf);
+                // step 4: Eq. sigma_relation
+                const double csig = ca * G.cos_eta +
+                                    ratio * G.sin_eta * (G.cosi * G.st - G.sini * G.ct * cphi);
+                // step 5
+                if (csig >= 0.0) {
+                    vis = true;
+                    const double cxi = -ratio * G.sini * sphi;
+                    const double delta = 1.0 / (G.gamma * (1.0 - G.beta * cxi));
+                    const double mu = delta * csig;
+                    sF[i] = G.sq1u * delta * delta * delta * mu * lf * G.gamma * G.area;
+                    sZ[i] = 1.0 / (delta * G.sq1u);
+                    const double dt = G.R / kC * td_lookup(Lc, G.u, ca) + G.dt_obl;
+                    sPh[i] = (double)i / (double)n_fp + G.nu * dt;
+                    sMu[i] = mu;
+                }
+            }
+            if (!vis) {
+                atomicMin(&s_inv_min, i);
+                atomicMax(&s_inv_max, i);
+                sF[i] = 0.0; sZ[i] = 0.0; sPh[i] = 0.0; sMu[i] = 0.0;
+            }
+            if (i == 0) s_vis0 = vis;
+        }
+        __syncthreads();
+        const bool vis0 = s_vis0;
+        // point n_fp is point 0 one rotation later (it closes the fill interval)
+        if (vis0 && threadIdx.x == 0) {
+            sF[n_fp] = sF[0]; sZ[n_fp] = sZ[0]; sMu[n_fp] = sMu[0]; sPh[n_fp] = sPh[0] + 1.0;
+        }
+        __syncthreads();
+        if (vis0) {
+            const int a = s_inv_min - 1, c = s_inv_max + 1;
+            for (int i = threadIdx.x; i < n_fp; i += blockDim.x) {
+                if (s_inv_min <= s_inv_max && i >= s_inv_min && i <= s_inv_max) {
+                    const double t = (double)(i - a) / (double)(c - a);
+                    sZ[i] = sZ[a] + (sZ[c] - sZ[a]) * t;
+                    sPh[i] = sPh[a] + (sPh[c] - sPh[a]) * t;
+                }
+            }
+        }
+        __syncthreads();
+        if (vis0) {
+            float *tp = tmpl + tbase;
+            for (int i = threadIdx.x; i <= n_fp; i += blockDim.x) {
+                tp[i] = (float)sPh[i];
+                tp[(n_fp + 1) + i] = (float)sF[i];
+                tp[2 * (n_fp + 1) + i] = (float)sZ[i];
+                tp[3 * (n_fp + 1) + i] = (float)sMu[i];
+                if (i < n_fp && !(sPh[i + 1] > sPh[i])) atomicOr(err, kErrPhaseOrder);
+            }
+        }
+    }
+
+    // active elements, compacted (FP64 mask test, as in the oracle)
+    int n_active = 0;
+    if (G.ok) {
+        float *ep = elems + (size_t)ip.elem0 + (size_t)local * ip.n_phi;
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (threadIdx.x == 0) s_base = 0;
+        __syncthreads();
+        for (int m0 = 0; m0 < ip.n_phi; m0 += blockDim.x) {
+            const int m = m0 + threadIdx.x;
+            bool act = false;
+            double phia = 0.0;
+            if (m < ip.n_phi) {
+                phia = G.phic - G.half + (m + 0.5) * G.dphi;
+                act = true;
+                if (G.has_mask) {
+                    const double cd = G.ct * G.mask_ct + G.st * G.mask_st * cos(phia - G.mask_phi);
+                    act = !(cd > G.mask_c);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, act);
+            if (lane == 0) s_wsum[wid] = __popc(bal);
+            __syncthreads();
+            int off = s_base;
+            for (int w = 0; w < wid; ++w) off += s_wsum[w];
+            if (act) ep[off + __popc(bal & ((1u << lane) - 1u))] = (float)(phia / (2.0 * kPI));
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wsum[w];
+                s_base += tot;
+            }
+            __syncthreads();
+        }
+        n_active = s_base;
+    }
+
+    if (threadIdx.x == 0) {
+        RingRec rec;
+        rec.visible = (G.ok && s_vis0 && n_active > 0) ? 1 : 0;
+        rec.n_active = n_active;
+        rec.iT = 0; rec.ig = 0; rec.wT = 0.0f; rec.wg = 0.0f;
+        const double lt = p.logT[sidx];
+        rec.kT = (float)(kKB_KEVK * pow(10.0, lt));
+        if (p.emission == 1) {
+            rec.iT = axis_cell(A.logT, A.nT, lt, &rec.wT);
+            rec.ig = axis_cell(A.logg, A.ng, G.logg, &rec.wg);
+        }
+        rec.pad = 0.0f;
+        recs[g] = rec;
+        if (triples && rec.visible)
+            atomicAdd(triples, (unsigned long long)n_active * ip.n_phase * nE);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L, const AtmDev &A,
+                        RingRec *recs, float *tmpl, float *elems, int *status, unsigned *err,
+                        unsigned long long *triples, int nE, cudaStream_t st)
+{
+    if (plan.total_rings <= 0) return cudaSuccess;
+    k_ring<<<plan.total_rings, 256, 0, st>>>(p, plan, L, A, recs, tmpl, elems, status, err,
+                                             triples, nE);
+    return cudaGetLastError();
+}
+
+}  // namespace ppm

@@ -1,0 +1,91 @@
+"""Parity of ppm_loglike (ISM, response contraction, Poisson logL) with the oracle.
+
+Model counts per (phase, channel) bin: 1e-3 relative where non-negligible.
+logL: a relative error eps per bin moves logL by at most eps * sum|d - lambda|
+(first order in lambda), so the test allows 1e-3 * sum|d - lambda| plus rounding.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_loglike, max_rel, rows_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_ll(orc, w, b=0, counts=None, bkg=None):
+    Ft = orc.profile(w, b=b)
+    C = orc.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[b]))
+    d = w.counts[rows_of(w, b)] if counts is None else counts
+    return orc.loglike(C, d, w.tau, bkg), C
+
+
+def _ll_tol(w, C, d):
+    return 1e-3 * np.sum(np.abs(d - w.tau * C)) + 1e-9 * np.sum(d)
+
+
+def test_loglike_two_spot_reduced(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=20, n_phi=36, n_phase=48, n_E=80, n_chan=70, atm=atm,
+                           lens=small_lens)
+    ll, mc, st = gpu_loglike(w)
+    llr, C = _oracle_ll(orc, w)
+    assert st[0] == 0
+    assert max_rel(mc, w.tau * C) < 1e-3
+    assert abs(ll[0] - llr) <= _ll_tol(w, C, w.counts)
+
+
+def test_loglike_full_size(orc, synth, atm):
+    """The benchmark workload: 2 x 128^2 elements, 128 phases, 256 energies,
+    300 channels, 1e6 counts.  Oracle on sampled phases (all energies)."""
+    w = synth.atm_two_spot(atm=atm)
+    ll, mc, st = gpu_loglike(w)
+    js = np.array([0, 31, 64, 100, 127])
+    Ft = orc.profile(w, jsel=js)
+    C = orc.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
+    assert max_rel(mc[js], w.tau * C) < 1e-3
+    assert np.isfinite(ll[0])
+
+
+def test_loglike_background_and_batch(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=12, n_phi=20, n_phase=32, n_E=48, n_chan=30, atm=atm,
+                           lens=small_lens)
+    inst = w.inst.select([0, 0])
+    inst.incl_rad[1] = 1.3
+    inst.logT[1, 1] = 5.95
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts, w.counts[::-1]]), tau=w.tau)
+    bkg = np.full(w2.counts.shape, 0.7, np.float32)
+    ll, mc, st = gpu_loglike(w2, bkg=bkg)
+    for b in range(2):
+        d = w2.counts[rows_of(w2, b)]
+        llr, C = _oracle_ll(orc, w2, b, counts=d, bkg=bkg[rows_of(w2, b)])
+        assert abs(ll[b] - llr) <= _ll_tol(w2, C, d)
+    # shared counts: one block of counts for every instance
+    ll2, _, _ = gpu_loglike(w2, counts=w.counts, counts_shared=True)
+    for b in range(2):
+        llr, C = _oracle_ll(orc, w2, b, counts=w.counts)
+        assert abs(ll2[b] - llr) <= _ll_tol(w2, C, w.counts)
+
+
+def test_loglike_out_of_range_is_minus_inf(synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=8, n_phi=8, n_phase=32, n_E=32, n_chan=8, atm=atm,
+                           lens=small_lens)
+    inst = w.inst.select([0, 0])
+    inst.mass_msun[1] = 2.2   # u = 0.54, beyond the lens grid
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts, w.counts]), tau=w.tau)
+    ll, _, st = gpu_loglike(w2)
+    assert st[0] == 0 and st[1] == 2
+    assert np.isfinite(ll[0]) and ll[1] == -np.inf
+
+
+def test_zero_model_with_counts_is_minus_inf(synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=8, n_phi=8, n_phase=32, n_E=32, n_chan=8, atm=atm,
+                           lens=small_lens)
+    w.inst = w.inst.replace(incl_rad=0.0)
+    w.inst.colat[0] = [np.pi - 0.05, np.pi - 0.05]   # hidden spots: lambda = 0
+    w.inst.zeta[0] = [0.04, 0.04]
+    w.inst.mask_zeta[0] = [0.0, 0.0]
+    ll, _, _ = gpu_loglike(w)
+    assert ll[0] == -np.inf
+    ll0, _, _ = gpu_loglike(w, counts=np.zeros_like(w.counts))
+    assert ll0[0] == 0.0

@@ -1,0 +1,145 @@
+"""Parity of the CUDA forward profile (ppm_profile) with the FP64 oracle.
+
+Tolerances (per phase-energy bin where the oracle flux is >= 1e-6 of its
+maximum, the paper's "non-negligible flux" criterion):
+  analytic blackbody workload ............. 1e-4 relative
+  atmosphere-table workloads .............. 1e-3 relative
+Full-size workloads are checked on sampled bins the oracle computes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import gpu_profile, max_rel, rows_of
+
+pytestmark = pytest.mark.gpu
+
+TOL_BB = 1e-4
+TOL_ATM = 1e-3
+
+
+def test_bb_small_full_size(orc, synth):
+    w = synth.bb_small()
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    ref = orc.profile(w)
+    assert max_rel(got, ref) < TOL_BB
+
+
+def test_bb_ragged_sizes(orc, synth, small_lens):
+    # 37 rings x 45 elements (ragged vs 32 lanes), 70 phases (ragged vs 32), 41 energies
+    w = synth.bb_small(n_theta=37, n_phi=45, n_phase=70, n_E=41, lens=small_lens)
+    got, _ = gpu_profile(w)
+    assert max_rel(got, orc.profile(w)) < TOL_BB
+
+
+def test_atm_two_spot_reduced(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=24, n_phi=40, n_phase=40, n_E=72, n_chan=24, atm=atm,
+                           lens=small_lens)
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
+
+
+def test_atm_two_spot_full_size_sampled(orc, synth, atm):
+    w = synth.atm_two_spot(atm=atm)
+    got, _ = gpu_profile(w)
+    rng = np.random.default_rng(3)
+    js = np.sort(rng.choice(128, 6, replace=False))
+    ks = np.sort(rng.choice(256, 10, replace=False))
+    ref = orc.profile(w, jsel=js, ksel=ks)
+    assert max_rel(got[np.ix_(js, ks)], ref) < TOL_ATM
+    # every output is finite and the total is positive
+    assert np.isfinite(got).all() and got.sum() > 0
+
+
+def test_crescent_reduced(orc, synth, atm):
+    w = synth.crescent_extreme(n_theta=48, n_phi=64, n_phase=64, n_E=100, n_chan=24, atm=atm)
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
+
+
+def test_crescent_full_size_sampled(orc, synth, atm):
+    w = synth.crescent_extreme(atm=atm)
+    got, _ = gpu_profile(w)
+    js = np.array([0, 63, 127, 128, 200, 255])
+    ks = np.array([0, 37, 150, 299])
+    ref = orc.profile(w, jsel=js, ksel=ks)
+    assert max_rel(got[np.ix_(js, ks)], ref) < TOL_ATM
+
+
+def test_batch_mixed_instances(orc, synth, atm):
+    inst = synth.random_instances(7, seed=11, res_theta=(20, 33), res_phase=(32, 45), mask=True)
+    w = synth.Workload("batch", inst, synth.LensSpec(), synth.logspace(0.1, 5.215, 64), atm=atm)
+    got, st = gpu_profile(w)
+    for b in range(inst.B):
+        wb = synth.Workload("one", inst.select(b), w.lens, w.E_keV, atm=atm)
+        try:
+            ref = orc.profile(wb)
+        except orc.OracleRangeError:
+            assert st[b] == 2
+            assert not got[rows_of(w, b)].any()
+            continue
+        assert st[b] == 0
+        assert max_rel(got[rows_of(w, b)], ref) < TOL_ATM, b
+
+
+def test_out_of_range_instance_is_isolated(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=12, n_phi=16, n_phase=32, n_E=40, n_chan=8, atm=atm,
+                           lens=small_lens)
+    inst = w.inst
+    two = inst.select([0, 0, 0])
+    two.radius_km[1] = 9.0          # u = 0.46: outside the lens grid [0.30, 0.40]
+    two.logT[2, 0] = 7.5            # outside the atmosphere table
+    w2 = synth.Workload("x", two, small_lens, w.E_keV, atm=atm)
+    got, st = gpu_profile(w2)
+    assert list(st) == [0, 2, 2]
+    assert not got[32:].any()
+    assert max_rel(got[:32], orc.profile(w)) < TOL_ATM
+
+
+def test_invisible_and_empty_spots(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=10, n_phi=16, n_phase=32, n_E=40, n_chan=8, atm=atm,
+                           lens=small_lens)
+    # spot 0 hidden behind the star (observer at the north pole, spot at the
+    # south pole), spot 1 fully masked (mask larger than the emitter)
+    inst = w.inst.replace(incl_rad=0.0)
+    inst.colat[0, 0] = math.pi - 0.05
+    inst.zeta[0, 0] = 0.04
+    inst.mask_zeta[0, 1] = 0.5
+    w.inst = inst
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    assert not got.any()
+    assert not orc.profile(w).any()
+
+
+def test_single_phase_single_energy(orc, synth, atm, small_lens):
+    w = synth.atm_two_spot(n_theta=9, n_phi=7, n_phase=1, n_E=1, n_chan=3, atm=atm,
+                           lens=small_lens)
+    got, _ = gpu_profile(w)
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
+
+
+def test_zero_inclination_is_phase_constant(synth, atm):
+    # holds at any size: no rotational modulation is visible from the pole
+    w = synth.atm_two_spot(atm=atm)
+    w.inst = w.inst.replace(incl_rad=0.0)
+    got, _ = gpu_profile(w)
+    assert got.max() > 0
+    assert np.max(np.abs(got - got[0:1])) / got.max() < 2e-5
+
+
+def test_bad_resolution_is_rejected(synth, small_lens):
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = synth.bb_small(lens=small_lens)
+    ctx = context(w)
+    for field, val in [("n_theta", 0), ("n_phi", 5000), ("n_phase", -1)]:
+        inst = w.inst.replace(**{field: val})
+        dp = ppm.DeviceParams(inst)
+        with pytest.raises(ppm.PPMError) as e:
+            ctx.profile(dp)
+        assert e.value.status == ppm.PPM_EINVAL
