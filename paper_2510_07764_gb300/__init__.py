@@ -158,7 +158,8 @@ class Context:
         """F_t [sum_b n_phase_b, nE] float32 (CUDA tensor)."""
         import torch
         if out is None:
-            out = torch.empty((dp.rows, self.nE), dtype=torch.float32, device="cuda:%d" % self.device)
+            out = torch.empty((max(dp.rows, 0), self.nE), dtype=torch.float32,
+                              device="cuda:%d" % self.device)
         if status is None:
             status = torch.empty(dp.B, dtype=torch.int32, device=out.device)
         self._check(_abi.ppm_profile(self.h, dp.struct(), dp.res, C.c_void_p(out.data_ptr()),

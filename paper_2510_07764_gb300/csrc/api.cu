@@ -1,6 +1,7 @@
 // C ABI of libppm.so: contexts, tables, planning, workspace and launches.
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -39,6 +40,7 @@ struct DevBuf {
 };
 
 struct HostPlan {
+    int pt = kPT;
     std::vector<InstPlan> inst;
     std::vector<Item> items;
     std::vector<int2> tiles;
@@ -79,7 +81,7 @@ struct ppm_ctx {
     DevBuf d_I, d_logT, d_logg, d_mu;
     // energies
     std::vector<double> E;
-    DevBuf d_E, d_E2, d_pk, d_invE;
+    DevBuf d_E, d_E3, d_pk, d_invE;
     bool energy_dirty = true;
     int nEpad = 0, sliding = 0;
     // response
@@ -95,6 +97,7 @@ struct ppm_ctx {
     // workspace
     DevBuf ws;
     unsigned *d_err = nullptr;
+    double *d_lfact = nullptr;  // ln d! for d < kLogFactN
     // stage timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -184,6 +187,16 @@ ppm_status ppm_create(ppm_ctx **out, int device)
     }
     ctx->sm_count = prop.multiProcessorCount;
     ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    {
+        std::vector<double> lf(kLogFactN);
+        for (int d = 0; d < kLogFactN; ++d) lf[d] = std::lgamma((double)d + 1.0);
+        if (cudaMalloc(&ctx->d_lfact, kLogFactN * sizeof(double)) != cudaSuccess ||
+            cudaMemcpy(ctx->d_lfact, lf.data(), kLogFactN * sizeof(double),
+                       cudaMemcpyHostToDevice) != cudaSuccess) {
+            ppm_destroy(ctx);
+            return PPM_ENOMEM;
+        }
+    }
     if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->plan_ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -200,11 +213,12 @@ void ppm_destroy(ppm_ctx *ctx)
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     for (DevBuf *b : {&ctx->d_Ca, &ctx->d_LF, &ctx->d_TD, &ctx->d_I, &ctx->d_logT, &ctx->d_logg,
-                      &ctx->d_mu, &ctx->d_E, &ctx->d_E2, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
+                      &ctx->d_mu, &ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
                       &ctx->d_sigma, &ctx->d_plan, &ctx->ws})
         b->release();
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_lfact) cudaFree(ctx->d_lfact);
     if (ctx->d_triples) cudaFree(ctx->d_triples);
     for (auto &pd : ctx->pending) ctx->ev_pool.push_back(pd.a), ctx->ev_pool.push_back(pd.b);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
@@ -353,11 +367,11 @@ static ppm_status refresh_energies(ppm_ctx *ctx)
     if (!ctx->energy_dirty) return PPM_OK;
     const int nE = (int)ctx->E.size();
     const int nEpad = (nE + kEC - 1) / kEC * kEC;
-    std::vector<float> E(nEpad), E2(nEpad), pk(nEpad), invE(nEpad);
+    std::vector<float> E(nEpad), E3(nEpad), pk(nEpad), invE(nEpad);
     for (int k = 0; k < nEpad; ++k) {
         const double e = ctx->E[std::min(k, nE - 1)];
         E[k] = (float)e;
-        E2[k] = (float)(e * e);
+        E3[k] = (float)(e * e * e);
         invE[k] = (float)(1.0 / e);
         pk[k] = ctx->atm_ready ? (float)((std::log(e) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
     }
@@ -369,10 +383,10 @@ static ppm_status refresh_energies(ppm_ctx *ctx)
     }
     DeviceGuard g(ctx->device);
     PPM_CUDA(cudaDeviceSynchronize(), "sync");
-    for (DevBuf *b : {&ctx->d_E, &ctx->d_E2, &ctx->d_pk, &ctx->d_invE})
+    for (DevBuf *b : {&ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE})
         PPM_CUDA(b->ensure((size_t)nEpad * 4), "alloc energies");
     PPM_CUDA(cudaMemcpy(ctx->d_E.p, E.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
-    PPM_CUDA(cudaMemcpy(ctx->d_E2.p, E2.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
+    PPM_CUDA(cudaMemcpy(ctx->d_E3.p, E3.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
     PPM_CUDA(cudaMemcpy(ctx->d_pk.p, pk.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
     PPM_CUDA(cudaMemcpy(ctx->d_invE.p, invE.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
     ctx->nEpad = nEpad;
@@ -425,10 +439,22 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     if (key == ctx->plan_key && ctx->d_plan.p) return PPM_OK;
 
     HostPlan hp;
-    long long T = 0;
-    for (int b = 0; b < B; ++b)
-        T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + kPT - 1) / kPT);
+    // phase tile: 32 output phases per item, 16 when that leaves fewer than
+    // eight waves of blocks (finer items shorten the last wave)
+    auto ring_tiles = [&](int pt) {
+        long long T = 0;
+        for (int b = 0; b < B; ++b)
+            T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + pt - 1) / pt);
+        return T;
+    };
     const long long D = (long long)ctx->sm_count * 12;
+    int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
+    if (const char *env = getenv("PPM_PHASE_TILE")) {
+        const int v = atoi(env);
+        if (v == 16 || v == 32) pt = v;
+    }
+    hp.pt = pt;
+    const long long T = ring_tiles(pt);
     const int g = (int)std::max<long long>(1, T / std::max<long long>(D, 1));
     hp.inst.resize(B);
     for (int b = 0; b < B; ++b) {
@@ -439,7 +465,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         ip.ring0 = hp.total_rings;
         ip.elem0 = (int)hp.total_elems;
         ip.row0 = hp.total_rows;
-        ip.tiles = (ip.n_phase + kPT - 1) / kPT;
+        ip.tiles = (ip.n_phase + pt - 1) / pt;
         ip.tile0 = (int)hp.tiles.size();
         hp.total_rings += p->n_spots * ip.n_theta;
         hp.total_elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
@@ -452,7 +478,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
                 for (int r0 = 0; r0 < ip.n_theta; r0 += gb) {
                     Item it;
                     it.b = b; it.spot = s; it.r0 = r0; it.r1 = std::min(r0 + gb, ip.n_theta);
-                    it.j0 = t * kPT; it.nj = std::min(kPT, ip.n_phase - t * kPT);
+                    it.j0 = t * pt; it.nj = std::min(pt, ip.n_phase - t * pt);
                     hp.items.push_back(it);
                 }
             hp.tiles.push_back(make_int2(begin, (int)hp.items.size()));
@@ -500,14 +526,14 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
                                    Work *w)
 {
     const HostPlan &hp = ctx->plan;
-    const int ct = ctx->nc ? (ctx->nc + 63) / 64 : 1;
+    const int ct = ctx->nc ? loglike_ctiles(ctx->nc) : 1;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
     const size_t o_status = take((size_t)p->B * sizeof(int));
     const size_t o_recs = take((size_t)hp.total_rings * sizeof(RingRec));
     const size_t o_tmpl = take((size_t)hp.total_rings * 4 * (n_fp + 1) * sizeof(float));
     const size_t o_elems = take(hp.total_elems * sizeof(float));
-    const size_t o_part = take((size_t)hp.items.size() * kPT * ctx->nEpad * sizeof(float));
+    const size_t o_part = take((size_t)hp.items.size() * hp.pt * ctx->nEpad * sizeof(float));
     const size_t o_ft = take(need_ft ? (size_t)hp.total_rows * ctx->E.size() * sizeof(float) : 0);
     const size_t o_ll = take(need_ft ? (size_t)hp.total_rows * ct * sizeof(double) : 0);
     if (off > ctx->ws.n) {
@@ -537,7 +563,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     const size_t b_inst = align256(hp.inst.size() * sizeof(InstPlan));
     const size_t b_items = align256(hp.items.size() * sizeof(Item));
     char *d = ctx->d_plan.as<char>();
-    plan->B = p->B; plan->n_fp = n_fp; plan->n_items = (int)hp.items.size();
+    plan->B = p->B; plan->n_fp = n_fp; plan->n_items = (int)hp.items.size(); plan->pt = hp.pt;
     plan->total_rings = hp.total_rings;
     plan->inst = reinterpret_cast<const InstPlan *>(d);
     plan->items = reinterpret_cast<const Item *>(d + b_inst);
@@ -553,7 +579,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     A->logg = ctx->d_logg.as<double>(); A->mu = ctx->d_mu.as<float>();
     A->lnE0 = ctx->lnE0_t; A->dlnE = ctx->dlnE_t;
     en->nE = (int)ctx->E.size(); en->nEpad = ctx->nEpad;
-    en->E = ctx->d_E.as<float>(); en->E2 = ctx->d_E2.as<float>();
+    en->E = ctx->d_E.as<float>(); en->E3 = ctx->d_E3.as<float>();
     en->pk = ctx->d_pk.as<float>(); en->invE = ctx->d_invE.as<float>();
     en->sliding = ctx->sliding;
 }
@@ -573,9 +599,7 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
     EnergyDev en;
     fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
     // shared-memory budget of the shift-and-add kernel
-    size_t smem = 4 * (size_t)(4 * (res->n_fp + 1) + ctx->plan.n_phi_max + 3 * ctx->nEpad +
-                               kPT * ctx->nEpad + 64);
-    if (p->emission == 1) smem += 4 * (size_t)(ctx->nmu + ctx->nEt * ctx->nmu_pad + 8);
+    const size_t smem = shift_add_smem_bytes(P, plan, A, en, ctx->plan.n_phi_max);
     if (smem > ctx->smem_optin)
         return fail(ctx, PPM_EINVAL, "shared memory need %zu B exceeds %zu B (n_phi, nE too large)",
                     smem, ctx->smem_optin);
@@ -650,8 +674,8 @@ ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, co
         StageTimer t(ctx, 3, st);
         PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
                                 ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc, counts,
-                                counts_shared, bkg, tau, w.status, w.row_ll, model_counts, logL,
-                                st),
+                                counts_shared, bkg, tau, w.status, ctx->d_lfact, w.row_ll,
+                                model_counts, logL, st),
                  "likelihood kernels");
         t.done(2);
     }

@@ -21,9 +21,10 @@ constexpr double kPI = 3.141592653589793238462643383279502884;
 // stays in the normal range for element areas down to ~1e-9 sr (R/D ~ 1e-15).
 constexpr double kFluxScale = 1e30;
 
-// Shift-and-add tiling: output phases per work item and energies per chunk.
+// Shift-and-add tiling: at most kPT output phases per work item (the plan
+// picks 16 or 32), kEC energies per register chunk.
 constexpr int kPT = 32;
-constexpr int kEC = 32;
+constexpr int kEC = 16;
 constexpr int kMaxFp = 1024;
 constexpr int kSABlock = 256;
 
@@ -59,7 +60,7 @@ struct InstPlan {
     int elem0;   // first element slot (rings of this instance use n_phi slots each)
     int row0;    // first F_t row
     int tile0;   // first entry in the tile-range table
-    int tiles;   // ceil(n_phase / kPT)
+    int tiles;   // ceil(n_phase / pt)
 };
 
 // One shift-and-add work item: rings [r0, r1) of one spot, phases [j0, j0+nj).
@@ -86,6 +87,7 @@ struct Params {
 
 struct PlanDev {
     int B, n_fp, n_items, total_rings;
+    int pt;  // output phases per work item
     const InstPlan *inst;
     const Item *items;
     const int2 *tile_items;  // [sum tiles] item range of (instance, tile)
@@ -95,7 +97,7 @@ struct PlanDev {
 struct EnergyDev {
     int nE, nEpad;
     const float *E;      // [nEpad] keV (padded with the last value)
-    const float *E2;     // [nEpad] E^2
+    const float *E3;     // [nEpad] E^3
     const float *pk;     // [nEpad] (ln E - lnE0_table) / dlnE_table
     const float *invE;   // [nEpad] 1/E
     int sliding;         // consecutive pk differ by < 1 (one node shift per step)
@@ -110,6 +112,8 @@ cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
                         int *status, unsigned *err, unsigned long long *triples, int nE,
                         cudaStream_t st);
 
+size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
+                            const EnergyDev &en, int n_phi_max);
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
@@ -118,10 +122,13 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
 cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
                           const int *status, int total_rows, float *Ft, cudaStream_t st);
 
+constexpr int kLogFactN = 4096;  // ln d! table size
+
+int loglike_ctiles(int nc);
 cudaError_t launch_loglike(const Params &p, const PlanDev &plan, const float *Ft,
                            int total_rows, int nE, const float *R, const float *sigma,
                            int nc, const int *counts, int counts_shared, const float *bkg,
-                           double tau, const int *status, double *row_ll,
+                           double tau, const int *status, const double *lfact, double *row_ll,
                            float *model_counts, double *logL, cudaStream_t st);
 
 // row -> instance lookup (binary search over InstPlan.row0)

@@ -1,7 +1,7 @@
 // Shift-and-add with atmosphere interpolation, FP32 (Sect. 2.8.3, Eq. add_Ft;
 // Sect. 4 mixed-order interpolation).
 //
-// Work item = (instance, spot, ring range, tile of kPT output phases).  Per
+// Work item = (instance, spot, ring range, tile of `pt` output phases).  Per
 // ring the block stages in shared memory:
 //   - the ring's template (phi_o, F, z, mu at n_fp + 1 fine phases),
 //   - the compacted azimuths of its active elements,
@@ -11,15 +11,18 @@
 // Each warp owns one output phase at a time; its lanes are 32 elements of
 // the ring (neighbouring elements see nearly the same redshift and emission
 // angle, so their table reads are broadcast-friendly and their stencil
-// shifts coincide).  A lane holds four elements and 32 energy accumulators:
-// for each element the mu stencil is contracted once per table energy node
-// (4 FMA) and the cubic in ln E is evaluated per observed energy from a
-// sliding window of four contracted nodes kept in registers (Newton form:
-// 3 FMA + 3 adds per energy).  After each chunk of 32 energies the 32
-// accumulators are transposed across the warp with 31 shuffles so lane l
-// owns energy l, and added to the block's phase x energy tile.  No atomics:
-// each item writes its tile to a partial buffer that a second kernel sums
-// in a fixed order.
+// shifts coincide).  A lane holds four elements and 16 energy accumulators.
+// For each element the mu stencil is contracted once per table energy node
+// (4 FMA) and the cubic in ln E of the current node interval is kept as
+// power-basis coefficients in registers, so an observed energy costs one add
+// (position), one compare (interval change) and three FMA (Horner); an
+// interval change contracts one new node and rebuilds the four coefficients.
+// After each chunk of 16 energies the accumulators are transposed across the
+// warp with 16 shuffles so lane l owns energy l, and added to the block's
+// phase x energy tile.  No atomics: each item writes its tile to a partial
+// buffer that a second kernel sums in a fixed order.
+#include <algorithm>
+
 #include "ppm_internal.cuh"
 
 namespace ppm {
@@ -28,7 +31,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Layout {
-    int tmpl, elems, slab, munodes, pk, E, E2, fblk, total;  // offsets in floats
+    int tmpl, elems, slab, munodes, pk, E, E3, fblk, total;  // offsets in floats
 };
 
 __device__ __forceinline__ float contract4(const float *__restrict__ s, int off, float w0,
@@ -37,11 +40,12 @@ __device__ __forceinline__ float contract4(const float *__restrict__ s, int off,
     return fmaf(w3, s[off + 3], fmaf(w2, s[off + 2], fmaf(w1, s[off + 1], w0 * s[off])));
 }
 
-// 32 accumulators per lane -> lane l receives the warp sum of accumulator l
-__device__ __forceinline__ float transpose_reduce(float (&acc)[kEC], int lane)
+// 16 accumulators per lane -> lanes l and l ^ 16 receive the warp sum of
+// accumulator l & 15
+__device__ __forceinline__ float transpose_reduce16(float (&acc)[kEC], int lane)
 {
 #pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
+    for (int off = 8; off >= 1; off >>= 1) {
         const bool upper = (lane & off) != 0;
 #pragma unroll
         for (int i = 0; i < off; ++i) {
@@ -50,16 +54,14 @@ __device__ __forceinline__ float transpose_reduce(float (&acc)[kEC], int lane)
             acc[i] = keep + __shfl_xor_sync(kFull, send, off);
         }
     }
-    return acc[0];
+    return acc[0] + __shfl_xor_sync(kFull, acc[0], 16);
 }
 
 // Template value at observed phase phip (linear, lower-bound search on phi_o).
-__device__ __forceinline__ void template_at(const float *__restrict__ ph,
-                                            const float *__restrict__ F,
-                                            const float *__restrict__ Z,
-                                            const float *__restrict__ M, int n_fp, int top,
+__device__ __forceinline__ void template_at(const float *__restrict__ ph, int n_fp, int top,
                                             float phip, float &Fp, float &zp, float &mp)
 {
+    const float *F = ph + (n_fp + 1), *Z = F + (n_fp + 1), *M = Z + (n_fp + 1);
     int lo = 0;
     for (int step = top; step > 0; step >>= 1) {
         const int c = lo + step;
@@ -72,92 +74,84 @@ __device__ __forceinline__ void template_at(const float *__restrict__ ph,
     mp = fmaf(M[lo + 1] - M[lo], w, M[lo]);
 }
 
-// State of one (element, output phase) pair in the atmosphere path.
-struct PairA {
+// Interpolation weights of one (element, output phase) pair.
+struct PairW {
     float w0, w1, w2, w3;  // mu stencil weights times F_p
     int s0;                // first mu row of the stencil
     float lz;              // ln(z_p) / dlnE_table
-    int mode;              // 0 off, 1 sliding window, 2 general (table edges)
-    int nb;                // smem offset of node q+2 (row) + s0
-    float q, qn, W1, W2, W3, d1, d2, d3;
+    bool on;               // contributes (active element, visible phase)
 };
 
-__device__ __forceinline__ void pair_setup_atm(PairA &P, bool on, float s, float phi_out,
-                                               const float *sm, const Layout &lay, int n_fp,
-                                               int top, const AtmDev &A,
-                                               const EnergyDev &en, float inv_dlnE,
-                                               float pk0, float pkl, float lz_safe)
+__device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, const float *ph,
+                                              const float *mun, int n_fp, int top,
+                                              const AtmDev &A, float inv_dlnE)
 {
-    const float *ph = sm + lay.tmpl;
-    const float *Fa = ph + (n_fp + 1);
-    const float *Za = Fa + (n_fp + 1);
-    const float *Ma = Za + (n_fp + 1);
-    const float *mun = sm + lay.munodes;
-    const int nmu = A.nmu;
+    PairW P;
     P.w0 = P.w1 = P.w2 = P.w3 = 0.0f;
     P.s0 = 0;
-    P.lz = lz_safe;
-    P.mode = 0;
-    if (on) {
-        const float x = phi_out + s + 1.0f - ph[0];
-        const float phip = x - floorf(x) + ph[0];
-        float Fp, zp, mp;
-        template_at(ph, Fa, Za, Ma, n_fp, top, phip, Fp, zp, mp);
-        if (Fp != 0.0f && zp > 0.0f && zp < 1e30f) {
-            // mu: clamp, interval, mixed-order weights (Sect. 4)
-            const float mu = fminf(fmaxf(mp, mun[0]), mun[nmu - 1]);
-            int i = 0;
-            for (int step = 64; step > 0; step >>= 1) {
-                const int c = i + step;
-                if (c <= nmu - 2 && mun[c] <= mu) i = c;
-            }
-            float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            int s0;
-            if (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1) {
-                s0 = i - 1;
-                const float x0 = mun[s0], x1 = mun[s0 + 1], x2 = mun[s0 + 2], x3 = mun[s0 + 3];
-                w[0] = (mu - x1) * (mu - x2) * (mu - x3) / ((x0 - x1) * (x0 - x2) * (x0 - x3));
-                w[1] = (mu - x0) * (mu - x2) * (mu - x3) / ((x1 - x0) * (x1 - x2) * (x1 - x3));
-                w[2] = (mu - x0) * (mu - x1) * (mu - x3) / ((x2 - x0) * (x2 - x1) * (x2 - x3));
-                w[3] = (mu - x0) * (mu - x1) * (mu - x2) / ((x3 - x0) * (x3 - x1) * (x3 - x2));
-            } else {
-                s0 = min(max(i - 1, 0), nmu - 4);
-                const float t = (mu - mun[i]) / (mun[i + 1] - mun[i]);
-                const int o = i - s0;
-#pragma unroll
-                for (int a = 0; a < 4; ++a) w[a] = (a == o) ? 1.0f - t : ((a == o + 1) ? t : 0.0f);
-            }
-            P.w0 = w[0] * Fp; P.w1 = w[1] * Fp; P.w2 = w[2] * Fp; P.w3 = w[3] * Fp;
-            P.s0 = s0;
-            const float lz = logf(zp) * inv_dlnE;
-            const bool fast = en.sliding && (pk0 + lz >= 1.0f) && (pkl + lz < (float)(A.nE - 2));
-            P.mode = fast ? 1 : 2;
-            P.lz = lz;
-        }
+    P.lz = 0.0f;
+    P.on = false;
+    if (!on) return P;
+    const float x = phi_out + s + 1.0f - ph[0];
+    const float phip = x - floorf(x) + ph[0];
+    float Fp, zp, mp;
+    template_at(ph, n_fp, top, phip, Fp, zp, mp);
+    if (!(Fp != 0.0f && zp > 0.0f && zp < 1e30f)) return P;
+    const int nmu = A.nmu;
+    // mu: clamp, interval, mixed-order weights (Sect. 4)
+    const float mu = fminf(fmaxf(mp, mun[0]), mun[nmu - 1]);
+    int i = 0;
+    for (int step = 64; step > 0; step >>= 1) {
+        const int c = i + step;
+        if (c <= nmu - 2 && mun[c] <= mu) i = c;
     }
+    float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int s0;
+    if (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1) {
+        s0 = i - 1;
+        const float x0 = mun[s0], x1 = mun[s0 + 1], x2 = mun[s0 + 2], x3 = mun[s0 + 3];
+        w[0] = (mu - x1) * (mu - x2) * (mu - x3) / ((x0 - x1) * (x0 - x2) * (x0 - x3));
+        w[1] = (mu - x0) * (mu - x2) * (mu - x3) / ((x1 - x0) * (x1 - x2) * (x1 - x3));
+        w[2] = (mu - x0) * (mu - x1) * (mu - x3) / ((x2 - x0) * (x2 - x1) * (x2 - x3));
+        w[3] = (mu - x0) * (mu - x1) * (mu - x2) / ((x3 - x0) * (x3 - x1) * (x3 - x2));
+    } else {
+        s0 = min(max(i - 1, 0), nmu - 4);
+        const float t = (mu - mun[i]) / (mun[i + 1] - mun[i]);
+        const int o = i - s0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) w[a] = (a == o) ? 1.0f - t : ((a == o + 1) ? t : 0.0f);
+    }
+    P.w0 = w[0] * Fp; P.w1 = w[1] * Fp; P.w2 = w[2] * Fp; P.w3 = w[3] * Fp;
+    P.s0 = s0;
+    P.lz = logf(zp) * inv_dlnE;
+    P.on = true;
+    return P;
 }
 
-__device__ __forceinline__ void sliding_init(PairA &P, const float *slab, int Pm, float pk0,
-                                             float lz_safe)
+// Sliding-interval state of one element in the fast loop.  The cubic of the
+// current interval q is c0 + c1 t + c2 t^2 + c3 t^3 with t = pk + off, off =
+// lz - q; nb addresses node q+2 (row) + stencil start.  W2, W3 keep nodes
+// q+1 and q+2 (c0 is node q).
+struct El {
+    float w0, w1, w2, w3;
+    int nb;
+    float off, c0, c1, c2, c3, W2, W3;
+};
+
+// cubic through (-1, a), (0, b), (1, c), (2, d) in power basis
+__device__ __forceinline__ void cubic_coeffs(float a, float b, float c, float d, El &E)
 {
-    const float lz = (P.mode == 1) ? P.lz : lz_safe;
-    const float q = floorf(pk0 + lz);
-    const int qi = (int)q;
-    P.nb = (qi + 2) * Pm + P.s0;
-    const float Wm = contract4(slab, P.nb - 3 * Pm, P.w0, P.w1, P.w2, P.w3);
-    P.W1 = contract4(slab, P.nb - 2 * Pm, P.w0, P.w1, P.w2, P.w3);
-    P.W2 = contract4(slab, P.nb - Pm, P.w0, P.w1, P.w2, P.w3);
-    P.W3 = contract4(slab, P.nb, P.w0, P.w1, P.w2, P.w3);
-    P.d1 = P.W2 - P.W1;
-    P.d2 = 0.5f * (Wm + P.W2) - P.W1;
-    P.d3 = ((P.W3 - Wm) + 3.0f * (P.W1 - P.W2)) * (1.0f / 6.0f);
-    P.q = q;
-    P.qn = q + 1.0f;
+    E.c0 = b;
+    E.c2 = fmaf(0.5f, a + c, -b);
+    E.c3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (b - c));
+    E.c1 = fmaf(c - a, 0.5f, -E.c3);
+    E.W2 = c;
+    E.W3 = d;
 }
 
 // general evaluation (table edges / clamping) of the contracted spectrum at p
-__device__ __noinline__ float eval_general(const PairA &P, const float *slab, int Pm,
-                                              int nE_t, float p)
+__device__ __noinline__ float eval_general(const PairW &P, const float *slab, int Pm, int nE_t,
+                                           float p)
 {
     if (p <= 0.0f) return contract4(slab, P.s0, P.w0, P.w1, P.w2, P.w3);
     if (p >= (float)(nE_t - 1))
@@ -170,13 +164,22 @@ __device__ __noinline__ float eval_general(const PairA &P, const float *slab, in
         const float b = contract4(slab, qi * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
         const float c = contract4(slab, (qi + 1) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
         const float d = contract4(slab, (qi + 2) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
-        const float d1 = c - b, d2 = 0.5f * (a + c) - b;
-        const float d3 = ((d - a) + 3.0f * (b - c)) * (1.0f / 6.0f);
-        return b + t * (d1 + (t - 1.0f) * (d2 + (t + 1.0f) * d3));
+        const float c2 = fmaf(0.5f, a + c, -b);
+        const float c3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (b - c));
+        const float c1 = fmaf(c - a, 0.5f, -c3);
+        return fmaf(t, fmaf(t, fmaf(t, c3, c2), c1), b);
     }
     const float b = contract4(slab, qi * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
     const float c = contract4(slab, (qi + 1) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
     return fmaf(t, c - b, b);
+}
+
+// weights of a pair for the slow path (kept out of line: it is rarely taken)
+__device__ __noinline__ PairW pair_weights_slow(float s, float phi_out, const float *ph,
+                                                const float *mun, int n_fp, int top,
+                                                const AtmDev &A, float inv_dlnE)
+{
+    return pair_weights(true, s, phi_out, ph, mun, n_fp, top, A, inv_dlnE);
 }
 
 template <int EMIS>
@@ -190,19 +193,20 @@ __global__ void __launch_bounds__(kSABlock, 2)
     const Item it = plan.items[blockIdx.x];
     const InstPlan ip = plan.inst[it.b];
     const int n_fp = plan.n_fp;
+    const int pt = plan.pt;
     const int nEpad = en.nEpad;
     const int nch = nEpad / kEC;
     float *Fblk = sm + lay.fblk;
     float *spk = sm + lay.pk;
     float *sE = sm + lay.E;
-    float *sE2 = sm + lay.E2;
+    float *sE3 = sm + lay.E3;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    for (int i = tid; i < kPT * nEpad; i += blockDim.x) Fblk[i] = 0.0f;
+    for (int i = tid; i < pt * nEpad; i += blockDim.x) Fblk[i] = 0.0f;
     for (int i = tid; i < nEpad; i += blockDim.x) {
         spk[i] = en.pk[i];
         sE[i] = en.E[i];
-        sE2[i] = en.E2[i];
+        sE3[i] = en.E3[i];
     }
     if (EMIS == 1)
         for (int i = tid; i < A.nmu; i += blockDim.x) sm[lay.munodes + i] = A.mu[i];
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
             const float *esrc = elems + (size_t)ip.elem0 + (size_t)(ring - ip.ring0) * ip.n_phi;
             for (int i = tid; i < rec.n_active; i += blockDim.x) sm[lay.elems + i] = esrc[i];
             if (EMIS == 1) {
-                const size_t plane = (size_t)A.nmu * A.nE;
+                const int plane = A.nmu * A.nE;
                 const float *I00 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
                 const float *I01 = I00 + plane;
                 const float *I10 = I00 + (size_t)A.ng * plane;
@@ -234,11 +238,25 @@ __global__ void __launch_bounds__(kSABlock, 2)
                 const float w00 = (1.0f - wT) * (1.0f - wg), w01 = (1.0f - wT) * wg;
                 const float w10 = wT * (1.0f - wg), w11 = wT * wg;
                 float *slab = sm + lay.slab;
-                for (int idx = tid; idx < (int)plane; idx += blockDim.x) {
-                    const int m = idx / A.nE, n = idx - m * A.nE;
-                    const float v = w00 * __ldg(I00 + idx) + w01 * __ldg(I01 + idx) +
-                                    w10 * __ldg(I10 + idx) + w11 * __ldg(I11 + idx);
-                    slab[n * Pm + m] = v;
+                constexpr int U = 4;  // loads in flight per thread
+                for (int base = tid; base < plane; base += U * kSABlock) {
+                    float v[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int idx = base + u * kSABlock;
+                        v[u] = 0.0f;
+                        if (idx < plane)
+                            v[u] = w00 * __ldg(I00 + idx) + w01 * __ldg(I01 + idx) +
+                                   w10 * __ldg(I10 + idx) + w11 * __ldg(I11 + idx);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int idx = base + u * kSABlock;
+                        if (idx < plane) {
+                            const int m = idx / A.nE, n = idx - m * A.nE;
+                            slab[n * Pm + m] = v[u];
+                        }
+                    }
                 }
             }
         }
@@ -247,6 +265,8 @@ __global__ void __launch_bounds__(kSABlock, 2)
         const int n_act = rec.n_active;
         const float *sel = sm + lay.elems;
         const float *slab = sm + lay.slab;
+        const float *ph = sm + lay.tmpl;
+        const float *mun = sm + lay.munodes;
         const float pk0 = spk[0], pkl = spk[en.nE - 1];
         const float lz_safe = 1.25f - pk0;
 
@@ -254,71 +274,88 @@ __global__ void __launch_bounds__(kSABlock, 2)
             const float phi_out = (float)(it.j0 + jl) * inv_nphase;
             for (int g0 = 0; g0 < n_act; g0 += 128) {
                 if (EMIS == 1) {
-                    PairA P[4];
+                    El E[4];
+                    bool slow[4], anyslow[4], anyon[4];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int m = g0 + lane + 32 * e;
-                        pair_setup_atm(P[e], m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, sm,
-                                       lay, n_fp, top, A, en, inv_dlnE, pk0, pkl, lz_safe);
-                    }
-                    bool anyfast[4], anyslow[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        anyfast[e] = __any_sync(kFull, P[e].mode == 1);
-                        anyslow[e] = __any_sync(kFull, P[e].mode == 2);
-                        if (anyfast[e]) sliding_init(P[e], slab, Pm, pk0, lz_safe);
+                        const PairW P = pair_weights(m < n_act, m < n_act ? sel[m] : 0.0f,
+                                                     phi_out, ph, mun, n_fp, top, A, inv_dlnE);
+                        const bool fast = P.on && en.sliding && (pk0 + P.lz >= 1.0f) &&
+                                          (pkl + P.lz < (float)(A.nE - 2));
+                        slow[e] = P.on && !fast;
+                        anyslow[e] = __any_sync(kFull, slow[e]);
+                        anyon[e] = __any_sync(kFull, fast);
+                        // lanes outside the sliding window run it with zero weights
+                        const float lz = fast ? P.lz : lz_safe;
+                        E[e].w0 = fast ? P.w0 : 0.0f;
+                        E[e].w1 = fast ? P.w1 : 0.0f;
+                        E[e].w2 = fast ? P.w2 : 0.0f;
+                        E[e].w3 = fast ? P.w3 : 0.0f;
+                        const float q = floorf(pk0 + lz);
+                        E[e].off = lz - q;
+                        E[e].nb = ((int)q + 2) * Pm + P.s0;
+                        if (anyon[e]) {
+                            const float a = contract4(slab, E[e].nb - 3 * Pm, E[e].w0, E[e].w1,
+                                                      E[e].w2, E[e].w3);
+                            const float b = contract4(slab, E[e].nb - 2 * Pm, E[e].w0, E[e].w1,
+                                                      E[e].w2, E[e].w3);
+                            const float c = contract4(slab, E[e].nb - Pm, E[e].w0, E[e].w1,
+                                                      E[e].w2, E[e].w3);
+                            const float d = contract4(slab, E[e].nb, E[e].w0, E[e].w1, E[e].w2,
+                                                      E[e].w3);
+                            cubic_coeffs(a, b, c, d, E[e]);
+                        } else {
+                            E[e].c0 = E[e].c1 = E[e].c2 = E[e].c3 = 0.0f;
+                            E[e].W2 = E[e].W3 = 0.0f;
+                        }
                     }
                     for (int c = 0; c < nch; ++c) {
                         float acc[kEC];
-#pragma unroll
-                        for (int s = 0; s < kEC; ++s) acc[s] = 0.0f;
                         const float *pkc = spk + c * kEC;
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (anyfast[e]) {
-                            // sliding window (lanes not in sliding mode add zero here)
-                            const float lz = (P[e].mode == 1) ? P[e].lz : lz_safe;
-                            const float sw = (P[e].mode == 1) ? 1.0f : 0.0f;
+                        for (int s = 0; s < kEC; ++s) {
+                            const float pk = pkc[s];
+                            float t[4];
 #pragma unroll
-                            for (int s = 0; s < kEC; ++s) {
-                                const float pv = pkc[s] + lz;
-                                if (pv >= P[e].qn) {
-                                    P[e].nb += Pm;
-                                    const float nv = contract4(slab, P[e].nb, P[e].w0, P[e].w1,
-                                                               P[e].w2, P[e].w3);
-                                    const float a = P[e].W1;
-                                    P[e].W1 = P[e].W2;
-                                    P[e].W2 = P[e].W3;
-                                    P[e].W3 = nv;
-                                    P[e].d1 = P[e].W2 - P[e].W1;
-                                    P[e].d2 = 0.5f * (a + P[e].W2) - P[e].W1;
-                                    P[e].d3 = ((P[e].W3 - a) + 3.0f * (P[e].W1 - P[e].W2)) *
-                                              (1.0f / 6.0f);
-                                    P[e].q = P[e].qn;
-                                    P[e].qn += 1.0f;
+                            for (int e = 0; e < 4; ++e) t[e] = pk + E[e].off;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                if (anyon[e] && t[e] >= 1.0f) {
+                                    E[e].nb += Pm;
+                                    const float d = contract4(slab, E[e].nb, E[e].w0, E[e].w1,
+                                                              E[e].w2, E[e].w3);
+                                    cubic_coeffs(E[e].c0, E[e].W2, E[e].W3, d, E[e]);
+                                    E[e].off -= 1.0f;
+                                    t[e] -= 1.0f;
                                 }
-                                const float t = pv - P[e].q;
-                                const float v = fmaf(t, fmaf(pv - P[e].qn,
-                                                             fmaf(t + 1.0f, P[e].d3, P[e].d2),
-                                                             P[e].d1),
-                                                     P[e].W1);
-                                acc[s] = fmaf(sw, v, acc[s]);
                             }
-                            }
-                            if (anyslow[e] && P[e].mode == 2) {
+                            float v[4];
 #pragma unroll
-                                for (int s = 0; s < kEC; ++s)
-                                    acc[s] += eval_general(P[e], slab, Pm, A.nE, pkc[s] + P[e].lz);
+                            for (int e = 0; e < 4; ++e)
+                                v[e] = fmaf(t[e], fmaf(t[e], fmaf(t[e], E[e].c3, E[e].c2), E[e].c1),
+                                            E[e].c0);
+                            acc[s] = (v[0] + v[1]) + (v[2] + v[3]);
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (anyslow[e] && slow[e]) {
+                                const int m = g0 + lane + 32 * e;
+                                const PairW P = pair_weights_slow(sel[m], phi_out, ph, mun, n_fp,
+                                                                  top, A, inv_dlnE);
+#pragma unroll
+                                for (int k = 0; k < kEC; ++k)
+                                    acc[k] += eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz);
                             }
                         }
-                        const float tot = transpose_reduce(acc, lane);
-                        Fblk[jl * nEpad + c * kEC + lane] += tot;
+                        const float tot = transpose_reduce16(acc, lane);
+                        if (lane < kEC) Fblk[jl * nEpad + c * kEC + lane] += tot;
                     }
                 } else {
-                    // analytic isotropic blackbody: I(E')/E = K z^3 E^2 / expm1(z E / kT)
+                    // analytic isotropic blackbody: I(z E) = K z^3 E^3 / expm1(z E / kT); the
+                    // 1/E of Eq. add_Ft is applied with the flux scale in the reduction
                     const float K = (float)(2.0 / (kH_KEVS * kH_KEVS * kH_KEVS * kC_CM * kC_CM));
                     const float inv_kT = 1.0f / rec.kT;
-                    const float *ph = sm + lay.tmpl;
                     float az[4], bz[4];
                     bool anyon[4];
 #pragma unroll
@@ -330,8 +367,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
                             const float x = phi_out + sel[m] + 1.0f - ph[0];
                             const float phip = x - floorf(x) + ph[0];
                             float Fp, zp, mp;
-                            template_at(ph, ph + (n_fp + 1), ph + 2 * (n_fp + 1),
-                                        ph + 3 * (n_fp + 1), n_fp, top, phip, Fp, zp, mp);
+                            template_at(ph, n_fp, top, phip, Fp, zp, mp);
                             if (Fp != 0.0f && zp > 0.0f && zp < 1e30f) {
                                 az[e] = zp * inv_kT;
                                 bz[e] = Fp * K * zp * zp * zp;
@@ -349,41 +385,92 @@ __global__ void __launch_bounds__(kSABlock, 2)
 #pragma unroll
                             for (int s = 0; s < kEC; ++s) {
                                 const int k = c * kEC + s;
-                                acc[s] += bz[e] * sE2[k] / expm1f(az[e] * sE[k]);
+                                acc[s] += bz[e] * sE3[k] / expm1f(az[e] * sE[k]);
                             }
                         }
-                        const float tot = transpose_reduce(acc, lane);
-                        Fblk[jl * nEpad + c * kEC + lane] += tot;
+                        const float tot = transpose_reduce16(acc, lane);
+                        if (lane < kEC) Fblk[jl * nEpad + c * kEC + lane] += tot;
                     }
                 }
             }
         }
     }
     __syncthreads();
-    float *dst = partials + (size_t)blockIdx.x * kPT * nEpad;
+    float *dst = partials + (size_t)blockIdx.x * pt * nEpad;
     for (int i = tid; i < it.nj * nEpad; i += blockDim.x) dst[i] = Fblk[i];
 }
 
-__global__ void k_reduce(PlanDev plan, EnergyDev en, const float *__restrict__ partials,
-                         const int *__restrict__ status, int total_rows, float *__restrict__ Ft)
+// F_t[row][k] = (sum over the work items of (instance, phase tile)) / E_k.
+// One block per (row, 128-energy chunk): warp w sums items w, w+8, ... with
+// float4 loads, then the 8 warp sums are added in warp order (fixed order, so
+// the result does not depend on scheduling).
+__global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
+                                               const float *__restrict__ partials,
+                                               const int *__restrict__ status, int total_rows,
+                                               float *__restrict__ Ft)
 {
+    __shared__ float4 red[8][32];
     const int nE = en.nE, nEpad = en.nEpad;
-    const size_t total = (size_t)total_rows * nE;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int row = (int)(t / nE), k = (int)(t - (size_t)row * nE);
-        const int b = find_instance_by_row(plan.inst, plan.B, row);
-        const InstPlan ip = plan.inst[b];
-        const int j = row - ip.row0;
-        const int tile = j / kPT, jl = j - tile * kPT;
-        const int2 rng = plan.tile_items[ip.tile0 + tile];
-        float s = 0.0f;
-        for (int i = rng.x; i < rng.y; ++i) s += partials[((size_t)i * kPT + jl) * nEpad + k];
-        Ft[t] = (status[b] == 0) ? s * en.invE[k] * (float)(1.0 / kFluxScale) : 0.0f;
+    const int pt = plan.pt;
+    const int row = blockIdx.x;
+    const int k4 = blockIdx.y * 32 + (threadIdx.x & 31);   // float4 index along energy
+    const int warp = threadIdx.x >> 5;
+    const int b = find_instance_by_row(plan.inst, plan.B, row);
+    const InstPlan ip = plan.inst[b];
+    const int j = row - ip.row0;
+    const int tile = j / pt, jl = j - tile * pt;
+    const int2 rng = plan.tile_items[ip.tile0 + tile];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * k4 < nEpad) {
+        const float4 *base = reinterpret_cast<const float4 *>(partials + (size_t)jl * nEpad) + k4;
+        const size_t stride4 = (size_t)pt * nEpad / 4;
+        int i = rng.x + warp;
+        for (; i + 8 < rng.y; i += 16) {
+            const float4 a = base[(size_t)i * stride4], c = base[(size_t)(i + 8) * stride4];
+            acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+            acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
+        }
+        if (i < rng.y) {
+            const float4 a = base[(size_t)i * stride4];
+            acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+        }
+    }
+    red[warp][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (warp == 0 && 4 * k4 < nEpad) {
+        float4 s = red[0][threadIdx.x];
+        for (int w = 1; w < 8; ++w) {
+            const float4 v = red[w][threadIdx.x];
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        }
+        const float sc = (float)(1.0 / kFluxScale);
+        const bool ok = status[b] == 0;
+        const float vals[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = 4 * k4 + q;
+            if (k < nE) Ft[(size_t)row * nE + k] = ok ? vals[q] * en.invE[k] * sc : 0.0f;
+        }
     }
 }
 
 }  // namespace
+
+size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
+                            const EnergyDev &en, int n_phi_max)
+{
+    int off = 0;
+    auto take = [&](int n) { off += (n + 3) & ~3; };
+    take(4 * (plan.n_fp + 1));
+    take(n_phi_max);
+    take(p.emission == 1 ? A.nmu : 0);
+    take(p.emission == 1 ? A.nE * A.nmu_pad : 0);
+    take(en.nEpad);
+    take(en.nEpad);
+    take(en.nEpad);
+    take(plan.pt * en.nEpad);
+    return (size_t)off * sizeof(float);
+}
 
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
@@ -400,8 +487,8 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
     lay.slab = take(p.emission == 1 ? A.nE * A.nmu_pad : 0);
     lay.pk = take(en.nEpad);
     lay.E = take(en.nEpad);
-    lay.E2 = take(en.nEpad);
-    lay.fblk = take(kPT * en.nEpad);
+    lay.E3 = take(en.nEpad);
+    lay.fblk = take(plan.pt * en.nEpad);
     lay.total = off;
     const size_t bytes = (size_t)off * sizeof(float);
     cudaError_t e;
@@ -424,10 +511,9 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
 cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
                           const int *status, int total_rows, float *Ft, cudaStream_t st)
 {
-    const size_t total = (size_t)total_rows * en.nE;
-    if (total == 0) return cudaSuccess;
-    const int blocks = (int)std::min<size_t>((total + 255) / 256, 65535);
-    k_reduce<<<blocks, 256, 0, st>>>(plan, en, partials, status, total_rows, Ft);
+    if (total_rows <= 0) return cudaSuccess;
+    dim3 grid(total_rows, (en.nEpad / 4 + 31) / 32);
+    k_reduce<<<grid, 256, 0, st>>>(plan, en, partials, status, total_rows, Ft);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ def _compare(orc, synth, spec):
     assert np.max(np.abs(Ca[m] - L.Ca[m])) < 1e-10
     assert np.max(np.abs(LF[m] - L.LF[m]) / np.abs(L.LF[m])) < 1e-7
     m = ~np.isnan(L.TD)
-    assert np.max(np.abs(TD[m] - L.TD[m])) < 1e-10
+    assert np.max(np.abs(TD[m] - L.TD[m])) < 2e-11
 
 
 def test_lens_tables_small_grid(orc, synth, small_lens):

@@ -143,3 +143,22 @@ def test_bad_resolution_is_rejected(synth, small_lens):
         with pytest.raises(ppm.PPMError) as e:
             ctx.profile(dp)
         assert e.value.status == ppm.PPM_EINVAL
+
+
+def test_energies_past_table_edges(orc, synth, atm, small_lens):
+    """Redshifted energies leave the table (E' up to ~12 keV > 10 keV, down to
+    0.07 keV near the 0.05 keV edge): linear edge intervals and clamping."""
+    w = synth.atm_two_spot(n_theta=14, n_phi=20, n_phase=32, n_E=48, n_chan=8, atm=atm,
+                           lens=small_lens)
+    w.E_keV = synth.logspace(0.06, 9.5, 48)
+    got, _ = gpu_profile(w)
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
+
+
+def test_coarse_energy_grid_general_path(orc, synth, atm, small_lens):
+    """Eight energies 0.1-5 keV step ~17 table nodes: the sliding window cannot
+    be used and every energy takes the general interpolation path."""
+    w = synth.atm_two_spot(n_theta=14, n_phi=36, n_phase=33, n_E=8, n_chan=8, atm=atm,
+                           lens=small_lens)
+    got, _ = gpu_profile(w)
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
