@@ -148,9 +148,9 @@ def test_bad_resolution_is_rejected(synth, small_lens):
 def test_energies_past_table_edges(orc, synth, atm, small_lens):
     """Redshifted energies leave the table (E' up to ~12 keV > 10 keV, down to
     0.07 keV near the 0.05 keV edge): linear edge intervals and clamping."""
-    w = synth.atm_two_spot(n_theta=14, n_phi=20, n_phase=32, n_E=48, n_chan=8, atm=atm,
+    w = synth.atm_two_spot(n_theta=14, n_phi=20, n_phase=32, n_E=200, n_chan=8, atm=atm,
                            lens=small_lens)
-    w.E_keV = synth.logspace(0.06, 9.5, 48)
+    w.E_keV = synth.logspace(0.06, 9.5, 200)   # fine grid: sliding and edge lanes mix
     got, _ = gpu_profile(w)
     assert max_rel(got, orc.profile(w)) < TOL_ATM
 
