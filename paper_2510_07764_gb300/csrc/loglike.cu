@@ -5,16 +5,16 @@
 //   lambda    = tau C + bkg
 //   logL[b]   = sum_{rows of b, c} d ln(lambda) - lambda - ln Gamma(d + 1)
 //
-// k_resp_ll: 32 x 32 output tile per block, K staged through shared memory
-// in steps of 32, each thread 2 x 2 outputs; the epilogue evaluates the
-// likelihood terms in FP64 and writes one partial sum per (row, column tile).
+// k_resp_ll: 16 x 32 output tile per block (128 threads, 2 x 2 outputs each),
+// K staged through shared memory in steps of 32; the epilogue evaluates the
+// likelihood terms (ln lambda in FP32, sums in FP64) and writes one partial sum per (row, column tile).
 // k_ll_final adds the partials of each instance in a fixed order.
 #include "ppm_internal.cuh"
 
 namespace ppm {
 namespace {
 
-constexpr int kTM = 32, kTN = 32, kTK = 32;
+constexpr int kTM = 16, kTN = 32, kTK = 32, kThreads = 128;
 
 // ln Gamma(d + 1) = ln d!: table below kLogFactN (built on the host in FP64),
 // Stirling series above it (relative error < 1e-16 for d >= 4096).
@@ -26,7 +26,7 @@ __device__ __forceinline__ double log_factorial(int d, const double *__restrict_
            r * (1.0 / 12.0 - r2 * (1.0 / 360.0 - r2 * (1.0 / 1260.0)));
 }
 
-__global__ void __launch_bounds__(256) k_resp_ll(Params p, PlanDev plan,
+__global__ void __launch_bounds__(kThreads) k_resp_ll(Params p, PlanDev plan,
                                                 const float *__restrict__ Ft, int total_rows,
                                                 int nE, const float *__restrict__ R,
                                                 const float *__restrict__ sigma, int nc,
@@ -39,10 +39,10 @@ __global__ void __launch_bounds__(256) k_resp_ll(Params p, PlanDev plan,
 {
     __shared__ float As[kTK][kTM + 1];
     __shared__ float Bs[kTK][kTN + 1];
-    __shared__ double red[kTM][17];
+    __shared__ double red[kTM][17];  // [row][column-pair]
     __shared__ float att_nh[kTM];
     const int row0 = blockIdx.y * kTM, col0 = blockIdx.x * kTN;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 2 x 2 outputs per thread
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 2 x 2 outputs per thread (8 x 16 threads)
     if (threadIdx.x < kTM) {
         const int row = row0 + threadIdx.x;
         att_nh[threadIdx.x] =
@@ -52,14 +52,14 @@ __global__ void __launch_bounds__(256) k_resp_ll(Params p, PlanDev plan,
     __syncthreads();
     float acc[2][2] = {};
     for (int k0 = 0; k0 < nE; k0 += kTK) {
-        for (int i = threadIdx.x; i < kTM * kTK; i += 256) {
+        for (int i = threadIdx.x; i < kTM * kTK; i += kThreads) {
             const int rr = i / kTK, kk = i - rr * kTK;
             const int row = row0 + rr, k = k0 + kk;
             As[kk][rr] = (row < total_rows && k < nE)
                              ? Ft[(size_t)row * nE + k] * expf(-att_nh[rr] * sigma[k])
                              : 0.0f;
         }
-        for (int i = threadIdx.x; i < kTK * kTN; i += 256) {
+        for (int i = threadIdx.x; i < kTK * kTN; i += kThreads) {
             const int kk = i / kTN, cc = i - kk * kTN;
             const int k = k0 + kk, c = col0 + cc;
             Bs[kk][cc] = (k < nE && c < nc) ? R[(size_t)k * nc + c] : 0.0f;
@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(256) k_resp_ll(Params p, PlanDev plan,
                 if (lam <= 0.0) {
                     if (d > 0) s += -INFINITY;
                 } else {
-                    s += (d > 0 ? (double)d * log(lam) : 0.0) - lam - log_factorial(d, lfact);
+                    // lambda carries the FP32 rounding of C; ln(lambda) in FP32 adds less
+                    const double ll = d > 0 ? (double)d * (double)logf((float)lam) : 0.0;
+                    s += ll - lam - log_factorial(d, lfact);
                 }
             }
         }
@@ -142,7 +144,7 @@ cudaError_t launch_loglike(const Params &p, const PlanDev &plan, const float *Ft
 {
     const int ct = loglike_ctiles(nc);
     dim3 grid(ct, (total_rows + kTM - 1) / kTM);
-    k_resp_ll<<<grid, 256, 0, st>>>(p, plan, Ft, total_rows, nE, R, sigma, nc, counts,
+    k_resp_ll<<<grid, kThreads, 0, st>>>(p, plan, Ft, total_rows, nE, R, sigma, nc, counts,
                                     counts_shared, bkg, tau, status, lfact, row_ll, model_counts);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

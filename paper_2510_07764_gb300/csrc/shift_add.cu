@@ -182,6 +182,129 @@ __device__ __noinline__ PairW pair_weights_slow(float s, float phi_out, const fl
     return pair_weights(true, s, phi_out, ph, mun, n_fp, top, A, inv_dlnE);
 }
 
+// dot product of a mu stencil row with its weights (four consecutive words)
+__device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, float w1, float w2,
+                                      float w3)
+{
+    return fmaf(w3, q[3], fmaf(w2, q[2], fmaf(w1, q[1], w0 * q[0])));
+}
+
+// component e & 1 of a packed pair
+#define PPM_C(v, e) (((e) & 1) ? (v)[(e) >> 1].y : (v)[(e) >> 1].x)
+
+// One group of 64 NP elements (lanes x 2 NP slots) at one output phase.
+// Slot e of a lane is element g0 + lane + 32 e; slots (2p, 2p+1) are packed
+// into float2 registers so the position update, the Horner evaluation and
+// the slot sum run as paired FP32 instructions (FADD2/FFMA2).  Interval
+// shifts stay per slot: a slot's 32 lanes are neighbouring elements and
+// shift together, so the branch is nearly warp-uniform.
+template <int NP>
+__device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi_out,
+                                          const float *sel, const float *ph, const float *mun,
+                                          const float *slab, int Pm, int n_fp, int top,
+                                          const AtmDev &A, float inv_dlnE, const float *spk,
+                                          int nch, bool sliding, float pk0, float pkl,
+                                          float lz_safe, float *frow)
+{
+    constexpr int NS = 2 * NP;
+    float2 w0[NP], w1[NP], w2[NP], w3[NP], c0[NP], c1[NP], c2[NP], c3[NP], W2[NP], W3[NP], off[NP];
+    const float *sp[NS];
+    bool slow[NS];
+    const float nEm2 = (float)(A.nE - 2);
+#pragma unroll
+    for (int e = 0; e < NS; ++e) {
+        const int m = g0 + lane + 32 * e;
+        const PairW P = pair_weights(m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, ph, mun,
+                                     n_fp, top, A, inv_dlnE);
+        const bool fast = P.on && sliding && (pk0 + P.lz >= 1.0f) && (pkl + P.lz < nEm2);
+        slow[e] = P.on && !fast;
+        // lanes outside the sliding window run it with zero weights
+        const float lz = fast ? P.lz : lz_safe;
+        const float q = floorf(pk0 + lz);
+        const float a0 = fast ? P.w0 : 0.0f, a1 = fast ? P.w1 : 0.0f;
+        const float a2 = fast ? P.w2 : 0.0f, a3 = fast ? P.w3 : 0.0f;
+        PPM_C(w0, e) = a0; PPM_C(w1, e) = a1; PPM_C(w2, e) = a2; PPM_C(w3, e) = a3;
+        PPM_C(off, e) = lz - q;
+        sp[e] = slab + ((int)q + 2) * Pm + P.s0;
+        const float na = dot4(sp[e] - 3 * Pm, a0, a1, a2, a3);
+        const float nb = dot4(sp[e] - 2 * Pm, a0, a1, a2, a3);
+        const float nc = dot4(sp[e] - Pm, a0, a1, a2, a3);
+        const float nd = dot4(sp[e], a0, a1, a2, a3);
+        PPM_C(c0, e) = nb;
+        PPM_C(c2, e) = fmaf(0.5f, na + nc, -nb);
+        PPM_C(c3, e) = fmaf(nd - na, 1.0f / 6.0f, 0.5f * (nb - nc));
+        PPM_C(c1, e) = fmaf(nc - na, 0.5f, -PPM_C(c3, e));
+        PPM_C(W2, e) = nc;
+        PPM_C(W3, e) = nd;
+    }
+    bool anyslow = false;
+#pragma unroll
+    for (int e = 0; e < NS; ++e) anyslow |= slow[e];
+    anyslow = __any_sync(kFull, anyslow);
+
+    for (int c = 0; c < nch; ++c) {
+        float acc[kEC];
+        const float *pkc = spk + c * kEC;
+#pragma unroll
+        for (int s = 0; s < kEC; ++s) acc[s] = 0.0f;
+        // the window walk is only in bounds when the host enabled sliding
+        if (sliding) {
+#pragma unroll
+        for (int s = 0; s < kEC; ++s) {
+            const float pk = pkc[s];
+            float2 t[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) t[p] = __fadd2_rn(make_float2(pk, pk), off[p]);
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+                if (PPM_C(t, e) >= 1.0f) {
+                    sp[e] += Pm;
+                    const float d = dot4(sp[e], PPM_C(w0, e), PPM_C(w1, e), PPM_C(w2, e),
+                                         PPM_C(w3, e));
+                    const float a = PPM_C(c0, e), b = PPM_C(W2, e), cc = PPM_C(W3, e);
+                    PPM_C(c0, e) = b;
+                    PPM_C(c2, e) = fmaf(0.5f, a + cc, -b);
+                    const float k3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (b - cc));
+                    PPM_C(c3, e) = k3;
+                    PPM_C(c1, e) = fmaf(cc - a, 0.5f, -k3);
+                    PPM_C(W2, e) = cc;
+                    PPM_C(W3, e) = d;
+                    PPM_C(off, e) -= 1.0f;
+                    PPM_C(t, e) -= 1.0f;
+                }
+            }
+            float2 v[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                v[p] = __ffma2_rn(t[p], __ffma2_rn(t[p], __ffma2_rn(t[p], c3[p], c2[p]), c1[p]),
+                                  c0[p]);
+            if (NP == 2) {
+                const float2 u = __fadd2_rn(v[0], v[NP - 1]);
+                acc[s] = u.x + u.y;
+            } else {
+                acc[s] = v[0].x + v[0].y;
+            }
+        }
+        }
+        if (anyslow) {
+#pragma unroll
+            for (int e = 0; e < NS; ++e) {
+                if (slow[e]) {
+                    const int m = g0 + lane + 32 * e;
+                    const PairW P =
+                        pair_weights_slow(sel[m], phi_out, ph, mun, n_fp, top, A, inv_dlnE);
+#pragma unroll
+                    for (int k = 0; k < kEC; ++k)
+                        acc[k] += eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz);
+                }
+            }
+        }
+        const float tot = transpose_reduce16(acc, lane);
+        if (lane < kEC) frow[c * kEC + lane] += tot;
+    }
+}
+#undef PPM_C
+
 template <int EMIS>
 __global__ void __launch_bounds__(kSABlock, 2)
     k_shift_add(Params p, PlanDev plan, AtmDev A, EnergyDev en, Layout lay,
@@ -269,89 +392,28 @@ __global__ void __launch_bounds__(kSABlock, 2)
         const float *mun = sm + lay.munodes;
         const float pk0 = spk[0], pkl = spk[en.nE - 1];
         const float lz_safe = 1.25f - pk0;
+        const bool sliding = en.sliding != 0;
 
         for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
             const float phi_out = (float)(it.j0 + jl) * inv_nphase;
+            if (EMIS == 1) {
+                for (int g0 = 0; g0 < n_act;) {
+                    if (n_act - g0 > 64) {
+                        atm_group<2>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
+                                     A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
+                                     Fblk + jl * nEpad);
+                        g0 += 128;
+                    } else {
+                        atm_group<1>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
+                                     A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
+                                     Fblk + jl * nEpad);
+                        g0 += 64;
+                    }
+                }
+                continue;
+            }
             for (int g0 = 0; g0 < n_act; g0 += 128) {
-                if (EMIS == 1) {
-                    El E[4];
-                    bool slow[4], anyslow[4], anyon[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int m = g0 + lane + 32 * e;
-                        const PairW P = pair_weights(m < n_act, m < n_act ? sel[m] : 0.0f,
-                                                     phi_out, ph, mun, n_fp, top, A, inv_dlnE);
-                        const bool fast = P.on && en.sliding && (pk0 + P.lz >= 1.0f) &&
-                                          (pkl + P.lz < (float)(A.nE - 2));
-                        slow[e] = P.on && !fast;
-                        anyslow[e] = __any_sync(kFull, slow[e]);
-                        anyon[e] = __any_sync(kFull, fast);
-                        // lanes outside the sliding window run it with zero weights
-                        const float lz = fast ? P.lz : lz_safe;
-                        E[e].w0 = fast ? P.w0 : 0.0f;
-                        E[e].w1 = fast ? P.w1 : 0.0f;
-                        E[e].w2 = fast ? P.w2 : 0.0f;
-                        E[e].w3 = fast ? P.w3 : 0.0f;
-                        const float q = floorf(pk0 + lz);
-                        E[e].off = lz - q;
-                        E[e].nb = ((int)q + 2) * Pm + P.s0;
-                        if (anyon[e]) {
-                            const float a = contract4(slab, E[e].nb - 3 * Pm, E[e].w0, E[e].w1,
-                                                      E[e].w2, E[e].w3);
-                            const float b = contract4(slab, E[e].nb - 2 * Pm, E[e].w0, E[e].w1,
-                                                      E[e].w2, E[e].w3);
-                            const float c = contract4(slab, E[e].nb - Pm, E[e].w0, E[e].w1,
-                                                      E[e].w2, E[e].w3);
-                            const float d = contract4(slab, E[e].nb, E[e].w0, E[e].w1, E[e].w2,
-                                                      E[e].w3);
-                            cubic_coeffs(a, b, c, d, E[e]);
-                        } else {
-                            E[e].c0 = E[e].c1 = E[e].c2 = E[e].c3 = 0.0f;
-                            E[e].W2 = E[e].W3 = 0.0f;
-                        }
-                    }
-                    for (int c = 0; c < nch; ++c) {
-                        float acc[kEC];
-                        const float *pkc = spk + c * kEC;
-#pragma unroll
-                        for (int s = 0; s < kEC; ++s) {
-                            const float pk = pkc[s];
-                            float t[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) t[e] = pk + E[e].off;
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                if (anyon[e] && t[e] >= 1.0f) {
-                                    E[e].nb += Pm;
-                                    const float d = contract4(slab, E[e].nb, E[e].w0, E[e].w1,
-                                                              E[e].w2, E[e].w3);
-                                    cubic_coeffs(E[e].c0, E[e].W2, E[e].W3, d, E[e]);
-                                    E[e].off -= 1.0f;
-                                    t[e] -= 1.0f;
-                                }
-                            }
-                            float v[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                v[e] = fmaf(t[e], fmaf(t[e], fmaf(t[e], E[e].c3, E[e].c2), E[e].c1),
-                                            E[e].c0);
-                            acc[s] = (v[0] + v[1]) + (v[2] + v[3]);
-                        }
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (anyslow[e] && slow[e]) {
-                                const int m = g0 + lane + 32 * e;
-                                const PairW P = pair_weights_slow(sel[m], phi_out, ph, mun, n_fp,
-                                                                  top, A, inv_dlnE);
-#pragma unroll
-                                for (int k = 0; k < kEC; ++k)
-                                    acc[k] += eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz);
-                            }
-                        }
-                        const float tot = transpose_reduce16(acc, lane);
-                        if (lane < kEC) Fblk[jl * nEpad + c * kEC + lane] += tot;
-                    }
-                } else {
+                {
                     // analytic isotropic blackbody: I(z E) = K z^3 E^3 / expm1(z E / kT); the
                     // 1/E of Eq. add_Ft is applied with the flux scale in the reduction
                     const float K = (float)(2.0 / (kH_KEVS * kH_KEVS * kH_KEVS * kC_CM * kC_CM));
