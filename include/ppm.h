@@ -172,6 +172,33 @@ ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
                        float *Ft, int *inst_status, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free forward profile.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate GPU memory at evaluation
+ * time -- for example a sampler that has already handed the rest of the
+ * device memory to its own pool, or one that cannot afford the
+ * device-wide synchronisation that cudaMalloc/cudaFree imply while other
+ * work is in flight.  It computes exactly what ppm_profile computes (same
+ * kernels, same arguments and layouts) but takes every per-call buffer from
+ * a fixed 64 MiB array in the library's device memory, which every GPU that
+ * loads the library holds until the process exits, and builds its plan in a
+ * fixed host buffer: it calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The context's tables must already be set by the usual setters.
+ *
+ * - Problems whose per-call buffers exceed 64 MiB (after widening ring
+ *   groups) or whose plan exceeds 1 MiB of host staging return PPM_EINVAL
+ *   with a message; nothing is enqueued.  (The default two-spot 128x128
+ *   workload with 128 phases and 256 energies fits.)
+ * - The first call on a device looks up the array's device address on that
+ *   device; make that first call before any stream capture.
+ * - All calls in the process share the one array per device, which keeps the
+ *   previous call's contents (the status words are cleared at every call).
+ *   Calls that overlap on the GPU -- two streams, two contexts on one device,
+ *   or two host threads -- race on it; serialise them.
+ * ------------------------------------------------------------------------ */
+ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                               float *Ft, int *inst_status, void *stream);
+
+/* ------------------------------------------------------------------------
  * Poisson log-likelihood (Sect. 2.7, 2.8.4; the paper states the likelihood
  * only through -2 Delta ln L ~ chi^2, Eq. chi2_def context, and its GPU-side
  * accumulation in Sect. 6): the profile of ppm_profile, attenuated,

@@ -19,7 +19,8 @@ STATUS_NAMES = ["PPM_OK", "PPM_EINVAL", "PPM_ERANGE", "PPM_ENOMEM", "PPM_ECUDA",
 # every entry point declared in include/ppm.h
 EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm_get_lens",
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
-           "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing"]
+           "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
+           "ppm_profile_noalloc"]
 
 
 class ppm_lens_spec(C.Structure):
@@ -75,6 +76,7 @@ def lib() -> C.CDLL:
         "ppm_set_energies": (i, [vp, vp, i]),
         "ppm_set_response": (i, [vp, vp, i, i, vp]),
         "ppm_profile": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
+        "ppm_profile_noalloc": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
         "ppm_loglike": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d, vp, vp,
                             vp, vp]),
         "ppm_sync": (i, [vp, vp, d]),
@@ -126,6 +128,10 @@ def ppm_set_response(ctx, R, nE, nc, sigma) -> int:
 
 def ppm_profile(ctx, params: ppm_params, res: ppm_res, Ft, inst_status, stream) -> int:
     return lib().ppm_profile(ctx, C.byref(params), C.byref(res), Ft, inst_status, stream)
+
+
+def ppm_profile_noalloc(ctx, params: ppm_params, res: ppm_res, Ft, inst_status, stream) -> int:
+    return lib().ppm_profile_noalloc(ctx, C.byref(params), C.byref(res), Ft, inst_status, stream)
 
 
 def ppm_loglike(ctx, params: ppm_params, res: ppm_res, counts, counts_shared, bkg, tau, logL,

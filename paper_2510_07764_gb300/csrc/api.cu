@@ -750,3 +750,226 @@ ppm_status ppm_sync(ppm_ctx *ctx, void *stream, double timeout_s)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward profile.
+//
+// Every per-call buffer of ppm_profile (plan, energy arrays, status, ring
+// records, templates, element lists, partial sums) is carved out of one
+// file-scope device array of fixed size instead of the context's growable
+// workspace, and the host-side plan is assembled in a fixed static host
+// buffer, so the call allocates neither device nor host memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocDeviceBytes = size_t(64) << 20;  // per device, held until exit
+constexpr size_t kNoAllocHostBytes = size_t(1) << 20;     // host staging of plan + energies
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocDeviceBytes];
+
+alignas(256) unsigned char g_noalloc_host[kNoAllocHostBytes];
+void *g_noalloc_dev[kNoAllocMaxDevices];   // device address of the array, per device
+
+// Sizes of one allocation-free plan (no containers: counts only).
+struct NoAllocPlan {
+    int pt, g, n_items, n_tiles, total_rings, total_rows, n_phi_max, nEpad;
+    size_t total_elems;
+    size_t o_inst, o_items, o_tiles, host_bytes;        // host staging layout
+    size_t o_E, o_E3, o_pk, o_invE;                     // (also mirrored on the device)
+    size_t o_status, o_recs, o_tmpl, o_elems, o_part, device_bytes;
+};
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void noalloc_sizes(const ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, int pt, int g,
+                   NoAllocPlan *L)
+{
+    L->pt = pt;
+    L->g = g;
+    L->n_items = L->n_tiles = L->total_rings = L->total_rows = L->n_phi_max = 0;
+    L->total_elems = 0;
+    for (int b = 0; b < p->B; ++b) {
+        const int tiles = (res->n_phase[b] + pt - 1) / pt;
+        const int gb = std::min(g, res->n_theta[b]);
+        const int groups = (res->n_theta[b] + gb - 1) / gb;
+        L->n_tiles += tiles;
+        L->n_items += tiles * p->n_spots * groups;
+        L->total_rings += p->n_spots * res->n_theta[b];
+        L->total_rows += res->n_phase[b];
+        L->total_elems += (size_t)p->n_spots * res->n_theta[b] * res->n_phi[b];
+        L->n_phi_max = std::max(L->n_phi_max, res->n_phi[b]);
+    }
+    const int nE = (int)ctx->E.size();
+    L->nEpad = (nE + kEC - 1) / kEC * kEC;
+    size_t o = 0;
+    L->o_inst = o; o += a256((size_t)p->B * sizeof(InstPlan));
+    L->o_items = o; o += a256((size_t)L->n_items * sizeof(Item));
+    L->o_tiles = o; o += a256((size_t)L->n_tiles * sizeof(int2));
+    L->o_E = o; o += a256((size_t)L->nEpad * sizeof(float));
+    L->o_E3 = o; o += a256((size_t)L->nEpad * sizeof(float));
+    L->o_pk = o; o += a256((size_t)L->nEpad * sizeof(float));
+    L->o_invE = o; o += a256((size_t)L->nEpad * sizeof(float));
+    L->host_bytes = o;
+    L->o_status = o; o += a256((size_t)p->B * sizeof(int));
+    L->o_recs = o; o += a256((size_t)L->total_rings * sizeof(RingRec));
+    L->o_tmpl = o; o += a256((size_t)L->total_rings * 4 * (res->n_fp + 1) * sizeof(float));
+    L->o_elems = o; o += a256(L->total_elems * sizeof(float));
+    L->o_part = o; o += a256((size_t)L->n_items * pt * L->nEpad * sizeof(float));
+    L->device_bytes = o;
+}
+
+}  // namespace
+
+extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                                          float *Ft, int *inst_status, void *stream)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (!Ft) return fail(ctx, PPM_EINVAL, "null Ft");
+    ppm_status s = check_params(ctx, p, res);
+    if (s != PPM_OK) return s;
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return fail(ctx, PPM_EINVAL, "device index beyond %d", kNoAllocMaxDevices);
+    DeviceGuard guard(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // one-time set-up on this device (the current device is ctx->device here)
+    if (!g_noalloc_dev[ctx->device]) {
+        void *ptr = nullptr;
+        PPM_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "scratch symbol address");
+        g_noalloc_dev[ctx->device] = ptr;
+    }
+    unsigned char *dev = static_cast<unsigned char *>(g_noalloc_dev[ctx->device]);
+
+    // plan: the ppm_profile heuristics, with ring groups widened until the
+    // per-call buffers fit the fixed device array
+    long long T32 = 0;
+    int max_theta = 1;
+    for (int b = 0; b < p->B; ++b) {
+        T32 += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + kPT - 1) / kPT);
+        max_theta = std::max(max_theta, res->n_theta[b]);
+    }
+    const int pt = T32 < (long long)ctx->sm_count * 16 ? 16 : kPT;
+    long long T = 0;
+    for (int b = 0; b < p->B; ++b)
+        T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + pt - 1) / pt);
+    int g = (int)std::max<long long>(1, T / std::max<long long>((long long)ctx->sm_count * 12, 1));
+    NoAllocPlan L;
+    for (;;) {
+        noalloc_sizes(ctx, p, res, pt, g, &L);
+        if (L.device_bytes <= kNoAllocDeviceBytes || g >= max_theta) break;
+        g = std::min(2 * g, max_theta);
+    }
+    if (L.device_bytes > kNoAllocDeviceBytes)
+        return fail(ctx, PPM_EINVAL,
+                    "problem needs %zu bytes of scratch; ppm_profile_noalloc is limited to %zu",
+                    L.device_bytes, kNoAllocDeviceBytes);
+    if (L.host_bytes > kNoAllocHostBytes)
+        return fail(ctx, PPM_EINVAL, "plan needs %zu bytes of host staging; limit %zu",
+                    L.host_bytes, kNoAllocHostBytes);
+
+    // host staging: instance table, items, tile ranges, energy arrays
+    unsigned char *h = g_noalloc_host;
+    InstPlan *hi = reinterpret_cast<InstPlan *>(h + L.o_inst);
+    Item *hit = reinterpret_cast<Item *>(h + L.o_items);
+    int2 *ht = reinterpret_cast<int2 *>(h + L.o_tiles);
+    int rings = 0, rows = 0, items = 0, tiles = 0;
+    size_t elems = 0;
+    for (int b = 0; b < p->B; ++b) {
+        InstPlan &ip = hi[b];
+        ip.n_theta = res->n_theta[b];
+        ip.n_phi = res->n_phi[b];
+        ip.n_phase = res->n_phase[b];
+        ip.ring0 = rings;
+        ip.elem0 = (int)elems;
+        ip.row0 = rows;
+        ip.tiles = (ip.n_phase + pt - 1) / pt;
+        ip.tile0 = tiles;
+        rings += p->n_spots * ip.n_theta;
+        elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
+        rows += ip.n_phase;
+        const int gb = std::min(L.g, ip.n_theta);
+        for (int t = 0; t < ip.tiles; ++t) {
+            const int begin = items;
+            for (int sp = 0; sp < p->n_spots; ++sp)
+                for (int r0 = 0; r0 < ip.n_theta; r0 += gb) {
+                    Item &it = hit[items++];
+                    it.b = b; it.spot = sp; it.r0 = r0; it.r1 = std::min(r0 + gb, ip.n_theta);
+                    it.j0 = t * pt; it.nj = std::min(pt, ip.n_phase - t * pt);
+                }
+            ht[tiles++] = make_int2(begin, items);
+        }
+    }
+    if (elems > (size_t)INT32_MAX) return fail(ctx, PPM_EINVAL, "problem too large");
+    const int nE = (int)ctx->E.size();
+    float *hE = reinterpret_cast<float *>(h + L.o_E), *hE3 = reinterpret_cast<float *>(h + L.o_E3);
+    float *hpk = reinterpret_cast<float *>(h + L.o_pk);
+    float *hinv = reinterpret_cast<float *>(h + L.o_invE);
+    for (int k = 0; k < L.nEpad; ++k) {
+        const double e = ctx->E[std::min(k, nE - 1)];
+        hE[k] = (float)e;
+        hE3[k] = (float)(e * e * e);
+        hinv[k] = (float)(1.0 / e);
+        hpk[k] = ctx->atm_ready ? (float)((std::log(e) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
+    }
+    int sliding = ctx->atm_ready ? 1 : 0;
+    if (sliding) {
+        for (int k = 0; k + 1 < nE; ++k)
+            if (!((double)hpk[k + 1] - hpk[k] < 0.999)) sliding = 0;
+        if (!((double)hpk[nE - 1] - hpk[0] < ctx->nEt - 3.5)) sliding = 0;
+    }
+
+    Params P;
+    P.B = p->B; P.n_spots = p->n_spots; P.oblate = p->oblate; P.emission = p->emission;
+    P.mass_msun = p->mass_msun; P.radius_km = p->radius_km; P.spin_hz = p->spin_hz;
+    P.incl_rad = p->incl_rad; P.dist_kpc = p->dist_kpc; P.nh_1e20 = p->nh_1e20;
+    P.colat = p->colat; P.azim = p->azim; P.zeta = p->zeta; P.logT = p->logT;
+    P.mask_colat = p->mask_colat; P.mask_azim = p->mask_azim; P.mask_zeta = p->mask_zeta;
+    PlanDev plan;
+    plan.B = p->B; plan.n_fp = res->n_fp; plan.n_items = L.n_items;
+    plan.total_rings = L.total_rings; plan.pt = L.pt;
+    plan.inst = reinterpret_cast<const InstPlan *>(dev + L.o_inst);
+    plan.items = reinterpret_cast<const Item *>(dev + L.o_items);
+    plan.tile_items = reinterpret_cast<const int2 *>(dev + L.o_tiles);
+    const ppm_lens_spec &ls = ctx->lens;
+    LensDev Ld;
+    Ld.u_min = ls.u_min; Ld.u_max = ls.u_max; Ld.n_u = ls.n_u;
+    Ld.cpsi_min = ls.cpsi_min; Ld.cpsi_max = ls.cpsi_max; Ld.n_cpsi = ls.n_cpsi;
+    Ld.ca_min = ls.calpha_min; Ld.ca_max = ls.calpha_max; Ld.n_calpha = ls.n_calpha;
+    Ld.Ca = ctx->d_Ca.as<double>(); Ld.LF = ctx->d_LF.as<double>(); Ld.TD = ctx->d_TD.as<double>();
+    AtmDev A;
+    A.nT = ctx->nT; A.ng = ctx->ng; A.nmu = ctx->nmu; A.nE = ctx->nEt;
+    A.n_protect = ctx->n_protect; A.nmu_pad = ctx->nmu_pad;
+    A.I = ctx->d_I.as<float>(); A.logT = ctx->d_logT.as<double>();
+    A.logg = ctx->d_logg.as<double>(); A.mu = ctx->d_mu.as<float>();
+    A.lnE0 = ctx->lnE0_t; A.dlnE = ctx->dlnE_t;
+    EnergyDev en;
+    en.nE = nE; en.nEpad = L.nEpad; en.sliding = sliding;
+    en.E = reinterpret_cast<const float *>(dev + L.o_E);
+    en.E3 = reinterpret_cast<const float *>(dev + L.o_E3);
+    en.pk = reinterpret_cast<const float *>(dev + L.o_pk);
+    en.invE = reinterpret_cast<const float *>(dev + L.o_invE);
+    const size_t smem_need = shift_add_smem_bytes(P, plan, A, en, L.n_phi_max);
+    if (smem_need > ctx->smem_optin)
+        return fail(ctx, PPM_EINVAL, "shared memory need %zu B exceeds %zu B", smem_need,
+                    ctx->smem_optin);
+    int *status = reinterpret_cast<int *>(dev + L.o_status);
+    RingRec *recs = reinterpret_cast<RingRec *>(dev + L.o_recs);
+    float *tmpl = reinterpret_cast<float *>(dev + L.o_tmpl);
+    float *el = reinterpret_cast<float *>(dev + L.o_elems);
+    float *part = reinterpret_cast<float *>(dev + L.o_part);
+    // pageable source: the copy has consumed the staging buffer when it returns
+    PPM_CUDA(cudaMemcpyAsync(dev, h, L.host_bytes, cudaMemcpyHostToDevice, st), "upload plan");
+    // the array keeps the previous call's contents: status must start at zero
+    PPM_CUDA(cudaMemsetAsync(dev + L.o_status, 0, sizeof(int) * p->B, st), "clear status");
+    PPM_CUDA(launch_ring(P, plan, Ld, A, recs, tmpl, el, status, ctx->d_err, nullptr, nE, st),
+             "ring kernel");
+    PPM_CUDA(launch_shift_add(P, plan, A, en, recs, tmpl, el, status, part, L.n_phi_max, st),
+             "shift-and-add kernel");
+    PPM_CUDA(launch_reduce(plan, en, part, status, L.total_rows, Ft, st), "reduce kernel");
+    if (inst_status)
+        PPM_CUDA(cudaMemcpyAsync(inst_status, status, sizeof(int) * p->B,
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy status");
+    ctx->err.clear();
+    return PPM_OK;
+}
