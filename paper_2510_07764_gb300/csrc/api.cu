@@ -44,6 +44,7 @@ struct HostPlan {
     std::vector<InstPlan> inst;
     std::vector<Item> items;
     std::vector<int2> tiles;
+    std::vector<int> order;
     int total_rings = 0, total_rows = 0, n_phi_max = 0;
     size_t total_elems = 0;
 };
@@ -431,6 +432,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(p->n_spots);
     key.push_back(res->n_fp);
     key.push_back(ctx->sm_count);
+    key.push_back((int)ctx->E.size());
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -447,15 +449,20 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
             T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + pt - 1) / pt);
         return T;
     };
-    const long long D = (long long)ctx->sm_count * 12;
     int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
     if (const char *env = getenv("PPM_PHASE_TILE")) {
         const int v = atoi(env);
         if (v == 16 || v == 32) pt = v;
     }
     hp.pt = pt;
-    const long long T = ring_tiles(pt);
-    const int g = (int)std::max<long long>(1, T / std::max<long long>(D, 1));
+    // ring groups sized by work (elements x phases x energies), aiming at
+    // ~16 waves of 2 blocks per SM; instances of very different resolution
+    // then give items of comparable cost
+    const double nE = (double)ctx->E.size();
+    double total = 0.0;
+    for (int b = 0; b < B; ++b)
+        total += (double)p->n_spots * res->n_theta[b] * res->n_phi[b] * res->n_phase[b] * nE;
+    const double target = std::max(1.0, total / ((double)ctx->sm_count * 2.0 * 16.0));
     hp.inst.resize(B);
     for (int b = 0; b < B; ++b) {
         InstPlan &ip = hp.inst[b];
@@ -471,7 +478,8 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         hp.total_elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
         hp.total_rows += ip.n_phase;
         hp.n_phi_max = std::max(hp.n_phi_max, ip.n_phi);
-        const int gb = std::min(g, ip.n_theta);
+        const double ring_cost = (double)ip.n_phi * std::min(pt, ip.n_phase) * nE;
+        const int gb = (int)std::min<double>(ip.n_theta, std::max(1.0, std::floor(target / ring_cost)));
         for (int t = 0; t < ip.tiles; ++t) {
             const int begin = (int)hp.items.size();
             for (int s = 0; s < p->n_spots; ++s)
@@ -485,10 +493,22 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         }
     }
     if (hp.total_elems > (size_t)INT32_MAX) return fail(ctx, PPM_EINVAL, "problem too large");
+    // launch order: largest items first (longest-processing-time heuristic)
+    hp.order.resize(hp.items.size());
+    {
+        std::vector<std::pair<double, int>> c(hp.items.size());
+        for (size_t i = 0; i < hp.items.size(); ++i) {
+            const Item &it = hp.items[i];
+            c[i] = {-(double)(it.r1 - it.r0) * hp.inst[it.b].n_phi * it.nj, (int)i};
+        }
+        std::stable_sort(c.begin(), c.end());
+        for (size_t i = 0; i < c.size(); ++i) hp.order[i] = c[i].second;
+    }
     const size_t b_inst = align256(hp.inst.size() * sizeof(InstPlan));
     const size_t b_items = align256(hp.items.size() * sizeof(Item));
     const size_t b_tiles = align256(hp.tiles.size() * sizeof(int2));
-    const size_t bytes = b_inst + b_items + b_tiles;
+    const size_t b_order = align256(hp.order.size() * sizeof(int));
+    const size_t bytes = b_inst + b_items + b_tiles + b_order;
     // the pinned staging buffer may still feed the previous upload
     PPM_CUDA(cudaEventSynchronize(ctx->plan_ev), "plan event");
     if (ctx->h_pinned_n < bytes) {
@@ -502,6 +522,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     memcpy(h, hp.inst.data(), hp.inst.size() * sizeof(InstPlan));
     memcpy(h + b_inst, hp.items.data(), hp.items.size() * sizeof(Item));
     memcpy(h + b_inst + b_items, hp.tiles.data(), hp.tiles.size() * sizeof(int2));
+    memcpy(h + b_inst + b_items + b_tiles, hp.order.data(), hp.order.size() * sizeof(int));
     if (ctx->d_plan.n < bytes) {
         PPM_CUDA(cudaDeviceSynchronize(), "sync");
         PPM_CUDA(ctx->d_plan.ensure(bytes), "alloc plan");
@@ -568,6 +589,8 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     plan->inst = reinterpret_cast<const InstPlan *>(d);
     plan->items = reinterpret_cast<const Item *>(d + b_inst);
     plan->tile_items = reinterpret_cast<const int2 *>(d + b_inst + b_items);
+    plan->order = reinterpret_cast<const int *>(
+        d + b_inst + b_items + align256(hp.tiles.size() * sizeof(int2)));
     const ppm_lens_spec &s = ctx->lens;
     L->u_min = s.u_min; L->u_max = s.u_max; L->n_u = s.n_u;
     L->cpsi_min = s.cpsi_min; L->cpsi_max = s.cpsi_max; L->n_cpsi = s.n_cpsi;
@@ -930,6 +953,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     plan.inst = reinterpret_cast<const InstPlan *>(dev + L.o_inst);
     plan.items = reinterpret_cast<const Item *>(dev + L.o_items);
     plan.tile_items = reinterpret_cast<const int2 *>(dev + L.o_tiles);
+    plan.order = nullptr;
     const ppm_lens_spec &ls = ctx->lens;
     LensDev Ld;
     Ld.u_min = ls.u_min; Ld.u_max = ls.u_max; Ld.n_u = ls.n_u;

@@ -91,6 +91,7 @@ struct PlanDev {
     const InstPlan *inst;
     const Item *items;
     const int2 *tile_items;  // [sum tiles] item range of (instance, tile)
+    const int *order;        // launch order of the items (largest first); null = identity
 };
 
 // Energy-side arrays (device).

@@ -313,7 +313,8 @@ __global__ void __launch_bounds__(kSABlock, 2)
                 float *__restrict__ partials)
 {
     extern __shared__ float sm[];
-    const Item it = plan.items[blockIdx.x];
+    const int item_id = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
+    const Item it = plan.items[item_id];
     const InstPlan ip = plan.inst[it.b];
     const int n_fp = plan.n_fp;
     const int pt = plan.pt;
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
         }
     }
     __syncthreads();
-    float *dst = partials + (size_t)blockIdx.x * pt * nEpad;
+    float *dst = partials + (size_t)item_id * pt * nEpad;
     for (int i = tid; i < it.nj * nEpad; i += blockDim.x) dst[i] = Fblk[i];
 }
 
