@@ -87,7 +87,7 @@ struct ppm_ctx {
     int nEpad = 0, sliding = 0;
     // response
     int nc = 0;
-    DevBuf d_R, d_sigma;
+    DevBuf d_R, d_sigma, d_Rtc;  // d_Rtc: R split into bf16 hi/lo tiles for the tensor cores
     // plan
     std::vector<int> plan_key;
     HostPlan plan;
@@ -215,7 +215,7 @@ void ppm_destroy(ppm_ctx *ctx)
     cudaDeviceSynchronize();
     for (DevBuf *b : {&ctx->d_Ca, &ctx->d_LF, &ctx->d_TD, &ctx->d_I, &ctx->d_logT, &ctx->d_logg,
                       &ctx->d_mu, &ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
-                      &ctx->d_sigma, &ctx->d_plan, &ctx->ws})
+                      &ctx->d_sigma, &ctx->d_Rtc, &ctx->d_plan, &ctx->ws})
         b->release();
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->d_err) cudaFree(ctx->d_err);
@@ -356,6 +356,13 @@ ppm_status ppm_set_response(ppm_ctx *ctx, const float *R, int nE, int nc, const 
     PPM_CUDA(ctx->d_sigma.ensure((size_t)nE * 4), "alloc sigma");
     PPM_CUDA(cudaMemcpy(ctx->d_R.p, R, (size_t)nE * nc * 4, cudaMemcpyHostToDevice), "copy R");
     PPM_CUDA(cudaMemcpy(ctx->d_sigma.p, sigma, (size_t)nE * 4, cudaMemcpyHostToDevice), "copy sigma");
+    {
+        std::vector<uint16_t> tc(resp_tc_layout_elems(nE, nc));
+        resp_tc_layout(R, nE, nc, tc.data());
+        PPM_CUDA(ctx->d_Rtc.ensure(tc.size() * 2), "alloc tensor-core response");
+        PPM_CUDA(cudaMemcpy(ctx->d_Rtc.p, tc.data(), tc.size() * 2, cudaMemcpyHostToDevice),
+                 "copy tensor-core response");
+    }
     ctx->nc = nc;
     return PPM_OK;
 }
@@ -694,12 +701,26 @@ ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, co
     EnergyDev en;
     fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
     {
+        // tensor cores for large row counts (batches); the FP32 tile kernel
+        // has lower latency for a few hundred rows
+        bool use_tc = ctx->plan.total_rows >= 512;
+        if (const char *env = getenv("PPM_RESP_TC")) use_tc = atoi(env) != 0;
         StageTimer t(ctx, 3, st);
-        PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
-                                ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc, counts,
-                                counts_shared, bkg, tau, w.status, ctx->d_lfact, w.row_ll,
-                                model_counts, logL, st),
-                 "likelihood kernels");
+        if (use_tc) {
+            PPM_CUDA(launch_loglike_tc(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
+                                       ctx->d_Rtc.as<uint16_t>(), ctx->d_sigma.as<float>(),
+                                       ctx->nc, counts, counts_shared, bkg, tau, w.status,
+                                       ctx->d_lfact, w.row_ll, model_counts, ctx->d_err, st),
+                     "tensor-core likelihood kernel");
+            launch_ll_final(plan, w.row_ll, resp_tc_ctiles(ctx->nc), w.status, logL, st);
+            PPM_CUDA(cudaGetLastError(), "likelihood reduction");
+        } else {
+            PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
+                                    ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc,
+                                    counts, counts_shared, bkg, tau, w.status, ctx->d_lfact,
+                                    w.row_ll, model_counts, logL, st),
+                     "likelihood kernels");
+        }
         t.done(2);
     }
     if (inst_status)
@@ -766,8 +787,9 @@ ppm_status ppm_sync(ppm_ctx *ctx, void *stream, double timeout_s)
     PPM_CUDA(cudaMemcpy(&bits, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
     if (bits) {
         PPM_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)), "clear error word");
-        return fail(ctx, PPM_ENOTREADY, "device invariant failed (bits 0x%x%s)", bits,
-                    (bits & kErrPhaseOrder) ? ": template observed phases not increasing" : "");
+        return fail(ctx, PPM_ENOTREADY, "device invariant failed (bits 0x%x%s%s)", bits,
+                    (bits & kErrPhaseOrder) ? ": template observed phases not increasing" : "",
+                    (bits & kErrTimeout) ? ": a bounded in-kernel wait timed out" : "");
     }
     return PPM_OK;
 }

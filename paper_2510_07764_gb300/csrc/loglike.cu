@@ -136,6 +136,12 @@ __global__ void k_ll_final(PlanDev plan, const double *__restrict__ row_ll, int 
 
 int loglike_ctiles(int nc) { return (nc + kTN - 1) / kTN; }
 
+void launch_ll_final(const PlanDev &plan, const double *row_ll, int n_ctiles, const int *status,
+                     double *logL, cudaStream_t st)
+{
+    k_ll_final<<<plan.B, 256, 0, st>>>(plan, row_ll, n_ctiles, status, logL);
+}
+
 cudaError_t launch_loglike(const Params &p, const PlanDev &plan, const float *Ft, int total_rows,
                            int nE, const float *R, const float *sigma, int nc,
                            const int *counts, int counts_shared, const float *bkg, double tau,

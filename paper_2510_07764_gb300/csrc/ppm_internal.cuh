@@ -32,6 +32,7 @@ constexpr int kSABlock = 256;
 enum : unsigned {
     kErrPhaseOrder = 1u,  // template observed phases not increasing
     kErrPlan = 2u,        // inconsistent plan (should not happen)
+    kErrTimeout = 4u,     // a bounded wait inside a kernel gave up
 };
 
 struct LensDev {
@@ -131,6 +132,20 @@ cudaError_t launch_loglike(const Params &p, const PlanDev &plan, const float *Ft
                            int nc, const int *counts, int counts_shared, const float *bkg,
                            double tau, const int *status, const double *lfact, double *row_ll,
                            float *model_counts, double *logL, cudaStream_t st);
+
+void launch_ll_final(const PlanDev &plan, const double *row_ll, int n_ctiles, const int *status,
+                     double *logL, cudaStream_t st);
+
+// tensor-core response contraction (resp_tc.cu)
+int resp_tc_ctiles(int nc);
+int resp_tc_kchunks(int nE);
+size_t resp_tc_layout_elems(int nE, int nc);
+void resp_tc_layout(const float *R, int nE, int nc, uint16_t *out);
+cudaError_t launch_loglike_tc(const Params &p, const PlanDev &plan, const float *Ft,
+                              int total_rows, int nE, const uint16_t *Rtc, const float *sigma,
+                              int nc, const int *counts, int counts_shared, const float *bkg,
+                              double tau, const int *status, const double *lfact,
+                              double *row_ll, float *model_counts, unsigned *err, cudaStream_t st);
 
 // row -> instance lookup (binary search over InstPlan.row0)
 __device__ __forceinline__ int find_instance_by_row(const InstPlan *ip, int B, int row)

@@ -128,27 +128,6 @@ __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, c
     return P;
 }
 
-// Sliding-interval state of one element in the fast loop.  The cubic of the
-// current interval q is c0 + c1 t + c2 t^2 + c3 t^3 with t = pk + off, off =
-// lz - q; nb addresses node q+2 (row) + stencil start.  W2, W3 keep nodes
-// q+1 and q+2 (c0 is node q).
-struct El {
-    float w0, w1, w2, w3;
-    int nb;
-    float off, c0, c1, c2, c3, W2, W3;
-};
-
-// cubic through (-1, a), (0, b), (1, c), (2, d) in power basis
-__device__ __forceinline__ void cubic_coeffs(float a, float b, float c, float d, El &E)
-{
-    E.c0 = b;
-    E.c2 = fmaf(0.5f, a + c, -b);
-    E.c3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (b - c));
-    E.c1 = fmaf(c - a, 0.5f, -E.c3);
-    E.W2 = c;
-    E.W3 = d;
-}
-
 // general evaluation (table edges / clamping) of the contracted spectrum at p
 __device__ __noinline__ float eval_general(const PairW &P, const float *slab, int Pm, int nE_t,
                                            float p)
@@ -397,7 +376,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
 
         for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
             const float phi_out = (float)(it.j0 + jl) * inv_nphase;
-            if (EMIS == 1) {
+            if constexpr (EMIS == 1) {
                 for (int g0 = 0; g0 < n_act;) {
                     if (n_act - g0 > 64) {
                         atm_group<2>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
@@ -412,7 +391,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
                     }
                 }
                 continue;
-            }
+            } else {
             for (int g0 = 0; g0 < n_act; g0 += 128) {
                 {
                     // analytic isotropic blackbody: I(z E) = K z^3 E^3 / expm1(z E / kT); the
@@ -455,6 +434,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
                         if (lane < kEC) Fblk[jl * nEpad + c * kEC + lane] += tot;
                     }
                 }
+            }
             }
         }
     }

@@ -89,3 +89,45 @@ def test_zero_model_with_counts_is_minus_inf(synth, atm, small_lens):
     assert ll[0] == -np.inf
     ll0, _, _ = gpu_loglike(w, counts=np.zeros_like(w.counts))
     assert ll0[0] == 0.0
+
+
+def _with_env(key, val, fn):
+    import os
+    old = os.environ.get(key)
+    os.environ[key] = val
+    try:
+        return fn()
+    finally:
+        if old is None:
+            del os.environ[key]
+        else:
+            os.environ[key] = old
+
+
+def test_tensor_core_response_matches_oracle(orc, synth, atm, small_lens):
+    """The tcgen05 response contraction (BF16 hi/lo split, FP32 accumulation)
+    against the oracle, on a ragged shape (100 rows, 300 channels, 200 energies)."""
+    w = synth.atm_two_spot(n_theta=12, n_phi=24, n_phase=100, n_E=200, n_chan=300, atm=atm,
+                           lens=small_lens)
+    ll, mc, st = _with_env("PPM_RESP_TC", "1", lambda: gpu_loglike(w))
+    llr, C = _oracle_ll(orc, w)
+    assert st[0] == 0
+    assert max_rel(mc, w.tau * C) < 1e-3
+    assert abs(ll[0] - llr) <= _ll_tol(w, C, w.counts)
+
+
+def test_tensor_core_and_fp32_paths_agree_on_a_batch(synth, atm, small_lens):
+    """A batch of 24 instances x 32 phases (768 rows: the tensor-core path by
+    default) against the FP32 tile path on the same profile."""
+    w = synth.atm_two_spot(n_theta=10, n_phi=16, n_phase=32, n_E=64, n_chan=300, atm=atm,
+                           lens=small_lens)
+    inst = w.inst.select(np.zeros(24, dtype=int))
+    inst.incl_rad[:] = np.linspace(0.3, 1.5, 24)
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts] * 24), tau=w.tau)
+    ll_tc, mc_tc, _ = _with_env("PPM_RESP_TC", "1", lambda: gpu_loglike(w2))
+    ll_32, mc_32, _ = _with_env("PPM_RESP_TC", "0", lambda: gpu_loglike(w2))
+    assert max_rel(mc_tc, mc_32) < 1e-4
+    for b in range(24):
+        d = w2.counts[rows_of(w2, b)]
+        assert abs(ll_tc[b] - ll_32[b]) <= 1e-4 * np.sum(np.abs(d - mc_32[rows_of(w2, b)])) + 1e-6
