@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PPM likelihood evals/s (ms/eval) at 1e-3 rel. accuracy; batched & grad evals/s"
 FLOP_PER_TRIPLE = 14          # algorithmic FP32 flops per (element, phase, energy) triple
+# backward shift-and-add: five interval cubics per triple (I, dI/dt, dI/dmu and the
+# two cell-weight derivatives), each Horner + accumulate, plus the amortised mu
+# contraction of four stencils: 18 FMA + 4 x 4 FMA x 0.48 nodes per energy
+FLOP_PER_TRIPLE_BWD = 50
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -167,14 +171,24 @@ def _single(w, b):
                           counts=w.counts[r0:r0 + int(inst.n_phase[0])], tau=w.tau)
 
 
-def cpu_baseline(w):
-    """The FP64 oracle (single thread) on a bounded sample, extrapolated."""
+def fd_evals(w):
+    """Oracle evaluations per gradient by central differences (logL + 2 per parameter)."""
+    return 1 + 2 * (5 + 4 * int(w.inst.n_spots))
+
+
+def cpu_baseline(w, grad_mode=False):
+    """The FP64 oracle (single thread) on a bounded sample, extrapolated; for
+    gradients, the cost of central differences with the oracle."""
     dt, factor = oracle_sample(w, CPU_RING_STRIDE)
     per_eval = dt * factor / w.inst.B
-    return {"value": 1.0 / per_eval, "unit": "evals/s", "cores": 1, "kind": "oracle",
+    mult = fd_evals(w) if grad_mode else 1
+    return {"value": 1.0 / (per_eval * mult), "unit": "grad-evals/s" if grad_mode else "evals/s",
+            "cores": 1, "kind": "oracle",
             "sample": "instance 0, every %dth ring, all phases x energies, response and logL; "
-                      "%.1f s measured, extrapolated x%.4g by element x phase x energy work"
-                      % (CPU_RING_STRIDE, dt, factor)}
+                      "%.1f s measured, extrapolated x%.4g by element x phase x energy work%s"
+                      % (CPU_RING_STRIDE, dt, factor,
+                         "; x%d evaluations per central-difference gradient" % mult
+                         if grad_mode else "")}
 
 
 def run_reference(args, rank, world):
@@ -183,24 +197,30 @@ def run_reference(args, rank, world):
     from paper_2510_07764_gb300 import synth
     import oracle
     w = synth.WORKLOADS[args.workload]()
+    grad_mode = args.workload == "grad_batch"
+    mult = fd_evals(w) if grad_mode else 1
     times = []
     for k in range(args.warmup + args.steps):
         dt, factor = oracle_sample(w, REF_RING_STRIDE)
         if k >= args.warmup:
-            times.append(dt * factor)
+            times.append(dt * factor * mult)
     per_step = sum(times) / len(times)
     value = w.inst.B / per_step
     per_eval = per_step / w.inst.B
     sample = ("instance 0, every %dth ring per step, extrapolated by element x phase x energy "
               "work to the whole workload" % REF_RING_STRIDE)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+    unit = "evals/s"
+    if grad_mode:
+        sample += "; x%d evaluations per central-difference gradient" % mult
+        unit = "grad-evals/s"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_eval * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_desc(w),
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -214,6 +234,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = synth.WORKLOADS[args.workload]()
+    grad_mode = args.workload == "grad_batch"
     ctx = ppm.Context(local_rank)
     t0 = time.perf_counter()
     ctx.setup(w)
@@ -222,6 +243,7 @@ def run_ours(args, rank, world, local_rank):
     B = dp.B
     counts = torch.from_numpy(w.counts).to(dev)
     logL = torch.empty(B, dtype=torch.float64, device=dev)
+    grad = torch.empty((B, ppm.N_GRAD), dtype=torch.float64, device=dev)
     flush = torch.empty(args.flush_mib * (1 << 20) // 4, dtype=torch.float32, device=dev)
     dist = world > 1
 
@@ -229,8 +251,14 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             torch.distributed.barrier()
 
+    def step():
+        if grad_mode:
+            ctx.loglike_grad(dp, counts, w.tau, out=logL, grad=grad)
+        else:
+            ctx.loglike(dp, counts, w.tau, out=logL)
+
     for _ in range(args.warmup):
-        ctx.loglike(dp, counts, w.tau, out=logL)
+        step()
     torch.cuda.synchronize()
 
     # ---- device-timed steps (inputs resident in HBM; L2 flushed before each)
@@ -251,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.fill_(float(k))
         evs[k][0].record()
-        ctx.loglike(dp, counts, w.tau, out=logL)
+        step()
         evs[k][1].record()
     torch.cuda.synchronize()
     barrier()
@@ -260,6 +288,18 @@ def run_ours(args, rank, world, local_rank):
     ctx.set_timing(False)
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
     n_bad = int((~np.isfinite(logL.cpu().numpy())).sum())
+    fwd_ms = None
+    if grad_mode:
+        # the forward alone on the same inputs, for the backward / forward ratio
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            evf[k][0].record()
+            ctx.loglike(dp, counts, w.tau, out=logL)
+            evf[k][1].record()
+        torch.cuda.synchronize()
+        fwd_ms = sum(a.elapsed_time(b) for a, b in evf)
 
     # ---- end to end through host buffers (params + counts in, logL out)
     pin = {f: torch.from_numpy(np.ascontiguousarray(getattr(w.inst, f), dtype=np.float64)
@@ -269,8 +309,9 @@ def run_ours(args, rank, world, local_rank):
         setattr(host_inst, f, t)
     counts_pin = torch.from_numpy(w.counts).pin_memory()
     out_pin = torch.empty(B, dtype=torch.float64).pin_memory()
+    grad_pin = torch.empty((B, ppm.N_GRAD), dtype=torch.float64).pin_memory()
     h2d = sum(t.numel() * 8 for t in pin.values()) + counts_pin.numel() * 4
-    d2h = B * 8
+    d2h = B * 8 * (1 + (ppm.N_GRAD if grad_mode else 0))
     evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(args.steps)]
     barrier()
@@ -280,8 +321,10 @@ def run_ours(args, rank, world, local_rank):
         evs2[k][0].record()
         dp.upload(host_inst, non_blocking=True)
         counts.copy_(counts_pin, non_blocking=True)
-        ctx.loglike(dp, counts, w.tau, out=logL)
+        step()
         out_pin.copy_(logL, non_blocking=True)
+        if grad_mode:
+            grad_pin.copy_(grad, non_blocking=True)
         evs2[k][1].record()
     torch.cuda.synchronize()
     barrier()
@@ -298,34 +341,46 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = units / (e2e_ms / 1e3)
 
     calls = max(timing["calls"], 1)
-    k_ms = timing["ms_shift_add"] / calls
     triples = timing["triples"] / calls
-    achieved = triples * FLOP_PER_TRIPLE / (k_ms / 1e3) / 1e12
-    traffic = profile_traffic()
+    stages = {"ring_template": timing["ms_ring"] / calls,
+              "shift_add": timing["ms_shift_add"] / calls,
+              "reduce": timing["ms_reduce"] / calls,
+              "response_loglike": timing["ms_loglike"] / calls}
+    if grad_mode:
+        stages.update({"grad_response": timing["ms_grad_resp"] / calls,
+                       "shift_add_bwd": timing["ms_shift_add_bwd"] / calls,
+                       "template_bwd_final": timing["ms_template_bwd"] / calls})
+        kernel, k_ms, fpt, traffic = ("k_shift_add_bwd<atmosphere>", stages["shift_add_bwd"],
+                                      FLOP_PER_TRIPLE_BWD, None)
+    else:
+        kernel, k_ms, fpt, traffic = ("k_shift_add<atmosphere>", stages["shift_add"],
+                                      FLOP_PER_TRIPLE, profile_traffic())
+    achieved = triples * fpt / (k_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "k_shift_add<atmosphere>", "kernel_ms": k_ms,
-                "triples_per_launch": triples, "flop_per_triple": FLOP_PER_TRIPLE,
+                "kernel": kernel, "kernel_ms": k_ms,
+                "triples_per_launch": triples, "flop_per_triple": fpt,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (derived)",
-                "stage_ms_per_eval": {"ring_template": timing["ms_ring"] / calls,
-                                      "shift_add": k_ms,
-                                      "reduce": timing["ms_reduce"] / calls,
-                                      "response_loglike": timing["ms_loglike"] / calls}}
+                "stage_ms_per_eval": stages}
     cfg = workload_desc(w)
     cfg["l2"] = "flushed before every timed step (%d MiB write)" % args.flush_mib
     cfg["parallelism"] = "replicas x%d" % world
     cfg["setup_s"] = round(setup_s, 3)
-    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+    unit = "grad-evals/s" if grad_mode else "evals/s"
+    line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": cfg,
-            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms / args.steps},
             "gpu_launches": int(timing["launches"]),
             "instances_logL_minus_inf": n_bad,
             "roofline": roofline, "clocks": clk}
+    if grad_mode:
+        line["forward_ms_per_step"] = fwd_ms / args.steps
+        line["backward_over_forward"] = (dev_ms - fwd_ms) / fwd_ms
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+        line["cpu_baseline"] = cpu_baseline(w, grad_mode)
     print(json.dumps(line), flush=True)
     ctx.close()
 

@@ -218,6 +218,31 @@ ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
                        int *inst_status, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Log-likelihood and its gradient (reverse mode of Sect. 2.8.3 Eq. add_Ft,
+ * the Sect. 4 interpolation, Sect. 2.7 attenuation and the response; the
+ * paper motivates gradients only through the inference of Sect. 6 and gives
+ * no adjoint, so this entry point has no direct counterpart in it).
+ * Arguments as ppm_loglike, plus
+ *   grad: DEVICE double [B][13], d logL[b] / d theta in the order
+ *         M (M_sun), R_e (km), inclination (rad), D (kpc), N_H (1e20 cm^-2),
+ *         then colatitude (rad), azimuth (rad), angular radius zeta (rad),
+ *         log10 T for spot 1 and for spot 2 (zeros for a missing spot 2).
+ * The gradient is that of the piecewise-smooth model the forward pass
+ * evaluates: branch decisions (visibility of template points, active
+ * elements, interpolation intervals, clamps) are held fixed; quantities
+ * clamped at a table edge contribute no derivative.  Spin and the mask
+ * parameters are not differentiated.  Instances with inst_status != 0 or
+ * logL = -inf get NaN gradients.  Needs emission 1 (atmosphere table) or 0
+ * (analytic blackbody), and shared memory for three nE x nmu slabs
+ * (PPM_EINVAL otherwise).  Runs the forward pass first (logL is written as
+ * by ppm_loglike), then the backward kernels, on `stream`.
+ * ------------------------------------------------------------------------ */
+ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                            const int *counts, int counts_shared, const float *bkg,
+                            double tau, double *logL, double *grad,
+                            int *inst_status, void *stream);
+
+/* ------------------------------------------------------------------------
  * Stage timing (no counterpart in the paper; tracing support).  When enabled,
  * every compute call records CUDA events around its stages on the call's
  * stream and counts its kernel launches and the (active element, output
@@ -230,6 +255,9 @@ typedef struct {
     double ms_shift_add;   /* shift-and-add + atmosphere interpolation kernel */
     double ms_reduce;      /* partial-sum reduction kernel */
     double ms_loglike;     /* response contraction + likelihood kernels */
+    double ms_grad_resp;   /* gradient: response / likelihood adjoint kernel */
+    double ms_shift_add_bwd; /* gradient: backward shift-and-add kernel */
+    double ms_template_bwd;  /* gradient: template tangents + final reduction */
     long long calls;       /* compute calls timed */
     long long launches;    /* kernels launched by those calls */
     double triples;        /* element x phase x energy triples evaluated */

@@ -16,8 +16,14 @@ from . import _abi
 from ._abi import (PPM_EINVAL, PPM_ENOMEM, PPM_ENOTREADY, PPM_ERANGE, PPM_ETIMEOUT, PPM_OK,
                    LibraryMissing)
 
-__all__ = ["Context", "DeviceParams", "PPMError", "LibraryMissing", "PPM_OK", "PPM_ERANGE",
-           "PPM_EINVAL", "PPM_ENOMEM", "PPM_ETIMEOUT", "PPM_ENOTREADY"]
+__all__ = ["Context", "DeviceParams", "PPMError", "LibraryMissing", "LogLikelihood",
+           "GRAD_NAMES", "N_GRAD", "PPM_OK", "PPM_ERANGE", "PPM_EINVAL", "PPM_ENOMEM", "PPM_ETIMEOUT",
+           "PPM_ENOTREADY"]
+
+# order of the gradient columns of ppm_loglike_grad
+GRAD_NAMES = ("mass_msun", "radius_km", "incl_rad", "dist_kpc", "nh_1e20",
+              "colat_1", "azim_1", "zeta_1", "logT_1", "colat_2", "azim_2", "zeta_2", "logT_2")
+N_GRAD = len(GRAD_NAMES)
 
 
 class PPMError(RuntimeError):
@@ -72,6 +78,28 @@ class DeviceParams:
             else:
                 self.t[f].copy_(torch.from_numpy(np.ascontiguousarray(src, dtype=np.float64).reshape(-1)),
                                 non_blocking=non_blocking)
+
+    def set_theta(self, theta):
+        """Write a [B, 13] float64 CUDA tensor of differentiated parameters
+        (columns in ``GRAD_NAMES`` order) into the device arrays."""
+        B, ns = self.B, self.n_spots
+        for j, f in enumerate(("mass_msun", "radius_km", "incl_rad", "dist_kpc", "nh_1e20")):
+            self.t[f].copy_(theta[:, j])
+        for s in range(ns):
+            for q, f in enumerate(("colat", "azim", "zeta", "logT")):
+                self.t[f].view(B, ns)[:, s].copy_(theta[:, 5 + 4 * s + q])
+
+    def theta(self):
+        """The differentiated parameters as a [B, 13] float64 CUDA tensor."""
+        import torch
+        B, ns = self.B, self.n_spots
+        th = torch.zeros((B, N_GRAD), dtype=torch.float64, device=self.t["mass_msun"].device)
+        for j, f in enumerate(("mass_msun", "radius_km", "incl_rad", "dist_kpc", "nh_1e20")):
+            th[:, j] = self.t[f]
+        for s in range(ns):
+            for q, f in enumerate(("colat", "azim", "zeta", "logT")):
+                th[:, 5 + 4 * s + q] = self.t[f].view(B, ns)[:, s]
+        return th
 
     def struct(self) -> _abi.ppm_params:
         p = _abi.ppm_params()
@@ -183,6 +211,25 @@ class Context:
         self.last_status = status
         return out
 
+    def loglike_grad(self, dp: DeviceParams, counts, tau: float, bkg=None, counts_shared=False,
+                     out=None, grad=None, status=None, stream=None):
+        """Log-likelihood [B] and its gradient [B, 13] (float64 CUDA tensors);
+        gradient columns in ``GRAD_NAMES`` order."""
+        import torch
+        dev = counts.device
+        if out is None:
+            out = torch.empty(dp.B, dtype=torch.float64, device=dev)
+        if grad is None:
+            grad = torch.empty((dp.B, N_GRAD), dtype=torch.float64, device=dev)
+        if status is None:
+            status = torch.empty(dp.B, dtype=torch.int32, device=dev)
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(_abi.ppm_loglike_grad(self.h, dp.struct(), dp.res, ptr(counts),
+                                          int(counts_shared), ptr(bkg), float(tau), ptr(out),
+                                          ptr(grad), ptr(status), _stream_handle(stream)))
+        self.last_status = status
+        return out, grad
+
     def set_timing(self, enable: bool = True):
         self._check(_abi.ppm_set_timing(self.h, int(enable)))
 
@@ -193,3 +240,39 @@ class Context:
 
     def sync(self, stream=None, timeout: float = 30.0):
         self._check(_abi.ppm_sync(self.h, _stream_handle(stream), timeout))
+
+
+def _loglike_function():
+    import torch
+
+    class _LogLike(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, theta, ctx, dp, counts, tau, bkg, counts_shared):
+            dp.set_theta(theta.detach())
+            ll, g = ctx.loglike_grad(dp, counts, tau, bkg=bkg, counts_shared=counts_shared)
+            fctx.save_for_backward(g)
+            return ll
+
+        @staticmethod
+        def backward(fctx, gout):
+            (g,) = fctx.saved_tensors
+            return gout[:, None] * g, None, None, None, None, None, None
+
+    return _LogLike
+
+
+_LOGLIKE_FN = None
+
+
+def LogLikelihood(theta, ctx: "Context", dp: DeviceParams, counts, tau: float, bkg=None,
+                  counts_shared: bool = False):
+    """logL[b](theta[b]) as a differentiable torch function.
+
+    theta: [B, 13] float64 CUDA tensor (``GRAD_NAMES`` order, requires_grad as
+    needed); the other parameters (spin, masks, resolutions) come from ``dp``.
+    The forward call computes logL and its gradient together through
+    ppm_loglike_grad; backward scales the stored gradient."""
+    global _LOGLIKE_FN
+    if _LOGLIKE_FN is None:
+        _LOGLIKE_FN = _loglike_function()
+    return _LOGLIKE_FN.apply(theta, ctx, dp, counts, tau, bkg, counts_shared)

@@ -20,7 +20,7 @@ STATUS_NAMES = ["PPM_OK", "PPM_EINVAL", "PPM_ERANGE", "PPM_ENOMEM", "PPM_ECUDA",
 EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm_get_lens",
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
            "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
-           "ppm_profile_noalloc"]
+           "ppm_profile_noalloc", "ppm_loglike_grad"]
 
 
 class ppm_lens_spec(C.Structure):
@@ -42,6 +42,8 @@ class ppm_params(C.Structure):
 class ppm_timing(C.Structure):
     _fields_ = [("ms_ring", C.c_double), ("ms_shift_add", C.c_double),
                 ("ms_reduce", C.c_double), ("ms_loglike", C.c_double),
+                ("ms_grad_resp", C.c_double), ("ms_shift_add_bwd", C.c_double),
+                ("ms_template_bwd", C.c_double),
                 ("calls", C.c_longlong), ("launches", C.c_longlong), ("triples", C.c_double)]
 
 
@@ -79,6 +81,8 @@ def lib() -> C.CDLL:
         "ppm_profile_noalloc": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
         "ppm_loglike": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d, vp, vp,
                             vp, vp]),
+        "ppm_loglike_grad": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d,
+                                 vp, vp, vp, vp]),
         "ppm_sync": (i, [vp, vp, d]),
         "ppm_set_timing": (i, [vp, i]),
         "ppm_get_timing": (i, [vp, C.POINTER(ppm_timing)]),
@@ -138,6 +142,12 @@ def ppm_loglike(ctx, params: ppm_params, res: ppm_res, counts, counts_shared, bk
                 model_counts, inst_status, stream) -> int:
     return lib().ppm_loglike(ctx, C.byref(params), C.byref(res), counts, counts_shared, bkg,
                              tau, logL, model_counts, inst_status, stream)
+
+
+def ppm_loglike_grad(ctx, params: ppm_params, res: ppm_res, counts, counts_shared, bkg, tau,
+                     logL, grad, inst_status, stream) -> int:
+    return lib().ppm_loglike_grad(ctx, C.byref(params), C.byref(res), counts, counts_shared,
+                                  bkg, tau, logL, grad, inst_status, stream)
 
 
 def ppm_sync(ctx, stream, timeout_s: float) -> int:

@@ -547,11 +547,14 @@ struct Work {
     RingRec *recs;
     float *tmpl, *elems, *partials, *Ft;
     double *row_ll;
+    // gradient only
+    float *lambda, *Aadj, *ringadj;
+    double *ring_grad, *row_sums;
 };
 }  // namespace
 
 static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, bool need_ft,
-                                   Work *w)
+                                   bool grad, Work *w)
 {
     const HostPlan &hp = ctx->plan;
     const int ct = ctx->nc ? loglike_ctiles(ctx->nc) : 1;
@@ -564,6 +567,12 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     const size_t o_part = take((size_t)hp.items.size() * hp.pt * ctx->nEpad * sizeof(float));
     const size_t o_ft = take(need_ft ? (size_t)hp.total_rows * ctx->E.size() * sizeof(float) : 0);
     const size_t o_ll = take(need_ft ? (size_t)hp.total_rows * ct * sizeof(double) : 0);
+    const size_t rows = grad ? (size_t)hp.total_rows : 0, rings = grad ? hp.total_rings : 0;
+    const size_t o_lam = take(rows * ctx->nc * sizeof(float));
+    const size_t o_aadj = take(rows * ctx->nEpad * sizeof(float));
+    const size_t o_radj = take(rings * (4 * (n_fp + 1) + kRingAdjTail) * sizeof(float));
+    const size_t o_rgrad = take(rings * kRingGrad * sizeof(double));
+    const size_t o_rsum = take(rows * grad_ktiles(ctx->nEpad) * 2 * sizeof(double));
     if (off > ctx->ws.n) {
         PPM_CUDA(cudaDeviceSynchronize(), "sync");
         PPM_CUDA(ctx->ws.ensure(off), "alloc workspace");
@@ -576,6 +585,11 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     w->partials = reinterpret_cast<float *>(base + o_part);
     w->Ft = reinterpret_cast<float *>(base + o_ft);
     w->row_ll = reinterpret_cast<double *>(base + o_ll);
+    w->lambda = reinterpret_cast<float *>(base + o_lam);
+    w->Aadj = reinterpret_cast<float *>(base + o_aadj);
+    w->ringadj = reinterpret_cast<float *>(base + o_radj);
+    w->ring_grad = reinterpret_cast<double *>(base + o_rgrad);
+    w->row_sums = reinterpret_cast<double *>(base + o_rsum);
     return PPM_OK;
 }
 
@@ -615,13 +629,13 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
 }
 
 static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
-                              bool internal_ft, cudaStream_t st, Work *w)
+                              bool internal_ft, cudaStream_t st, Work *w, bool grad = false)
 {
     ppm_status s = check_params(ctx, p, res);
     if (s != PPM_OK) return s;
     if ((s = refresh_energies(ctx)) != PPM_OK) return s;
     if ((s = make_plan(ctx, p, res, st)) != PPM_OK) return s;
-    if ((s = ensure_workspace(ctx, p, res->n_fp, internal_ft, w)) != PPM_OK) return s;
+    if ((s = ensure_workspace(ctx, p, res->n_fp, internal_ft, grad, w)) != PPM_OK) return s;
     Params P;
     PlanDev plan;
     LensDev L;
@@ -677,11 +691,10 @@ ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, fl
     return PPM_OK;
 }
 
-ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, const int *counts,
-                       int counts_shared, const float *bkg, double tau, double *logL,
-                       float *model_counts, int *inst_status, void *stream)
+static ppm_status check_loglike_args(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                                     const int *counts, int counts_shared, double tau,
+                                     const double *logL)
 {
-    if (!ctx) return PPM_EINVAL;
     if (!counts || !logL) return fail(ctx, PPM_EINVAL, "null counts or logL");
     if (!ctx->nc) return fail(ctx, PPM_EINVAL, "response not set");
     if (!(tau > 0.0) || !std::isfinite(tau)) return fail(ctx, PPM_EINVAL, "tau must be positive");
@@ -689,38 +702,133 @@ ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, co
         for (int b = 1; b < p->B; ++b)
             if (res->n_phase[b] != res->n_phase[0])
                 return fail(ctx, PPM_EINVAL, "shared counts need equal n_phase");
-    DeviceGuard g(ctx->device);
-    cudaStream_t st = (cudaStream_t)stream;
-    Work w;
-    ppm_status s = run_profile(ctx, p, res, nullptr, true, st, &w);
-    if (s != PPM_OK) return s;
+    return PPM_OK;
+}
+
+// response contraction + likelihood of the profile in w.Ft
+static ppm_status run_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                              const int *counts, int counts_shared, const float *bkg, double tau,
+                              double *logL, float *model_counts, cudaStream_t st, const Work &w)
+{
     Params P;
     PlanDev plan;
     LensDev L;
     AtmDev A;
     EnergyDev en;
     fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
+    // tensor cores for large row counts (batches); the FP32 tile kernel
+    // has lower latency for a few hundred rows
+    bool use_tc = ctx->plan.total_rows >= 512;
+    if (const char *env = getenv("PPM_RESP_TC")) use_tc = atoi(env) != 0;
+    StageTimer t(ctx, 3, st);
+    if (use_tc) {
+        PPM_CUDA(launch_loglike_tc(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
+                                   ctx->d_Rtc.as<uint16_t>(), ctx->d_sigma.as<float>(), ctx->nc,
+                                   counts, counts_shared, bkg, tau, w.status, ctx->d_lfact,
+                                   w.row_ll, model_counts, ctx->d_err, st),
+                 "tensor-core likelihood kernel");
+        launch_ll_final(plan, w.row_ll, resp_tc_ctiles(ctx->nc), w.status, logL, st);
+        PPM_CUDA(cudaGetLastError(), "likelihood reduction");
+    } else {
+        PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
+                                ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc, counts,
+                                counts_shared, bkg, tau, w.status, ctx->d_lfact, w.row_ll,
+                                model_counts, logL, st),
+                 "likelihood kernels");
+    }
+    t.done(2);
+    return PPM_OK;
+}
+
+ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, const int *counts,
+                       int counts_shared, const float *bkg, double tau, double *logL,
+                       float *model_counts, int *inst_status, void *stream)
+{
+    if (!ctx) return PPM_EINVAL;
+    ppm_status s = check_loglike_args(ctx, p, res, counts, counts_shared, tau, logL);
+    if (s != PPM_OK) return s;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Work w;
+    if ((s = run_profile(ctx, p, res, nullptr, true, st, &w)) != PPM_OK) return s;
+    if ((s = run_loglike(ctx, p, res, counts, counts_shared, bkg, tau, logL, model_counts, st,
+                         w)) != PPM_OK)
+        return s;
+    if (inst_status)
+        PPM_CUDA(cudaMemcpyAsync(inst_status, w.status, sizeof(int) * p->B,
+                                 cudaMemcpyDeviceToDevice, st),
+                 "copy status");
+    ctx->err.clear();
+    return PPM_OK;
+}
+
+ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
+                            const int *counts, int counts_shared, const float *bkg, double tau,
+                            double *logL, double *grad, int *inst_status, void *stream)
+{
+    if (!ctx) return PPM_EINVAL;
+    ppm_status s = check_loglike_args(ctx, p, res, counts, counts_shared, tau, logL);
+    if (s != PPM_OK) return s;
+    if (!grad) return fail(ctx, PPM_EINVAL, "null grad");
+    if ((s = check_params(ctx, p, res)) != PPM_OK) return s;
+    if ((s = refresh_energies(ctx)) != PPM_OK) return s;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
     {
-        // tensor cores for large row counts (batches); the FP32 tile kernel
-        // has lower latency for a few hundred rows
-        bool use_tc = ctx->plan.total_rows >= 512;
-        if (const char *env = getenv("PPM_RESP_TC")) use_tc = atoi(env) != 0;
-        StageTimer t(ctx, 3, st);
-        if (use_tc) {
-            PPM_CUDA(launch_loglike_tc(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
-                                       ctx->d_Rtc.as<uint16_t>(), ctx->d_sigma.as<float>(),
-                                       ctx->nc, counts, counts_shared, bkg, tau, w.status,
-                                       ctx->d_lfact, w.row_ll, model_counts, ctx->d_err, st),
-                     "tensor-core likelihood kernel");
-            launch_ll_final(plan, w.row_ll, resp_tc_ctiles(ctx->nc), w.status, logL, st);
-            PPM_CUDA(cudaGetLastError(), "likelihood reduction");
-        } else {
-            PPM_CUDA(launch_loglike(P, plan, w.Ft, ctx->plan.total_rows, (int)ctx->E.size(),
-                                    ctx->d_R.as<float>(), ctx->d_sigma.as<float>(), ctx->nc,
-                                    counts, counts_shared, bkg, tau, w.status, ctx->d_lfact,
-                                    w.row_ll, model_counts, logL, st),
-                     "likelihood kernels");
-        }
+        // the backward shift-and-add holds the slab and its two cell-weight
+        // derivatives; check its shared memory before any work is enqueued
+        PlanDev pd{};
+        pd.n_fp = res->n_fp;
+        AtmDev A{};
+        A.nmu = ctx->nmu;
+        A.nE = ctx->nEt;
+        A.nmu_pad = ctx->nmu_pad;
+        EnergyDev en{};
+        en.nEpad = ctx->nEpad;
+        int n_phi_max = 0;
+        for (int b = 0; b < p->B; ++b) n_phi_max = std::max(n_phi_max, res->n_phi[b]);
+        const size_t need = shift_add_bwd_smem_bytes(p->emission, pd, A, en, n_phi_max);
+        if (need > ctx->smem_optin)
+            return fail(ctx, PPM_EINVAL,
+                        "gradient needs %zu B of shared memory per block (three nE x nmu "
+                        "slabs); the device allows %zu B",
+                        need, ctx->smem_optin);
+    }
+    Work w;
+    if ((s = run_profile(ctx, p, res, nullptr, true, st, &w, true)) != PPM_OK) return s;
+    if ((s = run_loglike(ctx, p, res, counts, counts_shared, bkg, tau, logL, w.lambda, st, w)) !=
+        PPM_OK)
+        return s;
+    Params P;
+    PlanDev plan;
+    LensDev L;
+    AtmDev A;
+    EnergyDev en;
+    fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
+    const HostPlan &hp = ctx->plan;
+    {
+        StageTimer t(ctx, 4, st);
+        PPM_CUDA(launch_grad_resp(P, plan, w.Ft, hp.total_rows, en, ctx->d_R.as<float>(),
+                                  ctx->d_sigma.as<float>(), ctx->nc, counts, counts_shared, bkg,
+                                  tau, w.lambda, w.status, w.Aadj, w.row_sums, st),
+                 "response adjoint kernel");
+        t.done(1);
+    }
+    {
+        StageTimer t(ctx, 5, st);
+        PPM_CUDA(launch_shift_add_bwd(P, plan, A, en, w.recs, w.tmpl, w.elems, w.status, w.Aadj,
+                                      w.ringadj, hp.n_phi_max, st),
+                 "backward shift-and-add kernel");
+        t.done(1);
+    }
+    {
+        StageTimer t(ctx, 6, st);
+        PPM_CUDA(launch_template_bwd(P, plan, L, A, w.recs, w.tmpl, w.status, w.ringadj,
+                                     w.ring_grad, st),
+                 "template tangent kernel");
+        PPM_CUDA(launch_grad_final(P, plan, w.ring_grad, w.row_sums, grad_ktiles(en.nEpad),
+                                   w.status, logL, grad, st),
+                 "gradient reduction kernel");
         t.done(2);
     }
     if (inst_status)
@@ -753,8 +861,10 @@ ppm_status ppm_get_timing(ppm_ctx *ctx, ppm_timing *out)
         PPM_CUDA(cudaEventSynchronize(pd.b), "timing event");
         float ms = 0.0f;
         PPM_CUDA(cudaEventElapsedTime(&ms, pd.a, pd.b), "elapsed");
-        double *slot[] = {&ctx->acc.ms_ring, &ctx->acc.ms_shift_add, &ctx->acc.ms_reduce,
-                          &ctx->acc.ms_loglike};
+        double *slot[] = {&ctx->acc.ms_ring,         &ctx->acc.ms_shift_add,
+                          &ctx->acc.ms_reduce,       &ctx->acc.ms_loglike,
+                          &ctx->acc.ms_grad_resp,    &ctx->acc.ms_shift_add_bwd,
+                          &ctx->acc.ms_template_bwd};
         *slot[pd.stage] += ms;
         ctx->ev_pool.push_back(pd.a);
         ctx->ev_pool.push_back(pd.b);

@@ -147,6 +147,32 @@ cudaError_t launch_loglike_tc(const Params &p, const PlanDev &plan, const float 
                               double tau, const int *status, const double *lfact,
                               double *row_ll, float *model_counts, unsigned *err, cudaStream_t st);
 
+// ---- gradient (ppm_loglike_grad) ------------------------------------------
+constexpr int kNGrad = 13;        // M, R_e, incl, D, N_H, (colat, azim, zeta, logT) x 2 spots
+constexpr int kRingAdjTail = 8;   // ring sums after the 4 (n_fp + 1) template adjoints
+constexpr int kRingGrad = 8;      // per ring: M, R_e, incl, colat, azim, zeta, logT, 0
+constexpr int kGradTN = 64;       // energies per block of the response-adjoint kernel
+
+size_t shift_add_bwd_smem_bytes(int emission, const PlanDev &plan, const AtmDev &A,
+                                const EnergyDev &en, int n_phi_max);
+cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const AtmDev &A,
+                                 const EnergyDev &en, const RingRec *recs, const float *tmpl,
+                                 const float *elems, const int *status, const float *Aadj,
+                                 float *ringadj, int n_phi_max, cudaStream_t st);
+cudaError_t launch_template_bwd(const Params &p, const PlanDev &plan, const LensDev &L,
+                                const AtmDev &A, const RingRec *recs, const float *tmpl,
+                                const int *status, const float *ringadj, double *ring_grad,
+                                cudaStream_t st);
+int grad_ktiles(int nEpad);
+cudaError_t launch_grad_resp(const Params &p, const PlanDev &plan, const float *Ft,
+                             int total_rows, const EnergyDev &en, const float *R,
+                             const float *sigma, int nc, const int *counts, int counts_shared,
+                             const float *bkg, double tau, const float *lambda,
+                             const int *status, float *Aadj, double *row_sums, cudaStream_t st);
+cudaError_t launch_grad_final(const Params &p, const PlanDev &plan, const double *ring_grad,
+                              const double *row_sums, int ktiles, const int *status,
+                              const double *logL, double *grad, cudaStream_t st);
+
 // row -> instance lookup (binary search over InstPlan.row0)
 __device__ __forceinline__ int find_instance_by_row(const InstPlan *ip, int B, int row)
 {

@@ -1,0 +1,503 @@
+// Adjoint of the shift-and-add with atmosphere interpolation (reverse mode of
+// Eq. add_Ft and of the Sect. 4 interpolation), FP32.
+//
+// Input: A[row][k] = dlogL/dF_t[row][k] / (E_k * flux scale), i.e. the adjoint
+// of every contribution F_p I(z_p E_k, mu_p) (F_p in template units).
+// One block per ring, all output phases.  For every (element, phase) pair the
+// block accumulates, over the energies,
+//     sF  = sum_k A_k I_k                 -> dlogL/dF_p
+//     sZ  = sum_k A_k dI/dt_k             -> dlogL/dz_p  (t = table position in ln E)
+//     sMu = sum_k A_k dI/dmu_k            -> dlogL/dmu_p
+//     sT  = sum_k A_k dI/dw_T,k           -> dlogL/d(logT cell weight)
+//     sG  = sum_k A_k dI/dw_g,k           -> dlogL/d(logg cell weight)
+// from four sliding interval cubics (intensity, mu-derivative weights, and the
+// two slab derivatives staged alongside the slab), then scatters them onto
+// the ring's template adjoints through the linear phase interpolation,
+// including the dependence of the interpolation weight on phi_o and on the
+// element azimuth.  The per-ring record (floats):
+//     gF[n_fp+1] gZ[n_fp+1] gMu[n_fp+1] gPh[n_fp+1] | sum gs | sum gs*(s - s_ref) | gWT | gWg
+//     | s_ref | 0 0 0
+// where gs is the adjoint of an element's azimuth / 2 pi and the second
+// tail sum is taken about s_ref (the ring's first active element), which
+// keeps it free of cancellation for narrow azimuth spans.
+#include "ppm_internal.cuh"
+
+namespace ppm {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBwdBlock = 512;
+
+struct BLayout {
+    int tmpl, elems, munodes, pk, E3, arow, adj, red, slab, slabT, slabG, total;
+};
+
+__device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, float w1, float w2,
+                                      float w3)
+{
+    return fmaf(w3, q[3], fmaf(w2, q[2], fmaf(w1, q[1], w0 * q[0])));
+}
+
+struct Cubic {
+    float c0, c1, c2, c3, W2, W3;  // power basis of the current interval + nodes q+1, q+2
+};
+
+__device__ __forceinline__ void cubic_set(Cubic &C, float a, float b, float c, float d)
+{
+    C.c0 = b;
+    C.c2 = fmaf(0.5f, a + c, -b);
+    C.c3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (b - c));
+    C.c1 = fmaf(c - a, 0.5f, -C.c3);
+    C.W2 = c;
+    C.W3 = d;
+}
+
+__device__ __forceinline__ void cubic_shift(Cubic &C, float d)
+{
+    cubic_set(C, C.c0, C.W2, C.W3, d);
+}
+
+__device__ __forceinline__ float horner(const Cubic &C, float t)
+{
+    return fmaf(t, fmaf(t, fmaf(t, C.c3, C.c2), C.c1), C.c0);
+}
+
+// state of one (element, phase) pair in the backward pass
+struct PairB {
+    bool on;
+    float Fp, zp, w, dphi, dF, dZ, dM;  // interpolation weight, phi_o step, template differences
+    int i;                              // template interval
+    float w0, w1, w2, w3;               // mu weights (not scaled by F_p)
+    float v0, v1, v2, v3;               // their mu derivatives
+    int s0;
+    float lz;
+};
+
+template <bool ATM>
+__device__ __forceinline__ PairB pair_bwd(bool on, float s, float phi_out, const float *ph,
+                                          const float *mun, int n_fp, int top, const AtmDev &A,
+                                          float inv_dlnE)
+{
+    PairB P;
+    P.on = false;
+    P.Fp = P.zp = P.w = P.dphi = P.dF = P.dZ = P.dM = 0.0f;
+    P.i = 0;
+    P.w0 = P.w1 = P.w2 = P.w3 = P.v0 = P.v1 = P.v2 = P.v3 = 0.0f;
+    P.s0 = 0;
+    P.lz = 0.0f;
+    if (!on) return P;
+    const float *F = ph + (n_fp + 1), *Z = F + (n_fp + 1), *M = Z + (n_fp + 1);
+    const float x = phi_out + s + 1.0f - ph[0];
+    const float phip = x - floorf(x) + ph[0];
+    int lo = 0;
+    for (int step = top; step > 0; step >>= 1) {
+        const int c = lo + step;
+        if (c <= n_fp - 1 && ph[c] <= phip) lo = c;
+    }
+    const float dphi = ph[lo + 1] - ph[lo];
+    float w = (phip - ph[lo]) / dphi;
+    const bool wclamp = !(w >= 0.0f && w <= 1.0f);
+    w = fminf(fmaxf(w, 0.0f), 1.0f);
+    const float Fp = fmaf(F[lo + 1] - F[lo], w, F[lo]);
+    const float zp = fmaf(Z[lo + 1] - Z[lo], w, Z[lo]);
+    const float mp = fmaf(M[lo + 1] - M[lo], w, M[lo]);
+    if (!(Fp != 0.0f && zp > 0.0f && zp < 1e30f)) return P;
+    P.on = true;
+    P.Fp = Fp;
+    P.zp = zp;
+    P.i = lo;
+    P.w = w;
+    P.dphi = wclamp ? 0.0f : dphi;  // zero marks a clamped weight (no phase derivative)
+    P.dF = F[lo + 1] - F[lo];
+    P.dZ = Z[lo + 1] - Z[lo];
+    P.dM = M[lo + 1] - M[lo];
+    if (!ATM) return P;
+    const int nmu = A.nmu;
+    const bool mclamp = !(mp > mun[0] && mp < mun[nmu - 1]);
+    const float mu = fminf(fmaxf(mp, mun[0]), mun[nmu - 1]);
+    int i = 0;
+    for (int step = 64; step > 0; step >>= 1) {
+        const int c = i + step;
+        if (c <= nmu - 2 && mun[c] <= mu) i = c;
+    }
+    float wv[4] = {0.f, 0.f, 0.f, 0.f}, dv[4] = {0.f, 0.f, 0.f, 0.f};
+    int s0;
+    if (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1) {
+        s0 = i - 1;
+        float x4[4] = {mun[s0], mun[s0 + 1], mun[s0 + 2], mun[s0 + 3]};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float den = 1.0f, prod = 1.0f, der = 0.0f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (b == a) continue;
+                den *= (x4[a] - x4[b]);
+                // d/dmu prod_{b != a} (mu - x_b): product rule
+                der = der * (mu - x4[b]) + prod;
+                prod *= (mu - x4[b]);
+            }
+            wv[a] = prod / den;
+            dv[a] = der / den;
+        }
+    } else {
+        s0 = min(max(i - 1, 0), nmu - 4);
+        const float h = mun[i + 1] - mun[i];
+        const float t = (mu - mun[i]) / h;
+        const int o = i - s0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            wv[a] = (a == o) ? 1.0f - t : ((a == o + 1) ? t : 0.0f);
+            dv[a] = (a == o) ? -1.0f / h : ((a == o + 1) ? 1.0f / h : 0.0f);
+        }
+    }
+    if (mclamp) dv[0] = dv[1] = dv[2] = dv[3] = 0.0f;
+    P.w0 = wv[0]; P.w1 = wv[1]; P.w2 = wv[2]; P.w3 = wv[3];
+    P.v0 = dv[0]; P.v1 = dv[1]; P.v2 = dv[2]; P.v3 = dv[3];
+    P.s0 = s0;
+    P.lz = logf(zp) * inv_dlnE;
+    return P;
+}
+
+struct Quint {
+    float I, dI, Im, It, Ig;
+};
+
+// general evaluation at table position p (edges / clamping), all five values
+__device__ __noinline__ Quint bwd_general(const PairB &P, const float *S, const float *ST,
+                                          const float *SG, int Pm, int nE_t, float p)
+{
+    Quint Q;
+    int q0, qn;
+    bool cubic = false, clamp = false;
+    float t = 0.0f;
+    if (p <= 0.0f) { q0 = 0; clamp = true; }
+    else if (p >= (float)(nE_t - 1)) { q0 = nE_t - 1; clamp = true; }
+    else {
+        const float q = floorf(p);
+        q0 = (int)q;
+        t = p - q;
+        cubic = q0 >= 1 && q0 + 2 <= nE_t - 1;
+    }
+    qn = q0;
+    auto node = [&](const float *B, int n, float a0, float a1, float a2, float a3) {
+        return dot4(B + n * Pm + P.s0, a0, a1, a2, a3);
+    };
+    if (clamp) {
+        Q.I = node(S, qn, P.w0, P.w1, P.w2, P.w3);
+        Q.Im = node(S, qn, P.v0, P.v1, P.v2, P.v3);
+        Q.It = node(ST, qn, P.w0, P.w1, P.w2, P.w3);
+        Q.Ig = node(SG, qn, P.w0, P.w1, P.w2, P.w3);
+        Q.dI = 0.0f;
+        return Q;
+    }
+    if (cubic) {
+        Cubic c[4];
+        const float *B[4] = {S, S, ST, SG};
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+            const bool der = (z == 1);
+            const float a0 = der ? P.v0 : P.w0, a1 = der ? P.v1 : P.w1;
+            const float a2 = der ? P.v2 : P.w2, a3 = der ? P.v3 : P.w3;
+            cubic_set(c[z], node(B[z], q0 - 1, a0, a1, a2, a3), node(B[z], q0, a0, a1, a2, a3),
+                      node(B[z], q0 + 1, a0, a1, a2, a3), node(B[z], q0 + 2, a0, a1, a2, a3));
+        }
+        Q.I = horner(c[0], t);
+        Q.dI = fmaf(t, fmaf(t, 3.0f * c[0].c3, 2.0f * c[0].c2), c[0].c1);
+        Q.Im = horner(c[1], t);
+        Q.It = horner(c[2], t);
+        Q.Ig = horner(c[3], t);
+        return Q;
+    }
+    const float b0 = node(S, q0, P.w0, P.w1, P.w2, P.w3), b1 = node(S, q0 + 1, P.w0, P.w1, P.w2, P.w3);
+    Q.I = fmaf(t, b1 - b0, b0);
+    Q.dI = b1 - b0;
+    const float m0 = node(S, q0, P.v0, P.v1, P.v2, P.v3), m1 = node(S, q0 + 1, P.v0, P.v1, P.v2, P.v3);
+    Q.Im = fmaf(t, m1 - m0, m0);
+    const float t0 = node(ST, q0, P.w0, P.w1, P.w2, P.w3), t1 = node(ST, q0 + 1, P.w0, P.w1, P.w2, P.w3);
+    Q.It = fmaf(t, t1 - t0, t0);
+    const float g0 = node(SG, q0, P.w0, P.w1, P.w2, P.w3), g1 = node(SG, q0 + 1, P.w0, P.w1, P.w2, P.w3);
+    Q.Ig = fmaf(t, g1 - g0, g0);
+    return Q;
+}
+
+template <int EMIS>
+__global__ void __launch_bounds__(kBwdBlock, 1)
+    k_shift_add_bwd(Params p, PlanDev plan, AtmDev A, EnergyDev en, BLayout lay,
+                    const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
+                    const float *__restrict__ elems, const int *__restrict__ status,
+                    const float *__restrict__ Aadj, float *__restrict__ ringadj)
+{
+    extern __shared__ float sm[];
+    const int ring = blockIdx.x;
+    const int b = find_instance_by_ring(plan.inst, plan.B, ring);
+    const InstPlan ip = plan.inst[b];
+    const int n_fp = plan.n_fp;
+    const int nE = en.nE, nEpad = en.nEpad;
+    const int rec_len = 4 * (n_fp + 1) + kRingAdjTail;
+    float *out = ringadj + (size_t)ring * rec_len;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const RingRec rec = recs[ring];
+    if (!rec.visible || status[b] != 0) {
+        for (int i = tid; i < rec_len; i += blockDim.x) out[i] = 0.0f;
+        return;
+    }
+    float *adj = sm + lay.adj;  // gF | gZ | gMu | gPh
+    float *red = sm + lay.red;  // 4 ring sums
+    for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) adj[i] = 0.0f;
+    if (tid < 4) red[tid] = 0.0f;
+    {
+        const float *tsrc = tmpl + (size_t)ring * 4 * (n_fp + 1);
+        for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) sm[lay.tmpl + i] = tsrc[i];
+        const float *esrc = elems + (size_t)ip.elem0 + (size_t)(ring - ip.ring0) * ip.n_phi;
+        for (int i = tid; i < rec.n_active; i += blockDim.x) sm[lay.elems + i] = esrc[i];
+        for (int i = tid; i < nEpad; i += blockDim.x) {
+            sm[lay.pk + i] = EMIS == 1 ? en.pk[i] : en.E[i];
+            if (EMIS == 0) sm[lay.E3 + i] = en.E3[i];
+        }
+        if (EMIS == 1) {
+            for (int i = tid; i < A.nmu; i += blockDim.x) sm[lay.munodes + i] = A.mu[i];
+            const int plane = A.nmu * A.nE;
+            const float *I00 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
+            const float *I01 = I00 + plane;
+            const float *I10 = I00 + (size_t)A.ng * plane;
+            const float *I11 = I10 + plane;
+            const float wT = rec.wT, wg = rec.wg;
+            const int Pm = A.nmu_pad;
+            for (int idx = tid; idx < plane; idx += blockDim.x) {
+                const float a = __ldg(I00 + idx), c = __ldg(I01 + idx);
+                const float d = __ldg(I10 + idx), e = __ldg(I11 + idx);
+                const int m = idx / A.nE, n = idx - m * A.nE;
+                const int o = n * Pm + m;
+                // the forward slab with the forward's corner weights, and its
+                // derivatives with respect to the two cell weights
+                sm[lay.slab + o] = (1.0f - wT) * (1.0f - wg) * a + (1.0f - wT) * wg * c +
+                                   wT * (1.0f - wg) * d + wT * wg * e;
+                sm[lay.slabT + o] = (1.0f - wg) * (d - a) + wg * (e - c);
+                sm[lay.slabG + o] = (1.0f - wT) * (c - a) + wT * (e - d);
+            }
+        }
+    }
+    __syncthreads();
+
+    int top = 1;
+    while (top * 2 <= n_fp) top *= 2;
+    const float inv_nphase = 1.0f / (float)ip.n_phase;
+    const float inv_dlnE = EMIS == 1 ? (float)(1.0 / A.dlnE) : 0.0f;
+    const int Pm = A.nmu_pad;
+    const int offT = lay.slabT - lay.slab, offG = lay.slabG - lay.slab;
+    const float *ph = sm + lay.tmpl;
+    const float *mun = sm + lay.munodes;
+    const float *sel = sm + lay.elems;
+    const float *S = sm + lay.slab;
+    const float *spk = sm + lay.pk;  // table positions (atmosphere) or energies (blackbody)
+    const float *sE3 = sm + lay.E3;
+    float *arow = sm + lay.arow + warp * nEpad;
+    const float pk0 = spk[0], pkl = spk[nE - 1];
+    const float lz_safe = 1.25f - pk0;
+    const bool sliding = en.sliding != 0;
+    const int n_act = rec.n_active;
+    const float s_ref = sel[0];
+    const float inv_kT = 1.0f / rec.kT;
+    const float Kbb = (float)(2.0 / (kH_KEVS * kH_KEVS * kH_KEVS * kC_CM * kC_CM));
+    float *gF = adj, *gZ = adj + (n_fp + 1), *gM = adj + 2 * (n_fp + 1), *gP = adj + 3 * (n_fp + 1);
+    float lane_gs = 0.0f, lane_gss = 0.0f, lane_T = 0.0f, lane_G = 0.0f;
+
+    for (int j = warp; j < ip.n_phase; j += kBwdBlock / 32) {
+        const float *asrc = Aadj + (size_t)(ip.row0 + j) * nEpad;
+        for (int k = lane; k < nEpad; k += 32) arow[k] = asrc[k];
+        __syncwarp();
+        const float phi_out = (float)j * inv_nphase;
+        for (int g0 = 0; g0 < n_act; g0 += 32) {
+            const int m = g0 + lane;
+            const bool on = m < n_act;
+            const float s = on ? sel[m] : 0.0f;
+            const PairB P = pair_bwd<EMIS == 1>(on, s, phi_out, ph, mun, n_fp, top, A, inv_dlnE);
+            float gFp = 0.f, gzp = 0.f, gmp = 0.f;
+            if constexpr (EMIS == 1) {
+                const bool fast = P.on && sliding && (pk0 + P.lz >= 1.0f) &&
+                                  (pkl + P.lz < (float)(A.nE - 2));
+                const bool anyslow = __any_sync(kFull, P.on && !fast);
+                float sF = 0.f, sZ = 0.f, sMu = 0.f, sT = 0.f, sG = 0.f;
+                if (sliding && !anyslow) {
+                    // lanes without a pair run the window with zero weights
+                    const float lz = fast ? P.lz : lz_safe;
+                    const float a0 = fast ? P.w0 : 0.f, a1 = fast ? P.w1 : 0.f;
+                    const float a2 = fast ? P.w2 : 0.f, a3 = fast ? P.w3 : 0.f;
+                    const float b0 = fast ? P.v0 : 0.f, b1 = fast ? P.v1 : 0.f;
+                    const float b2 = fast ? P.v2 : 0.f, b3 = fast ? P.v3 : 0.f;
+                    const float q = floorf(pk0 + lz);
+                    float off = lz - q;
+                    const float *sp = S + ((int)q + 2) * Pm + P.s0;
+                    Cubic cI, cM, cT, cG;
+                    cubic_set(cI, dot4(sp - 3 * Pm, a0, a1, a2, a3), dot4(sp - 2 * Pm, a0, a1, a2, a3),
+                              dot4(sp - Pm, a0, a1, a2, a3), dot4(sp, a0, a1, a2, a3));
+                    cubic_set(cM, dot4(sp - 3 * Pm, b0, b1, b2, b3), dot4(sp - 2 * Pm, b0, b1, b2, b3),
+                              dot4(sp - Pm, b0, b1, b2, b3), dot4(sp, b0, b1, b2, b3));
+                    cubic_set(cT, dot4(sp + offT - 3 * Pm, a0, a1, a2, a3),
+                              dot4(sp + offT - 2 * Pm, a0, a1, a2, a3),
+                              dot4(sp + offT - Pm, a0, a1, a2, a3), dot4(sp + offT, a0, a1, a2, a3));
+                    cubic_set(cG, dot4(sp + offG - 3 * Pm, a0, a1, a2, a3),
+                              dot4(sp + offG - 2 * Pm, a0, a1, a2, a3),
+                              dot4(sp + offG - Pm, a0, a1, a2, a3), dot4(sp + offG, a0, a1, a2, a3));
+                    for (int k = 0; k < nE; ++k) {
+                        float t = spk[k] + off;
+                        if (t >= 1.0f) {
+                            sp += Pm;
+                            const float x0 = sp[0], x1 = sp[1], x2 = sp[2], x3 = sp[3];
+                            cubic_shift(cI, fmaf(a3, x3, fmaf(a2, x2, fmaf(a1, x1, a0 * x0))));
+                            cubic_shift(cM, fmaf(b3, x3, fmaf(b2, x2, fmaf(b1, x1, b0 * x0))));
+                            cubic_shift(cT, dot4(sp + offT, a0, a1, a2, a3));
+                            cubic_shift(cG, dot4(sp + offG, a0, a1, a2, a3));
+                            off -= 1.0f;
+                            t -= 1.0f;
+                        }
+                        const float ak = arow[k];
+                        sF = fmaf(ak, horner(cI, t), sF);
+                        sZ = fmaf(ak, fmaf(t, fmaf(t, 3.0f * cI.c3, 2.0f * cI.c2), cI.c1), sZ);
+                        sMu = fmaf(ak, horner(cM, t), sMu);
+                        sT = fmaf(ak, horner(cT, t), sT);
+                        sG = fmaf(ak, horner(cG, t), sG);
+                    }
+                } else if (P.on) {
+                    for (int k = 0; k < nE; ++k) {
+                        const Quint Q = bwd_general(P, S, S + offT, S + offG, Pm, A.nE, spk[k] + P.lz);
+                        const float ak = arow[k];
+                        sF = fmaf(ak, Q.I, sF);
+                        sZ = fmaf(ak, Q.dI, sZ);
+                        sMu = fmaf(ak, Q.Im, sMu);
+                        sT = fmaf(ak, Q.It, sT);
+                        sG = fmaf(ak, Q.Ig, sG);
+                    }
+                }
+                if (P.on) {
+                    gFp = sF;
+                    gzp = P.Fp * sZ * inv_dlnE / P.zp;
+                    gmp = P.Fp * sMu;
+                    lane_T = fmaf(P.Fp, sT, lane_T);
+                    lane_G = fmaf(P.Fp, sG, lane_G);
+                }
+            } else {
+                // analytic isotropic blackbody: C_k = F_p K z^3 E^3 / expm1(x), x = z E / kT;
+                // dC/dz = C (3 - r) / z and dC/dkT = C r / kT with r = x e^x / expm1(x)
+                if (__any_sync(kFull, P.on) && P.on) {
+                    const float bz = Kbb * P.zp * P.zp * P.zp, az = P.zp * inv_kT;
+                    float sF = 0.f, sR = 0.f;
+                    for (int k = 0; k < nE; ++k) {
+                        const float x = az * spk[k];
+                        const float em = expm1f(x);
+                        const float I0 = bz * sE3[k] / em;
+                        const float r = x * (1.0f + 1.0f / em);
+                        const float ak = arow[k];
+                        sF = fmaf(ak, I0, sF);
+                        sR = fmaf(ak, I0 * r, sR);
+                    }
+                    gFp = sF;
+                    gzp = P.Fp * (3.0f * sF - sR) / P.zp;
+                    lane_T = fmaf(P.Fp, sR * inv_kT, lane_T);
+                }
+            }
+            if (P.on) {
+                const float w = P.w, u = 1.0f - w;
+                atomicAdd(&gF[P.i], gFp * u);
+                atomicAdd(&gF[P.i + 1], gFp * w);
+                atomicAdd(&gZ[P.i], gzp * u);
+                atomicAdd(&gZ[P.i + 1], gzp * w);
+                if (EMIS == 1) {
+                    atomicAdd(&gM[P.i], gmp * u);
+                    atomicAdd(&gM[P.i + 1], gmp * w);
+                }
+                if (P.dphi > 0.0f) {
+                    // phi_p = phi_out + s (mod 1); w = (phi_p - phi_o[i]) / (phi_o[i+1] - phi_o[i])
+                    const float gw = gFp * P.dF + gzp * P.dZ + gmp * P.dM;
+                    const float gwd = gw / P.dphi;
+                    atomicAdd(&gP[P.i], gwd * (w - 1.0f));
+                    atomicAdd(&gP[P.i + 1], -gwd * w);
+                    lane_gs += gwd;
+                    lane_gss = fmaf(gwd, s - s_ref, lane_gss);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // ring sums
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        lane_gs += __shfl_xor_sync(kFull, lane_gs, o);
+        lane_gss += __shfl_xor_sync(kFull, lane_gss, o);
+        lane_T += __shfl_xor_sync(kFull, lane_T, o);
+        lane_G += __shfl_xor_sync(kFull, lane_G, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&red[0], lane_gs);
+        atomicAdd(&red[1], lane_gss);
+        atomicAdd(&red[2], lane_T);
+        atomicAdd(&red[3], lane_G);
+    }
+    __syncthreads();
+    for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) out[i] = adj[i];
+    if (tid < kRingAdjTail)
+        out[4 * (n_fp + 1) + tid] = tid < 4 ? red[tid] : (tid == 4 ? s_ref : 0.0f);
+}
+
+struct BwdSizes {
+    BLayout lay;
+    size_t bytes;
+};
+
+BwdSizes bwd_layout(int emission, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
+                    int n_phi_max)
+{
+    BwdSizes z;
+    BLayout &lay = z.lay;
+    int off = 0;
+    auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
+    const int slab = emission == 1 ? A.nE * A.nmu_pad : 0;
+    lay.tmpl = take(4 * (plan.n_fp + 1));
+    lay.elems = take(n_phi_max);
+    lay.munodes = take(emission == 1 ? A.nmu : 0);
+    lay.pk = take(en.nEpad);
+    lay.E3 = take(emission == 1 ? 0 : en.nEpad);
+    lay.arow = take((kBwdBlock / 32) * en.nEpad);
+    lay.adj = take(4 * (plan.n_fp + 1));
+    lay.red = take(4);
+    lay.slab = take(slab);
+    lay.slabT = take(slab);
+    lay.slabG = take(slab);
+    lay.total = off;
+    z.bytes = (size_t)off * sizeof(float);
+    return z;
+}
+
+}  // namespace
+
+size_t shift_add_bwd_smem_bytes(int emission, const PlanDev &plan, const AtmDev &A,
+                                const EnergyDev &en, int n_phi_max)
+{
+    return bwd_layout(emission, plan, A, en, n_phi_max).bytes;
+}
+
+cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const AtmDev &A,
+                                 const EnergyDev &en, const RingRec *recs, const float *tmpl,
+                                 const float *elems, const int *status, const float *Aadj,
+                                 float *ringadj, int n_phi_max, cudaStream_t st)
+{
+    if (plan.total_rings <= 0) return cudaSuccess;
+    const BwdSizes z = bwd_layout(p.emission, plan, A, en, n_phi_max);
+    cudaError_t e;
+    if (p.emission == 1) {
+        e = cudaFuncSetAttribute(k_shift_add_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)z.bytes);
+        if (e != cudaSuccess) return e;
+        k_shift_add_bwd<1><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
+            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
+    } else {
+        e = cudaFuncSetAttribute(k_shift_add_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)z.bytes);
+        if (e != cudaSuccess) return e;
+        k_shift_add_bwd<0><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
+            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ppm

@@ -100,7 +100,10 @@ class Instances:
         return Instances(**d)
 
     def copy(self) -> "Instances":
-        return self.replace()
+        """Independent copy (arrays duplicated)."""
+        d = {f.name: getattr(self, f.name) for f in dataclasses.fields(self)}
+        return Instances(**{k: (np.array(v) if isinstance(v, np.ndarray) else v)
+                            for k, v in d.items()})
 
 
 @dataclasses.dataclass

@@ -1,0 +1,167 @@
+"""Gradient of the log-likelihood (ppm_loglike_grad, hand-written adjoints)
+against central finite differences of the FP64 oracle, step 1e-5 relative,
+tolerance 1e-3 relative per component (plus a floor of 1e-5 of the largest
+scale-weighted component for components near zero).
+
+The model is piecewise smooth (template visibility, interpolation intervals);
+where a difference step could straddle a branch change, the reference is
+first checked against a second step size and only components whose two
+references agree are compared.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import context
+from grad_helpers import (NAMES, grad_tol, n_params, oracle_fd, oracle_ll, single)
+
+pytestmark = pytest.mark.gpu
+
+DEG = math.pi / 180.0
+
+
+def gpu_grad(w, counts=None):
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(np.ascontiguousarray(w.counts if counts is None else counts)).cuda()
+    ll, g = ctx.loglike_grad(dp, cnt, w.tau)
+    ctx.sync()
+    return ll.cpu().numpy(), g.cpu().numpy(), ctx.last_status.cpu().numpy()
+
+
+def visible_two_cap(synth, atm, lens, **kw):
+    """Two caps that stay on the visible hemisphere at every phase, with
+    temperatures between table nodes."""
+    w = synth.atm_two_spot(atm=atm, lens=lens, **kw)
+    i = w.inst
+    i.incl_rad[0] = 30 * DEG
+    i.colat[0] = [25 * DEG, 55 * DEG]
+    i.azim[0] = [0.3, math.pi]
+    i.zeta[0] = [0.2, 0.15]
+    i.logT[0] = [6.112, 6.023]
+    i.mask_zeta[0] = [0.0, 0.0]
+    return w
+
+
+def _check(g, ref, mask=None):
+    tol = grad_tol(ref)
+    bad = np.abs(g - ref) > tol
+    if mask is not None:
+        bad &= mask
+    assert not bad.any(), "\n".join(
+        "%-10s gpu %.9e ref %.9e rel %.2e" % (NAMES[j], g[j], ref[j], abs(g[j] / ref[j] - 1))
+        for j in np.nonzero(bad)[0])
+
+
+def test_grad_two_caps_visible(orc, synth, atm, small_lens):
+    w = visible_two_cap(synth, atm, small_lens, n_theta=16, n_phi=24, n_phase=32, n_E=64,
+                        n_chan=40)
+    ll, g, st = gpu_grad(w)
+    assert st[0] == 0
+    assert abs(ll[0] - oracle_ll(orc, w)) < 1e-3 * abs(ll[0])
+    ref = oracle_fd(orc, w, rel=1e-5)
+    _check(g[0, :13], ref)
+
+
+def test_grad_cap_and_ring_with_limb(orc, synth, atm, small_lens):
+    """The two-spot workload (a cap and a masked ring crossing the limb, 60 deg
+    inclination), temperatures moved off the table nodes."""
+    w = synth.atm_two_spot(n_theta=16, n_phi=24, n_phase=32, n_E=64, n_chan=40, atm=atm,
+                           lens=small_lens)
+    w.inst.logT[0] = [6.112, 6.023]
+    ll, g, st = gpu_grad(w)
+    assert st[0] == 0
+    ref = oracle_fd(orc, w, rel=1e-5)
+    ref2 = oracle_fd(orc, w, rel=5e-6)
+    smooth = np.abs(ref - ref2) <= 1e-4 * np.abs(ref) + 1e-7 * np.max(np.abs(ref))
+    assert smooth.sum() >= 10, "finite differences straddle branch changes in %d components" % (
+        13 - smooth.sum())
+    _check(g[0, :13], ref, mask=smooth)
+
+
+def test_grad_one_spot_blackbody(orc, synth, small_lens):
+    """Analytic blackbody emission (the logT derivative through kT), one cap."""
+    w = synth.bb_small(n_theta=16, n_phi=20, n_phase=32, n_E=32, lens=small_lens)
+    w = synth._with_response(w, 24, tau=1.0e3)
+    w.inst.logT[0, 0] = 6.1
+    ll, g, st = gpu_grad(w)
+    assert st[0] == 0
+    ref = oracle_fd(orc, w, rel=1e-5)
+    assert n_params(w.inst) == 9
+    _check(g[0, :9], ref)
+    assert np.all(g[0, 9:] == 0.0)
+
+
+def test_grad_batch_matches_single_and_flags_out_of_range(synth, atm, small_lens):
+    w = visible_two_cap(synth, atm, small_lens, n_theta=12, n_phi=16, n_phase=32, n_E=48,
+                        n_chan=30)
+    inst = w.inst.select([0, 0, 0])
+    inst.n_theta[:] = [12, 20, 12]
+    inst.n_phi[:] = [16, 28, 16]
+    inst.mass_msun[2] = 2.2      # u = 0.54, beyond the lens grid
+    inst.incl_rad[1] = 40 * DEG
+    w3 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts] * 3), tau=w.tau)
+    ll, g, st = gpu_grad(w3)
+    assert list(st) == [0, 0, 2]
+    assert np.all(np.isnan(g[2])) and ll[2] == -np.inf
+    for b in range(2):
+        llb, gb, _ = gpu_grad(single(w3, b))
+        assert abs(ll[b] - llb[0]) <= 1e-6 * abs(llb[0])
+        assert np.all(np.abs(g[b] - gb[0]) <= grad_tol(gb[0], rtol=1e-5, floor=1e-7))
+
+
+def test_autograd_function(synth, atm, small_lens):
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    w = visible_two_cap(synth, atm, small_lens, n_theta=8, n_phi=12, n_phase=32, n_E=48,
+                        n_chan=30)
+    inst = w.inst.select([0, 0])
+    inst.incl_rad[1] = 35 * DEG
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts] * 2), tau=w.tau)
+    ctx = context(w2)
+    dp = ppm.DeviceParams(w2.inst)
+    cnt = torch.from_numpy(w2.counts).cuda()
+    theta = dp.theta().clone().requires_grad_(True)
+    ll = ppm.LogLikelihood(theta, ctx, dp, cnt, w2.tau)
+    (gt,) = torch.autograd.grad((ll * torch.tensor([1.0, -2.0], device="cuda",
+                                                   dtype=torch.float64)).sum(), theta)
+    _, g = ctx.loglike_grad(dp, cnt, w2.tau)
+    # two calls: the backward's shared-memory atomics make the last bits
+    # depend on scheduling
+    assert torch.allclose(gt[0], g[0], rtol=1e-6, atol=0)
+    assert torch.allclose(gt[1], -2.0 * g[1], rtol=1e-6, atol=0)
+
+
+def test_grad_full_size_directional(synth, atm):
+    """The differentiated workload's resolution (two caps, 128 x 128 elements,
+    128 phases, 256 energies, 300 channels, default lens grid): the gradient
+    against central differences of the GPU logL along three directions (the
+    forward is FP32, so the step is 1e-4 relative and the tolerance 1e-2)."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    w = visible_two_cap(synth, atm, None)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    _, g = ctx.loglike_grad(dp, cnt, w.tau)
+    g = g[0].cpu().numpy()
+    th0 = dp.theta()
+    sc = torch.tensor([1.0, 10.0, 1.0, 0.3, 1.0, 1.0, 1.0, 0.2, 6.0, 1.0, 1.0, 0.2, 6.0],
+                      dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        v = torch.from_numpy(rng.standard_normal(13)).cuda() * sc
+        h = 1e-4
+        lls = []
+        for sgn in (1.0, -1.0):
+            dp.set_theta(th0 + sgn * h * v)
+            lls.append(float(ctx.loglike(dp, cnt, w.tau)[0]))
+        dp.set_theta(th0)
+        fd = (lls[0] - lls[1]) / (2 * h)
+        gv = float(np.dot(g, v.cpu().numpy()))
+        assert abs(gv - fd) <= 1e-2 * abs(fd) + 1e-3 * float(np.sum(np.abs(g * v.cpu().numpy())))
