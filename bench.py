@@ -54,9 +54,18 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="atm_two_spot",
                     choices=["atm_two_spot", "bb_small", "crescent_extreme", "batch", "grad_batch"])
+    ap.add_argument("--batch", type=int, default=None,
+                    help="parameter vectors of the batch / grad_batch workloads")
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
+
+
+def make_workload(args):
+    from paper_2510_07764_gb300 import synth
+    if args.batch is not None and args.workload in ("batch", "grad_batch"):
+        return synth.WORKLOADS[args.workload](B=args.batch)
+    return synth.WORKLOADS[args.workload]()
 
 
 def workload_desc(w):
@@ -196,7 +205,7 @@ def run_reference(args, rank, world):
         return
     from paper_2510_07764_gb300 import synth
     import oracle
-    w = synth.WORKLOADS[args.workload]()
+    w = make_workload(args)
     grad_mode = args.workload == "grad_batch"
     mult = fd_evals(w) if grad_mode else 1
     times = []
@@ -233,7 +242,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.WORKLOADS[args.workload]()
+    w = make_workload(args)
     grad_mode = args.workload == "grad_batch"
     ctx = ppm.Context(local_rank)
     t0 = time.perf_counter()

@@ -52,14 +52,36 @@ __device__ __forceinline__ void cubic_set(Cubic &C, float a, float b, float c, f
     C.W3 = d;
 }
 
-__device__ __forceinline__ void cubic_shift(Cubic &C, float d)
-{
-    cubic_set(C, C.c0, C.W2, C.W3, d);
-}
-
 __device__ __forceinline__ float horner(const Cubic &C, float t)
 {
     return fmaf(t, fmaf(t, fmaf(t, C.c3, C.c2), C.c1), C.c0);
+}
+
+// the same for two interleaved cubics (packed FP32 pair arithmetic)
+struct Cubic2 {
+    float2 c0, c1, c2, c3, W2, W3;
+};
+
+__device__ __forceinline__ void cubic2_set(Cubic2 &C, float2 a, float2 b, float2 c, float2 d)
+{
+    const float2 h = make_float2(0.5f, 0.5f), s6 = make_float2(1.0f / 6.0f, 1.0f / 6.0f);
+    C.c0 = b;
+    C.c2 = __ffma2_rn(h, __fadd2_rn(a, c), make_float2(-b.x, -b.y));
+    C.c3 = __ffma2_rn(__fadd2_rn(d, make_float2(-a.x, -a.y)), s6,
+                      __fmul2_rn(h, __fadd2_rn(b, make_float2(-c.x, -c.y))));
+    C.c1 = __ffma2_rn(__fadd2_rn(c, make_float2(-a.x, -a.y)), h, make_float2(-C.c3.x, -C.c3.y));
+    C.W2 = c;
+    C.W3 = d;
+}
+
+__device__ __forceinline__ void cubic2_shift(Cubic2 &C, float2 d)
+{
+    cubic2_set(C, C.c0, C.W2, C.W3, d);
+}
+
+__device__ __forceinline__ float2 horner2(const Cubic2 &C, float2 t)
+{
+    return __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, C.c3, C.c2), C.c1), C.c0);
 }
 
 // state of one (element, phase) pair in the backward pass
@@ -291,7 +313,8 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
     const float *S = sm + lay.slab;
     const float *spk = sm + lay.pk;  // table positions (atmosphere) or energies (blackbody)
     const float *sE3 = sm + lay.E3;
-    float *arow = sm + lay.arow + warp * nEpad;
+    float *arow = sm + lay.arow + warp * 2 * nEpad;  // (table position or energy, adjoint) pairs
+    const float2 *parow = reinterpret_cast<const float2 *>(arow);
     const float pk0 = spk[0], pkl = spk[nE - 1];
     const float lz_safe = 1.25f - pk0;
     const bool sliding = en.sliding != 0;
@@ -304,7 +327,10 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
 
     for (int j = warp; j < ip.n_phase; j += kBwdBlock / 32) {
         const float *asrc = Aadj + (size_t)(ip.row0 + j) * nEpad;
-        for (int k = lane; k < nEpad; k += 32) arow[k] = asrc[k];
+        for (int k = lane; k < nEpad; k += 32) {
+            arow[2 * k] = spk[k];
+            arow[2 * k + 1] = asrc[k];
+        }
         __syncwarp();
         const float phi_out = (float)j * inv_nphase;
         for (int g0 = 0; g0 < n_act; g0 += 32) {
@@ -328,40 +354,48 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                     const float q = floorf(pk0 + lz);
                     float off = lz - q;
                     const float *sp = S + ((int)q + 2) * Pm + P.s0;
-                    Cubic cI, cM, cT, cG;
-                    cubic_set(cI, dot4(sp - 3 * Pm, a0, a1, a2, a3), dot4(sp - 2 * Pm, a0, a1, a2, a3),
-                              dot4(sp - Pm, a0, a1, a2, a3), dot4(sp, a0, a1, a2, a3));
-                    cubic_set(cM, dot4(sp - 3 * Pm, b0, b1, b2, b3), dot4(sp - 2 * Pm, b0, b1, b2, b3),
-                              dot4(sp - Pm, b0, b1, b2, b3), dot4(sp, b0, b1, b2, b3));
-                    cubic_set(cT, dot4(sp + offT - 3 * Pm, a0, a1, a2, a3),
-                              dot4(sp + offT - 2 * Pm, a0, a1, a2, a3),
-                              dot4(sp + offT - Pm, a0, a1, a2, a3), dot4(sp + offT, a0, a1, a2, a3));
-                    cubic_set(cG, dot4(sp + offG - 3 * Pm, a0, a1, a2, a3),
-                              dot4(sp + offG - 2 * Pm, a0, a1, a2, a3),
-                              dot4(sp + offG - Pm, a0, a1, a2, a3), dot4(sp + offG, a0, a1, a2, a3));
+                    // (I, I_mu) and (I_T, I_g) as packed pairs: one FFMA2 chain each
+                    auto nodeIM = [&](const float *r) {
+                        return make_float2(dot4(r, a0, a1, a2, a3), dot4(r, b0, b1, b2, b3));
+                    };
+                    auto nodeTG = [&](const float *r) {
+                        return make_float2(dot4(r + offT, a0, a1, a2, a3), dot4(r + offG, a0, a1, a2, a3));
+                    };
+                    Cubic2 cIM, cTG;
+                    cubic2_set(cIM, nodeIM(sp - 3 * Pm), nodeIM(sp - 2 * Pm), nodeIM(sp - Pm), nodeIM(sp));
+                    cubic2_set(cTG, nodeTG(sp - 3 * Pm), nodeTG(sp - 2 * Pm), nodeTG(sp - Pm), nodeTG(sp));
+                    float d1 = 2.0f * cIM.c2.x, d2 = 3.0f * cIM.c3.x;  // dI/dt coefficients
+                    float2 sFM = make_float2(0.f, 0.f), sTG = make_float2(0.f, 0.f);
+                    float sZa = 0.f;
+                    const float2 *pa = parow;
+#pragma unroll 2
                     for (int k = 0; k < nE; ++k) {
-                        float t = spk[k] + off;
+                        const float2 pka = pa[k];  // (table position, adjoint)
+                        float t = pka.x + off;
                         if (t >= 1.0f) {
                             sp += Pm;
-                            const float x0 = sp[0], x1 = sp[1], x2 = sp[2], x3 = sp[3];
-                            cubic_shift(cI, fmaf(a3, x3, fmaf(a2, x2, fmaf(a1, x1, a0 * x0))));
-                            cubic_shift(cM, fmaf(b3, x3, fmaf(b2, x2, fmaf(b1, x1, b0 * x0))));
-                            cubic_shift(cT, dot4(sp + offT, a0, a1, a2, a3));
-                            cubic_shift(cG, dot4(sp + offG, a0, a1, a2, a3));
+                            cubic2_shift(cIM, nodeIM(sp));
+                            cubic2_shift(cTG, nodeTG(sp));
+                            d1 = 2.0f * cIM.c2.x;
+                            d2 = 3.0f * cIM.c3.x;
                             off -= 1.0f;
                             t -= 1.0f;
                         }
-                        const float ak = arow[k];
-                        sF = fmaf(ak, horner(cI, t), sF);
-                        sZ = fmaf(ak, fmaf(t, fmaf(t, 3.0f * cI.c3, 2.0f * cI.c2), cI.c1), sZ);
-                        sMu = fmaf(ak, horner(cM, t), sMu);
-                        sT = fmaf(ak, horner(cT, t), sT);
-                        sG = fmaf(ak, horner(cG, t), sG);
+                        const float2 tt = make_float2(t, t), ak = make_float2(pka.y, pka.y);
+                        const float2 vIM = horner2(cIM, tt), vTG = horner2(cTG, tt);
+                        sFM = __ffma2_rn(ak, vIM, sFM);
+                        sTG = __ffma2_rn(ak, vTG, sTG);
+                        sZa = fmaf(pka.y, fmaf(t, fmaf(t, d2, d1), cIM.c1.x), sZa);
                     }
+                    sF = sFM.x;
+                    sMu = sFM.y;
+                    sT = sTG.x;
+                    sG = sTG.y;
+                    sZ = sZa;
                 } else if (P.on) {
                     for (int k = 0; k < nE; ++k) {
                         const Quint Q = bwd_general(P, S, S + offT, S + offG, Pm, A.nE, spk[k] + P.lz);
-                        const float ak = arow[k];
+                        const float ak = parow[k].y;
                         sF = fmaf(ak, Q.I, sF);
                         sZ = fmaf(ak, Q.dI, sZ);
                         sMu = fmaf(ak, Q.Im, sMu);
@@ -387,7 +421,7 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                         const float em = expm1f(x);
                         const float I0 = bz * sE3[k] / em;
                         const float r = x * (1.0f + 1.0f / em);
-                        const float ak = arow[k];
+                        const float ak = parow[k].y;
                         sF = fmaf(ak, I0, sF);
                         sR = fmaf(ak, I0 * r, sR);
                     }
@@ -457,7 +491,7 @@ BwdSizes bwd_layout(int emission, const PlanDev &plan, const AtmDev &A, const En
     lay.munodes = take(emission == 1 ? A.nmu : 0);
     lay.pk = take(en.nEpad);
     lay.E3 = take(emission == 1 ? 0 : en.nEpad);
-    lay.arow = take((kBwdBlock / 32) * en.nEpad);
+    lay.arow = take((kBwdBlock / 32) * 2 * en.nEpad);
     lay.adj = take(4 * (plan.n_fp + 1));
     lay.red = take(4);
     lay.slab = take(slab);
