@@ -20,18 +20,28 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ppm_oracle.c")
 _LIB = os.path.join(_HERE, "libppm_oracle.so")
+_SRC_T = os.path.join(_HERE, "ppm_oracle_tangent.c")
+_LIB_T = os.path.join(_HERE, "libppm_oracle_tangent.so")
 _lib = None
+_lib_t = None
 
 PI = math.pi
 
 
+def _compile(src, lib, std, force):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(src))
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = lib + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=" + std, "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, lib)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (double precision, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (double precision, no FMA contraction), and
+    its forward-mode (complex-step) build."""
+    _compile(_SRC, _LIB, "c99", force)
+    _compile(_SRC_T, _LIB_T, "c11", force)
     return _LIB
 
 
@@ -99,6 +109,31 @@ def lib():
         L.orc_loglike.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, d]
         _lib = L
     return _lib
+
+
+class _CD(C.Structure):
+    """C99 double complex (real part, imaginary part)."""
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class InstT(C.Structure):
+    """orc_inst of the tangent build: every real field is a complex pair."""
+    _fields_ = [(n, (_CD * t._length_) if hasattr(t, "_length_") else _CD)
+                if t in (C.c_double,) or (hasattr(t, "_type_") and t._type_ is C.c_double)
+                else (n, t) for n, t in InstC._fields_]
+
+
+def lib_tangent():
+    global _lib_t
+    if _lib_t is None:
+        build()
+        L = C.CDLL(_LIB_T)
+        L.orc_loglike_full.restype = C.c_int
+        L.orc_loglike_full.argtypes = [C.POINTER(InstT), C.POINTER(LensC), C.POINTER(AtmC),
+                                       C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]
+        _lib_t = L
+    return _lib_t
 
 
 def _ptr(a):
@@ -279,3 +314,65 @@ def loglike(Cm: np.ndarray, d: np.ndarray, tau: float, bkg: Optional[np.ndarray]
     d = np.ascontiguousarray(d, dtype=np.int32)
     bg = None if bkg is None else np.ascontiguousarray(bkg, dtype=np.float32)
     return lib().orc_loglike(_ptr(Cm), Cm.size, _ptr(d), _ptr(bg), float(tau))
+
+
+# ---------------------------------------------------------------------------
+# forward-mode derivatives (tangent build)
+# ---------------------------------------------------------------------------
+# differentiable parameters in the order of the GPU gradient
+GRAD_PARAMS = (("mass_msun", None), ("radius_km", None), ("incl_rad", None),
+               ("dist_kpc", None), ("nh_1e20", None),
+               ("colat", 0), ("azim", 0), ("zeta", 0), ("logT", 0),
+               ("colat", 1), ("azim", 1), ("zeta", 1), ("logT", 1))
+
+
+def loglike_tangent(w, v, b: int = 0, h: float = 1e-20):
+    """(logL, dlogL/dtheta . v) of instance b of w through the forward-mode
+    build of the oracle; v has one entry per GRAD_PARAMS entry (13; the last
+    four are ignored for one spot)."""
+    inst = w.inst
+    ic = InstT()
+    base = inst_c(inst, b)
+    for name, t in InstC._fields_:
+        val = getattr(base, name)
+        if t is C.c_double:
+            getattr(ic, name).re = val
+        elif hasattr(t, "_type_") and t._type_ is C.c_double:
+            arr = getattr(ic, name)
+            for s in range(len(arr)):
+                arr[s].re = val[s]
+        else:
+            setattr(ic, name, val)
+    for (name, s), vj in zip(GRAD_PARAMS, v):
+        if s is None:
+            getattr(ic, name).im = h * float(vj)
+        elif s < inst.n_spots:
+            getattr(ic, name)[s].im = h * float(vj)
+    L = lens(w.lens)
+    A = Atm(w.atm) if inst.emission == 1 else None
+    E = np.ascontiguousarray(w.E_keV, dtype=np.float64)
+    R = np.ascontiguousarray(w.R, dtype=np.float32)
+    sg = np.ascontiguousarray(w.sigma_ism, dtype=np.float32)
+    r0 = int(np.sum(inst.n_phase[:b]))
+    d = np.ascontiguousarray(w.counts[r0:r0 + int(inst.n_phase[b])], dtype=np.int32)
+    out = np.zeros(2)
+    st = lib_tangent().orc_loglike_full(C.byref(ic), C.byref(L.c), C.byref(A.c) if A else None,
+                                        _ptr(E), len(E), _ptr(R), R.shape[1], _ptr(sg),
+                                        _ptr(d), None, float(w.tau), _ptr(out))
+    if st == 2:
+        raise OracleRangeError("parameters outside the lens or atmosphere tables")
+    if st != 0:
+        raise ValueError("oracle rejected the instance (status %d)" % st)
+    return out[0], out[1] / h
+
+
+def grad_tangent(w, b: int = 0):
+    """Gradient of logL (GRAD_PARAMS order) by forward mode, one direction per
+    parameter."""
+    n = 5 + 4 * w.inst.n_spots
+    g = np.zeros(n)
+    for j in range(n):
+        e = np.zeros(13)
+        e[j] = 1.0
+        g[j] = loglike_tangent(w, e, b)[1]
+    return g

@@ -27,10 +27,73 @@
  *
  * Where the paper is silent the reading is stated next to the code.
  * Compile with -ffp-contract=off so x86 and Arm builds round identically.
+ *
+ * Forward-mode derivatives.  Everything downstream of the parameters is
+ * written in the type `real`.  The ordinary build has real = double.  The
+ * tangent build (ppm_oracle_tangent.c: ORC_CSTEP defined, then this file
+ * included) has real = double complex and seeds a parameter p as
+ * p + i h v_p with h ~ 1e-20 |p|: the imaginary parts then carry h times
+ * the directional derivative along v, exactly to rounding, because every
+ * product of two imaginary parts (order h^2) vanishes against the real parts
+ * (the complex-step method of Squire & Trapp 1998; Martins, Sturdza & Alonso
+ * 2003).  Elementary functions take their first-order expansion
+ * f(a + ib) = f(a) + i b f'(a); branches, comparisons, floors and clamps act
+ * on the real part only, so the derivative is that of the same
+ * piecewise-smooth function the ordinary build evaluates.  The lens tables
+ * and the quadrature do not depend on the parameters and stay double.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef ORC_CSTEP
+#include <complex.h>
+#undef I /* the imaginary unit macro; this file names intensities I */
+typedef double complex real;
+static double RE(real x) { return creal(x); }
+static double IM(real x) { return cimag(x); }
+static real mk(double a, double b) { return CMPLX(a, b); }
+static real r_sqrt(real x)
+{
+    double a = creal(x), s = sqrt(a);
+    return mk(s, s > 0.0 ? cimag(x) * 0.5 / s : 0.0);
+}
+static real r_sin(real x) { return mk(sin(creal(x)), cimag(x) * cos(creal(x))); }
+static real r_cos(real x) { return mk(cos(creal(x)), -cimag(x) * sin(creal(x))); }
+static real r_acos(real x)
+{
+    double a = creal(x);
+    return mk(acos(a), -cimag(x) / sqrt(1.0 - a * a));
+}
+static real r_log(real x) { return mk(log(creal(x)), cimag(x) / creal(x)); }
+static real r_log10(real x) { return mk(log10(creal(x)), cimag(x) / (creal(x) * log(10.0))); }
+static real r_exp(real x)
+{
+    double e = exp(creal(x));
+    return mk(e, cimag(x) * e);
+}
+static real r_expm1(real x) { return mk(expm1(creal(x)), cimag(x) * exp(creal(x))); }
+static real r_pow(double base, real x)
+{
+    double v = pow(base, creal(x));
+    return mk(v, cimag(x) * v * log(base));
+}
+static real r_fabs(real x) { return creal(x) < 0.0 ? -x : x; }
+#else
+typedef double real;
+#define RE(x) (x)
+#define IM(x) (0.0)
+#define r_sqrt sqrt
+#define r_sin sin
+#define r_cos cos
+#define r_acos acos
+#define r_log log
+#define r_log10 log10
+#define r_exp exp
+#define r_expm1 expm1
+#define r_pow pow
+#define r_fabs fabs
+#endif
 
 /* ---- physical constants (CODATA 2018, IAU 2015 nominal GM_sun) ---- */
 #define ORC_PI 3.14159265358979323846
@@ -278,17 +341,17 @@ int orc_lens_build(const orc_lens_spec *sp, double *Ca, double *LF, double *TD)
 
 /* Bilinear lookup of C_alpha and LF at (u, cos psi) (reading: bilinear).
  * Returns 1 if all four corners are valid, 0 otherwise (point invisible). */
-int orc_lens_lookup(const orc_lens *L, double u, double cpsi, double *ca, double *lf)
+int orc_lens_lookup(const orc_lens *L, real u, real cpsi, real *ca, real *lf)
 {
     const orc_lens_spec *s = &L->spec;
-    double fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
-    double fc = (cpsi - s->cpsi_min) / (s->cpsi_max - s->cpsi_min) * (s->n_cpsi - 1);
-    int iu = (int)floor(fu), ic = (int)floor(fc);
+    real fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
+    real fc = (cpsi - s->cpsi_min) / (s->cpsi_max - s->cpsi_min) * (s->n_cpsi - 1);
+    int iu = (int)floor(RE(fu)), ic = (int)floor(RE(fc));
     if (iu < 0) iu = 0;
     if (iu > s->n_u - 2) iu = s->n_u - 2;
     if (ic < 0) ic = 0;
     if (ic > s->n_cpsi - 2) ic = s->n_cpsi - 2;
-    double tu = fu - iu, tc = fc - ic;
+    real tu = fu - iu, tc = fc - ic;
     size_t k00 = (size_t)iu * s->n_cpsi + ic, k10 = k00 + s->n_cpsi;
     double a00 = L->Ca[k00], a01 = L->Ca[k00 + 1], a10 = L->Ca[k10], a11 = L->Ca[k10 + 1];
     double d00 = L->LF[k00], d01 = L->LF[k00 + 1], d10 = L->LF[k10], d11 = L->LF[k10 + 1];
@@ -299,19 +362,19 @@ int orc_lens_lookup(const orc_lens *L, double u, double cpsi, double *ca, double
 }
 
 /* Bilinear lookup of TD at (u, cos alpha); cos alpha is clamped to the grid. */
-double orc_td_lookup(const orc_lens *L, double u, double calpha)
+real orc_td_lookup(const orc_lens *L, real u, real calpha)
 {
     const orc_lens_spec *s = &L->spec;
-    if (calpha < s->calpha_min) calpha = s->calpha_min;
-    if (calpha > s->calpha_max) calpha = s->calpha_max;
-    double fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
-    double fc = (calpha - s->calpha_min) / (s->calpha_max - s->calpha_min) * (s->n_calpha - 1);
-    int iu = (int)floor(fu), ic = (int)floor(fc);
+    if (RE(calpha) < s->calpha_min) calpha = s->calpha_min;
+    if (RE(calpha) > s->calpha_max) calpha = s->calpha_max;
+    real fu = (u - s->u_min) / (s->u_max - s->u_min) * (s->n_u - 1);
+    real fc = (calpha - s->calpha_min) / (s->calpha_max - s->calpha_min) * (s->n_calpha - 1);
+    int iu = (int)floor(RE(fu)), ic = (int)floor(RE(fc));
     if (iu < 0) iu = 0;
     if (iu > s->n_u - 2) iu = s->n_u - 2;
     if (ic < 0) ic = 0;
     if (ic > s->n_calpha - 2) ic = s->n_calpha - 2;
-    double tu = fu - iu, tc = fc - ic;
+    real tu = fu - iu, tc = fc - ic;
     size_t k00 = (size_t)iu * s->n_calpha + ic, k10 = k00 + s->n_calpha;
     return (1.0 - tu) * ((1.0 - tc) * L->TD[k00] + tc * L->TD[k00 + 1]) +
            tu * ((1.0 - tc) * L->TD[k10] + tc * L->TD[k10 + 1]);
@@ -327,14 +390,14 @@ typedef struct {
 } orc_atm;
 
 /* interval index i with x[i] <= q < x[i+1] after clamping q to [x0, x_{n-1}] */
-static int find_interval(const double *x, int n, double *q)
+static int find_interval(const double *x, int n, real *q)
 {
-    if (*q <= x[0]) { *q = x[0]; return 0; }
-    if (*q >= x[n - 1]) { *q = x[n - 1]; return n - 2; }
+    if (RE(*q) <= x[0]) { *q = x[0]; return 0; }
+    if (RE(*q) >= x[n - 1]) { *q = x[n - 1]; return n - 2; }
     int lo = 0, hi = n - 1;
     while (hi - lo > 1) {
         int mid = (lo + hi) / 2;
-        if (x[mid] <= *q) lo = mid; else hi = mid;
+        if (x[mid] <= RE(*q)) lo = mid; else hi = mid;
     }
     return lo;
 }
@@ -344,14 +407,14 @@ static int find_interval(const double *x, int n, double *q)
  * i-1..i+2 around interval i (actual node positions); falls back to linear
  * on (i, i+1) when the interval lies in the protected zone (i < n_protect-1)
  * or when the four-node stencil would leave the grid. */
-static int axis_weights(const double *x, int n, double q, int cubic, int n_protect,
-                        int *idx, double *w)
+static int axis_weights(const double *x, int n, real q, int cubic, int n_protect,
+                        int *idx, real *w)
 {
     int i = find_interval(x, n, &q);
     if (cubic && i >= 1 && i + 2 <= n - 1 && i >= n_protect - 1) {
         for (int a = 0; a < 4; a++) {
             int ka = i - 1 + a;
-            double l = 1.0;
+            real l = 1.0;
             for (int b = 0; b < 4; b++) {
                 if (b == a) continue;
                 int kb = i - 1 + b;
@@ -362,7 +425,7 @@ static int axis_weights(const double *x, int n, double q, int cubic, int n_prote
         }
         return 4;
     }
-    double t = (q - x[i]) / (x[i + 1] - x[i]);
+    real t = (q - x[i]) / (x[i + 1] - x[i]);
     idx[0] = i; w[0] = 1.0 - t;
     idx[1] = i + 1; w[1] = t;
     return 2;
@@ -370,15 +433,15 @@ static int axis_weights(const double *x, int n, double q, int cubic, int n_prote
 
 /* I(E', mu; logT, logg): linear in logT and logg, cubic (mixed) in mu and ln E.
  * Out-of-range queries clamp to the edge node; negative interpolants are kept. */
-double orc_atm_interp(const orc_atm *A, double logT, double logg, double mu, double E_keV)
+real orc_atm_interp(const orc_atm *A, real logT, real logg, real mu, real E_keV)
 {
     int iT[4], ig[4], im[4], ie[4];
-    double wT[4], wg[4], wm[4], we[4];
+    real wT[4], wg[4], wm[4], we[4];
     int nT = axis_weights(A->logT, A->nT, logT, 0, 0, iT, wT);
     int ng = axis_weights(A->logg, A->ng, logg, 0, 0, ig, wg);
     int nm = axis_weights(A->mu, A->nmu, mu, 1, A->n_protect, im, wm);
-    int ne = axis_weights(A->lnE, A->nE, log(E_keV), 1, 0, ie, we);
-    double v = 0.0;
+    int ne = axis_weights(A->lnE, A->nE, r_log(E_keV), 1, 0, ie, we);
+    real v = 0.0;
     for (int a = 0; a < nT; a++)
         for (int b = 0; b < ng; b++)
             for (int c = 0; c < nm; c++)
@@ -391,23 +454,23 @@ double orc_atm_interp(const orc_atm *A, double logT, double logg, double mu, dou
 
 /* comoving blackbody specific intensity 2 E^3 / (h^3 c^2) / (e^{E/kT} - 1)
  * in keV cm^-2 s^-1 keV^-1 sr^-1 (App. C) */
-double orc_bb_intensity(double E_keV, double kT_keV)
+real orc_bb_intensity(real E_keV, real kT_keV)
 {
     return 2.0 * E_keV * E_keV * E_keV / (H_KEVS * H_KEVS * H_KEVS * C_CMS * C_CMS) /
-           expm1(E_keV / kT_keV);
+           r_expm1(E_keV / kT_keV);
 }
 
 /* =====================================================================
  * Star, rings, elements (Sect. 2.1, 2.2, 2.4, 2.6)
  * ===================================================================== */
 typedef struct {
-    double mass_msun, radius_km, spin_hz, incl_rad, dist_kpc, nh_1e20;
-    double colat[2], azim[2], zeta[2], logT[2], mask_colat[2], mask_azim[2], mask_zeta[2];
+    real mass_msun, radius_km, spin_hz, incl_rad, dist_kpc, nh_1e20;
+    real colat[2], azim[2], zeta[2], logT[2], mask_colat[2], mask_azim[2], mask_zeta[2];
     int n_spots, oblate, emission, n_theta, n_phi, n_phase, n_fp;
 } orc_inst;
 
 typedef struct {
-    double GM, Rs, Re, nu, Obar, x, o2, g0, sini, cosi, D;
+    real GM, Rs, Re, nu, Obar, x, o2, g0, sini, cosi, D;
     int oblate;
 } orc_star;
 
@@ -417,84 +480,86 @@ static void star_init(const orc_inst *in, orc_star *s)
     s->Rs = 2.0 * s->GM / (C_MS * C_MS);
     s->Re = in->radius_km * 1e3;
     s->nu = in->spin_hz;
-    s->Obar = 2.0 * ORC_PI * s->nu * sqrt(s->Re * s->Re * s->Re / s->GM);  /* Eq. Omega_c_def */
+    s->Obar = 2.0 * ORC_PI * s->nu * r_sqrt(s->Re * s->Re * s->Re / s->GM);  /* Eq. Omega_c_def */
     s->x = s->GM / (C_MS * C_MS * s->Re);
     s->oblate = in->oblate;
     /* Eq. Rtheta; the S+D mode is the spherical star o2 = 0 */
     s->o2 = in->oblate ? s->Obar * s->Obar * (-0.788 + 1.030 * s->x) : 0.0;
-    s->g0 = s->GM / (s->Re * s->Re) / sqrt(1.0 - s->Rs / s->Re);
-    s->sini = sin(in->incl_rad);
-    s->cosi = cos(in->incl_rad);
+    s->g0 = s->GM / (s->Re * s->Re) / r_sqrt(1.0 - s->Rs / s->Re);
+    s->sini = r_sin(in->incl_rad);
+    s->cosi = r_cos(in->incl_rad);
     s->D = in->dist_kpc * KPC_M;
 }
 
 typedef struct {
-    double theta, dcos, R, u, f, cos_eta, sin_eta, logg, beta, gamma;
+    real theta, dcos, R, u, f, cos_eta, sin_eta, logg, beta, gamma;
 } orc_ring;
 
 /* Ring quantities at colatitude theta (Eqs. Rtheta, def_f, the g(theta)
  * polynomial of Sect. 2.2, beta/gamma of Sect. 2.4).  Readings: R and u are
  * the local R(theta), u(theta) (Omega_bar and x use R_e); dR/dtheta =
  * -2 o2 R_e cos(theta) sin(theta); in the S+D mode g = g0. */
-static void ring_geom(const orc_star *s, double theta, double dcos, orc_ring *r)
+static void ring_geom(const orc_star *s, real theta, real dcos, orc_ring *r)
 {
-    double ct = cos(theta), st = sin(theta);
+    real ct = r_cos(theta), st = r_sin(theta);
     r->theta = theta;
     r->dcos = dcos;
     r->R = s->Re * (1.0 + s->o2 * ct * ct);
     r->u = s->Rs / r->R;
-    double dRdth = -2.0 * s->o2 * s->Re * ct * st;
-    r->f = dRdth / (r->R * sqrt(1.0 - r->u));
-    r->cos_eta = 1.0 / sqrt(1.0 + r->f * r->f);
-    r->sin_eta = r->f / sqrt(1.0 + r->f * r->f);
-    double g = s->g0;
+    real dRdth = -2.0 * s->o2 * s->Re * ct * st;
+    r->f = dRdth / (r->R * r_sqrt(1.0 - r->u));
+    r->cos_eta = 1.0 / r_sqrt(1.0 + r->f * r->f);
+    r->sin_eta = r->f / r_sqrt(1.0 + r->f * r->f);
+    real g = s->g0;
     if (s->oblate) {
-        double O2 = s->Obar * s->Obar, O4 = O2 * O2, O6 = O4 * O2, x = s->x;
-        double c2 = ct * ct, s2 = st * st;
-        double ratio = 1.0
+        real O2 = s->Obar * s->Obar, O4 = O2 * O2, O6 = O4 * O2, x = s->x;
+        real c2 = ct * ct, s2 = st * st;
+        real ratio = 1.0
             + s2 * (O2 * (-0.791 + 0.776 * x) + O4 * (-1.315 * x + 2.431 * x * x) + O6 * (-1.172 * x))
             + c2 * (O2 * (1.138 - 1.431 * x) + O4 * (0.653 * x - 2.864 * x * x) + O6 * (0.975 * x)
                     - O4 * (13.47 * x - 27.13 * x * x))
-            + fabs(ct) * O4 * (13.47 * x - 27.13 * x * x);
+            + r_fabs(ct) * O4 * (13.47 * x - 27.13 * x * x);
         g = s->g0 * ratio;
     }
-    r->logg = log10(g * 100.0); /* m s^-2 -> cm s^-2 */
-    r->beta = 2.0 * ORC_PI * s->nu * r->R * st / (C_MS * sqrt(1.0 - r->u));
-    r->gamma = 1.0 / sqrt(1.0 - r->beta * r->beta);
+    r->logg = r_log10(g * 100.0); /* m s^-2 -> cm s^-2 */
+    r->beta = 2.0 * ORC_PI * s->nu * r->R * st / (C_MS * r_sqrt(1.0 - r->u));
+    r->gamma = 1.0 / r_sqrt(1.0 - r->beta * r->beta);
 }
 
 /* Element grid of one spot (reading): n_theta rings uniform in theta over
  * [max(0, theta_c - zeta), min(pi, theta_c + zeta)]; each ring holds n_phi
  * elements uniform over the emitter's azimuth span phi_c +- Delta_i; an
  * element is active unless its centre lies inside the spot's masking cap. */
-static void ring_of_spot(const orc_inst *in, int spot, int r, double *theta,
-                         double *dcos, double *half)
+static void ring_of_spot(const orc_inst *in, int spot, int r, real *theta,
+                         real *dcos, real *half)
 {
-    double tc = in->colat[spot], z = in->zeta[spot];
-    double lo = tc - z > 0.0 ? tc - z : 0.0;
-    double hi = tc + z < ORC_PI ? tc + z : ORC_PI;
-    double dth = (hi - lo) / in->n_theta;
-    double e0 = lo + r * dth, e1 = lo + (r + 1) * dth;
+    real tc = in->colat[spot], z = in->zeta[spot];
+    real lo = RE(tc - z) > 0.0 ? tc - z : 0.0;
+    real hi = RE(tc + z) < ORC_PI ? tc + z : ORC_PI;
+    real dth = (hi - lo) / in->n_theta;
+    real e0 = lo + r * dth, e1 = lo + (r + 1) * dth;
     *theta = lo + (r + 0.5) * dth;
-    *dcos = cos(e0) - cos(e1);
-    double num = cos(z) - cos(*theta) * cos(tc);
-    double den = sin(*theta) * sin(tc);
-    if (den <= 0.0) {
-        *half = num <= 0.0 ? ORC_PI : 0.0;
+    *dcos = r_cos(e0) - r_cos(e1);
+    real num = r_cos(z) - r_cos(*theta) * r_cos(tc);
+    real den = r_sin(*theta) * r_sin(tc);
+    if (RE(den) <= 0.0) {
+        *half = RE(num) <= 0.0 ? ORC_PI : 0.0;
     } else {
-        double a = num / den;
-        if (a < -1.0) a = -1.0;
-        if (a > 1.0) a = 1.0;
-        *half = acos(a);
+        real a = num / den;
+        if (RE(a) < -1.0) a = -1.0;
+        if (RE(a) > 1.0) a = 1.0;
+        *half = r_acos(a);
     }
 }
 
-static int element_active(const orc_inst *in, int spot, double theta, double phi)
+/* a decision only: evaluated on the real parts */
+static int element_active(const orc_inst *in, int spot, real theta_r, real phi_r)
 {
-    double mz = in->mask_zeta[spot];
+    double mz = RE(in->mask_zeta[spot]);
     if (!(mz > 0.0)) return 1;
-    double cd = cos(theta) * cos(in->mask_colat[spot]) +
-                sin(theta) * sin(in->mask_colat[spot]) * cos(phi - in->mask_azim[spot]);
+    double theta = RE(theta_r), phi = RE(phi_r);
+    double cd = cos(theta) * cos(RE(in->mask_colat[spot])) +
+                sin(theta) * sin(RE(in->mask_colat[spot])) * cos(phi - RE(in->mask_azim[spot]));
     return !(cd > cos(mz));
 }
 
@@ -504,18 +569,18 @@ static int element_active(const orc_inst *in, int spot, double theta, double phi
  * Returns 1 if the ring contributes, 0 if it is invisible at i_fp = 0
  * (whole ring skipped), -1 if u lies outside the lens table.
  * ===================================================================== */
-static int ring_template(const orc_star *s, const orc_ring *rg, double dphi,
-                         const orc_lens *L, int n_fp, double *F, double *z,
-                         double *phio, double *mu)
+static int ring_template(const orc_star *s, const orc_ring *rg, real dphi,
+                         const orc_lens *L, int n_fp, real *F, real *z,
+                         real *phio, real *mu)
 {
     const orc_lens_spec *ls = &L->spec;
-    if (rg->u < ls->u_min || rg->u > ls->u_max) return -1;
-    double st = sin(rg->theta), ct = cos(rg->theta);
-    double sq = sqrt(1.0 - rg->u);
+    if (RE(rg->u) < ls->u_min || RE(rg->u) > ls->u_max) return -1;
+    real st = r_sin(rg->theta), ct = r_cos(rg->theta);
+    real sq = r_sqrt(1.0 - rg->u);
     /* area element R^2 sqrt(1+f^2) dcos(theta) dphi / D^2 (Eq. area_oblate) */
-    double area = rg->R * rg->R * sqrt(1.0 + rg->f * rg->f) * rg->dcos * dphi / (s->D * s->D);
+    real area = rg->R * rg->R * r_sqrt(1.0 + rg->f * rg->f) * rg->dcos * dphi / (s->D * s->D);
     /* radial delay of emission radius R relative to R_e (Eq. delta_t_oblate) */
-    double dt_obl = (s->Re - rg->R + s->Rs * log((s->Re - s->Rs) / (rg->R - s->Rs))) / C_MS;
+    real dt_obl = (s->Re - rg->R + s->Rs * r_log((s->Re - s->Rs) / (rg->R - s->Rs))) / C_MS;
     int inv_min = n_fp, inv_max = 0;
     int vis0 = 0;
     for (int i = 0; i <= n_fp; i++) {
@@ -532,27 +597,28 @@ static int ring_template(const orc_star *s, const orc_ring *rg, double dphi,
         double phi = 2.0 * ORC_PI * (double)i / (double)n_fp;
         double cphi = cos(phi), sphi = sin(phi);
         /* step 2: cos psi */
-        double cpsi = s->sini * st * cphi + s->cosi * ct;
+        real cpsi = s->sini * st * cphi + s->cosi * ct;
         int visible = 0;
-        double ca, lf;
+        real ca, lf;
         /* step 3: lens lookup; points beyond the cos psi grid are invisible */
-        if (cpsi >= ls->cpsi_min && orc_lens_lookup(L, rg->u, cpsi, &ca, &lf)) {
-            double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
-            double sp = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
+        if (RE(cpsi) >= ls->cpsi_min && orc_lens_lookup(L, rg->u, cpsi, &ca, &lf)) {
+            real one_ca2 = 1.0 - ca * ca, one_cp2 = 1.0 - cpsi * cpsi;
+            real sa = r_sqrt(RE(one_ca2) > 0.0 ? one_ca2 : 0.0);
+            real sp = r_sqrt(RE(one_cp2) > 0.0 ? one_cp2 : 0.0);
             /* sin(alpha)/sin(psi); limit sqrt(LF) as psi -> 0 (reading) */
-            double ratio = sp > 1e-12 ? sa / sp : sqrt(lf);
+            real ratio = RE(sp) > 1e-12 ? sa / sp : r_sqrt(lf);
             /* step 4: Eq. sigma_relation */
-            double csig = ca * rg->cos_eta +
-                          ratio * rg->sin_eta * (s->cosi * st - s->sini * ct * cphi);
+            real csig = ca * rg->cos_eta +
+                        ratio * rg->sin_eta * (s->cosi * st - s->sini * ct * cphi);
             /* step 5 */
-            if (csig >= 0.0) {
+            if (RE(csig) >= 0.0) {
                 visible = 1;
-                double cxi = -ratio * s->sini * sphi;          /* Table tab:angles */
-                double delta = 1.0 / (rg->gamma * (1.0 - rg->beta * cxi));
-                double m = delta * csig;                        /* mu = cos sigma' */
+                real cxi = -ratio * s->sini * sphi;            /* Table tab:angles */
+                real delta = 1.0 / (rg->gamma * (1.0 - rg->beta * cxi));
+                real m = delta * csig;                          /* mu = cos sigma' */
                 F[i] = sq * delta * delta * delta * m * lf * rg->gamma * area;
                 z[i] = 1.0 / (delta * sq);
-                double dt = rg->R / C_MS * orc_td_lookup(L, rg->u, ca) + dt_obl;
+                real dt = rg->R / C_MS * orc_td_lookup(L, rg->u, ca) + dt_obl;
                 phio[i] = (double)i / (double)n_fp + s->nu * dt;
                 mu[i] = m;
             }
@@ -583,26 +649,26 @@ static int ring_template(const orc_star *s, const orc_ring *rg, double dphi,
  * ===================================================================== */
 
 /* floor-mod into [0, 1) */
-static double frac1(double x) { return x - floor(x); }
+static real frac1(real x) { return x - floor(RE(x)); }
 
 /* Linear interpolation of the template at phase phip (reading: linear,
  * binary search on the monotone phi_o). */
-static void template_at(const double *phio, const double *F, const double *z,
-                        const double *mu, int n_fp, double phip,
-                        double *Fp, double *zp, double *mup)
+static void template_at(const real *phio, const real *F, const real *z,
+                        const real *mu, int n_fp, real phip,
+                        real *Fp, real *zp, real *mup)
 {
     int lo = 0, hi = n_fp;
-    if (phip <= phio[0]) hi = 1;
-    else if (phip >= phio[n_fp]) lo = n_fp - 1;
+    if (RE(phip) <= RE(phio[0])) hi = 1;
+    else if (RE(phip) >= RE(phio[n_fp])) lo = n_fp - 1;
     else {
         while (hi - lo > 1) {
             int mid = (lo + hi) / 2;
-            if (phio[mid] <= phip) lo = mid; else hi = mid;
+            if (RE(phio[mid]) <= RE(phip)) lo = mid; else hi = mid;
         }
     }
-    double w = (phip - phio[lo]) / (phio[lo + 1] - phio[lo]);
-    if (w < 0.0) w = 0.0;
-    if (w > 1.0) w = 1.0;
+    real w = (phip - phio[lo]) / (phio[lo + 1] - phio[lo]);
+    if (RE(w) < 0.0) w = 0.0;
+    if (RE(w) > 1.0) w = 1.0;
     *Fp = F[lo] + (F[lo + 1] - F[lo]) * w;
     *zp = z[lo] + (z[lo + 1] - z[lo]) * w;
     *mup = mu[lo] + (mu[lo + 1] - mu[lo]) * w;
@@ -617,7 +683,7 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ERANGE = 2 };
  * (used to time a bounded sample).  Ft has n_j * n_k entries, row-major. */
 int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
                 const double *E_keV, int nE, const int *jsel, int nj,
-                const int *ksel, int nk, int ring_stride, double *Ft)
+                const int *ksel, int nk, int ring_stride, real *Ft)
 {
     if (in->n_spots < 1 || in->n_spots > 2 || in->n_theta < 1 || in->n_phi < 1 ||
         in->n_phase < 1 || in->n_fp < 2 || nE < 1)
@@ -626,52 +692,53 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
     if (ring_stride < 1) ring_stride = 1;
     int NJ = jsel ? nj : in->n_phase;
     int NK = ksel ? nk : nE;
-    memset(Ft, 0, sizeof(double) * (size_t)NJ * NK);
+    for (size_t q = 0; q < (size_t)NJ * NK; q++) Ft[q] = 0.0;
     orc_star s;
     star_init(in, &s);
     int n_fp = in->n_fp;
-    double *F = (double *)malloc(sizeof(double) * (n_fp + 1));
-    double *z = (double *)malloc(sizeof(double) * (n_fp + 1));
-    double *ph = (double *)malloc(sizeof(double) * (n_fp + 1));
-    double *mu = (double *)malloc(sizeof(double) * (n_fp + 1));
+    real *F = (real *)malloc(sizeof(real) * (n_fp + 1));
+    real *z = (real *)malloc(sizeof(real) * (n_fp + 1));
+    real *ph = (real *)malloc(sizeof(real) * (n_fp + 1));
+    real *mu = (real *)malloc(sizeof(real) * (n_fp + 1));
     int status = ORC_OK;
     for (int sp = 0; sp < in->n_spots && status == ORC_OK; sp++) {
-        double logT = in->logT[sp];
-        double kT = KB_KEVK * pow(10.0, logT);
-        if (in->emission == 1 && (logT < A->logT[0] || logT > A->logT[A->nT - 1])) {
+        real logT = in->logT[sp];
+        real kT = KB_KEVK * r_pow(10.0, logT);
+        if (in->emission == 1 && (RE(logT) < A->logT[0] || RE(logT) > A->logT[A->nT - 1])) {
             status = ORC_ERANGE;
             break;
         }
         for (int r = 0; r < in->n_theta; r += ring_stride) {
-            double theta, dcos, half;
+            real theta, dcos, half;
             ring_of_spot(in, sp, r, &theta, &dcos, &half);
-            if (!(half > 0.0)) continue;
+            if (!(RE(half) > 0.0)) continue;
             orc_ring rg;
             ring_geom(&s, theta, dcos, &rg);
-            if (in->emission == 1 && (rg.logg < A->logg[0] || rg.logg > A->logg[A->ng - 1])) {
+            if (in->emission == 1 &&
+                (RE(rg.logg) < A->logg[0] || RE(rg.logg) > A->logg[A->ng - 1])) {
                 status = ORC_ERANGE;
                 break;
             }
-            double dphi = 2.0 * half / in->n_phi;
+            real dphi = 2.0 * half / in->n_phi;
             int tv = ring_template(&s, &rg, dphi, L, n_fp, F, z, ph, mu);
             if (tv < 0) { status = ORC_ERANGE; break; }
             if (tv == 0) continue;
             for (int m = 0; m < in->n_phi; m++) {
-                double phia = in->azim[sp] - half + (m + 0.5) * dphi;
+                real phia = in->azim[sp] - half + (m + 0.5) * dphi;
                 if (!element_active(in, sp, theta, phia)) continue;
-                double sm = phia / (2.0 * ORC_PI);
+                real sm = phia / (2.0 * ORC_PI);
                 for (int jj = 0; jj < NJ; jj++) {
                     int j = jsel ? jsel[jj] : jj;
                     double phi_out = (double)j / (double)in->n_phase;
-                    double phip = frac1(phi_out + sm + 1.0 - ph[0]) + ph[0];
-                    double Fp, zp, mup;
+                    real phip = frac1(phi_out + sm + 1.0 - ph[0]) + ph[0];
+                    real Fp, zp, mup;
                     template_at(ph, F, z, mu, n_fp, phip, &Fp, &zp, &mup);
-                    if (Fp == 0.0) continue;
+                    if (RE(Fp) == 0.0) continue;
                     for (int kk = 0; kk < NK; kk++) {
                         int k = ksel ? ksel[kk] : kk;
                         double E = E_keV[k];
-                        double Ep = zp * E;
-                        double I = (in->emission == 1)
+                        real Ep = zp * E;
+                        real I = (in->emission == 1)
                                        ? orc_atm_interp(A, logT, rg.logg, mup, Ep)
                                        : orc_bb_intensity(Ep, kT);
                         Ft[(size_t)jj * NK + kk] += Fp * I / E;
@@ -692,17 +759,26 @@ int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
 {
     orc_star s;
     star_init(in, &s);
-    double theta, dcos, half;
+    real theta, dcos, half;
     ring_of_spot(in, spot, r, &theta, &dcos, &half);
     orc_ring rg;
     ring_geom(&s, theta, dcos, &rg);
-    double dphi = 2.0 * half / in->n_phi;
+    real dphi = 2.0 * half / in->n_phi;
     int nact = 0;
     for (int m = 0; m < in->n_phi; m++)
         nact += element_active(in, spot, theta, in->azim[spot] - half + (m + 0.5) * dphi);
-    int st = half > 0.0 ? ring_template(&s, &rg, dphi, L, in->n_fp, F, z, phio, mu) : 0;
-    double v[14] = {rg.theta, rg.dcos, half, rg.R, rg.u, rg.f, rg.cos_eta, rg.sin_eta,
-                    rg.logg, rg.beta, rg.gamma, dphi, (double)nact, (double)st};
+    int n = in->n_fp + 1;
+    real *t = (real *)malloc(sizeof(real) * 4 * n);
+    int st = RE(half) > 0.0 ? ring_template(&s, &rg, dphi, L, in->n_fp, t, t + n, t + 2 * n,
+                                            t + 3 * n)
+                            : 0;
+    for (int i = 0; i < n && RE(half) > 0.0; i++) {
+        F[i] = RE(t[i]); z[i] = RE(t[n + i]); phio[i] = RE(t[2 * n + i]); mu[i] = RE(t[3 * n + i]);
+    }
+    free(t);
+    double v[14] = {RE(rg.theta), RE(rg.dcos), RE(half), RE(rg.R), RE(rg.u), RE(rg.f),
+                    RE(rg.cos_eta), RE(rg.sin_eta), RE(rg.logg), RE(rg.beta), RE(rg.gamma),
+                    RE(dphi), (double)nact, (double)st};
     memcpy(info, v, sizeof(v));
     return st;
 }
@@ -712,15 +788,15 @@ int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
  * ===================================================================== */
 
 /* C[j][c] = sum_k Ft[j][k] ATT_k R[k][c], ATT_k = exp(-N_H sigma_k) */
-void orc_counts(const double *Ft, int n_phase, int nE, const float *R, int nc,
-                const float *sigma, double nh_1e20, double *C)
+void orc_counts(const real *Ft, int n_phase, int nE, const float *R, int nc,
+                const float *sigma, real nh_1e20, real *C)
 {
-    double nh = nh_1e20 * 1e20;
+    real nh = nh_1e20 * 1e20;
     for (int j = 0; j < n_phase; j++)
         for (int c = 0; c < nc; c++) {
-            double s = 0.0;
+            real s = 0.0;
             for (int k = 0; k < nE; k++)
-                s += Ft[(size_t)j * nE + k] * exp(-nh * (double)sigma[k]) * (double)R[(size_t)k * nc + c];
+                s += Ft[(size_t)j * nE + k] * r_exp(-nh * (double)sigma[k]) * (double)R[(size_t)k * nc + c];
             C[(size_t)j * nc + c] = s;
         }
 }
@@ -728,16 +804,46 @@ void orc_counts(const double *Ft, int n_phase, int nE, const float *R, int nc,
 /* logL = sum d ln(lambda) - lambda - ln Gamma(d + 1), lambda = tau C + b.
  * (reading: the Poisson log-likelihood; lambda = 0 gives 0 for d = 0 and
  * -inf for d > 0). */
-double orc_loglike(const double *C, int n, const int *d, const float *bkg, double tau)
+static real loglike_sum(const real *C, int n, const int *d, const float *bkg, double tau)
 {
-    double s = 0.0;
+    real s = 0.0;
     for (int i = 0; i < n; i++) {
-        double lam = tau * C[i] + (bkg ? (double)bkg[i] : 0.0);
-        if (lam <= 0.0) {
+        real lam = tau * C[i] + (bkg ? (double)bkg[i] : 0.0);
+        if (RE(lam) <= 0.0) {
             if (d[i] > 0) return -INFINITY;
             continue;
         }
-        s += (double)d[i] * log(lam) - lam - lgamma((double)d[i] + 1.0);
+        s += (double)d[i] * r_log(lam) - lam - lgamma((double)d[i] + 1.0);
     }
     return s;
+}
+
+#ifndef ORC_CSTEP
+double orc_loglike(const double *C, int n, const int *d, const float *bkg, double tau)
+{
+    return loglike_sum(C, n, d, bkg, tau);
+}
+#endif
+
+/* The whole chain for one instance: profile, attenuation and response,
+ * likelihood.  out[0] = logL; out[1] = its imaginary part (the tangent
+ * build's h times the directional derivative; 0 in the ordinary build).
+ * Returns the orc_profile status. */
+int orc_loglike_full(const orc_inst *in, const orc_lens *L, const orc_atm *A,
+                     const double *E_keV, int nE, const float *R, int nc,
+                     const float *sigma, const int *d, const float *bkg, double tau,
+                     double *out)
+{
+    real *Ft = (real *)malloc(sizeof(real) * (size_t)in->n_phase * nE);
+    real *C = (real *)malloc(sizeof(real) * (size_t)in->n_phase * nc);
+    int st = orc_profile(in, L, A, E_keV, nE, NULL, 0, NULL, 0, 1, Ft);
+    if (st == ORC_OK) {
+        orc_counts(Ft, in->n_phase, nE, R, nc, sigma, in->nh_1e20, C);
+        real ll = loglike_sum(C, in->n_phase * nc, d, bkg, tau);
+        out[0] = RE(ll);
+        out[1] = IM(ll);
+    }
+    free(Ft);
+    free(C);
+    return st;
 }
