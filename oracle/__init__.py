@@ -62,7 +62,11 @@ class AtmC(C.Structure):
                 ("n_protect", C.c_int),
                 ("logT", C.POINTER(C.c_double)), ("logg", C.POINTER(C.c_double)),
                 ("mu", C.POINTER(C.c_double)), ("lnE", C.POINTER(C.c_double)),
-                ("I", C.POINTER(C.c_float))]
+                ("I", C.POINTER(C.c_float)), ("strategy", C.c_int)]
+
+
+# interpolation strategies of Sect. 4 (ORC_INTERP_* in ppm_oracle.c)
+INTERP = {"d": 0, "a": 1, "b": 2, "c": 3}
 
 
 class InstC(C.Structure):
@@ -210,7 +214,7 @@ def lens(spec) -> Lens:
 # atmosphere (Sect. 4)
 # ---------------------------------------------------------------------------
 class Atm:
-    def __init__(self, table):
+    def __init__(self, table, strategy: str = "d"):
         self.t = table
         self._arr = [np.ascontiguousarray(table.logT, dtype=np.float64),
                      np.ascontiguousarray(table.logg, dtype=np.float64),
@@ -221,7 +225,7 @@ class Atm:
         dp = lambda x: x.ctypes.data_as(C.POINTER(C.c_double))
         self.c = AtmC(len(a[0]), len(a[1]), len(a[2]), len(a[3]), int(table.n_protect),
                       dp(a[0]), dp(a[1]), dp(a[2]), dp(a[3]),
-                      a[4].ctypes.data_as(C.POINTER(C.c_float)))
+                      a[4].ctypes.data_as(C.POINTER(C.c_float)), INTERP[strategy])
 
     def interp(self, logT, logg, mu, E_keV):
         return lib().orc_atm_interp(C.byref(self.c), logT, logg, mu, E_keV)
@@ -263,7 +267,7 @@ def profile(w, b: int = 0, jsel: Optional[Sequence[int]] = None,
     """
     inst = w.inst
     L = lens_obj or lens(w.lens)
-    A = atm_obj or (Atm(w.atm) if (inst.emission == 1) else None)
+    A = atm_obj or (Atm(w.atm, getattr(w, "interp", "d")) if (inst.emission == 1) else None)
     E = np.ascontiguousarray(w.E_keV, dtype=np.float64)
     js = None if jsel is None else np.ascontiguousarray(jsel, dtype=np.int32)
     ks = None if ksel is None else np.ascontiguousarray(ksel, dtype=np.int32)
@@ -349,7 +353,7 @@ def loglike_tangent(w, v, b: int = 0, h: float = 1e-20):
         elif s < inst.n_spots:
             getattr(ic, name)[s].im = h * float(vj)
     L = lens(w.lens)
-    A = Atm(w.atm) if inst.emission == 1 else None
+    A = Atm(w.atm, getattr(w, "interp", "d")) if inst.emission == 1 else None
     E = np.ascontiguousarray(w.E_keV, dtype=np.float64)
     R = np.ascontiguousarray(w.R, dtype=np.float32)
     sg = np.ascontiguousarray(w.sigma_ism, dtype=np.float32)

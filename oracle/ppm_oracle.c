@@ -387,7 +387,22 @@ typedef struct {
     int nT, ng, nmu, nE, n_protect;
     const double *logT, *logg, *mu, *lnE;  /* node positions */
     const float *I;                         /* [nT][ng][nmu][nE], linear intensity */
+    int strategy;                           /* ORC_INTERP_* below */
 } orc_atm;
+
+/* Interpolation strategies of Sect. 4 (the four compared on the paper's two
+ * interpolation tests):
+ *   D  the method's mixed scheme: linear in logT and logg; cubic Lagrange in
+ *      mu and ln E, linear where the centred stencil would leave the grid
+ *      and on the protected small-mu intervals;
+ *   A  cubic Lagrange in all four axes, the four-node stencil shifted to stay
+ *      inside the grid at the edges (one-sided);
+ *   B  as A, negative interpolants clipped to zero;
+ *   C  cubic in all four axes with the linear treatment of D at the table
+ *      edges and on the protected small-mu intervals. */
+enum { ORC_INTERP_D = 0, ORC_INTERP_A = 1, ORC_INTERP_B = 2, ORC_INTERP_C = 3 };
+/* per-axis rules */
+enum { AX_LINEAR = 0, AX_CUBIC = 1, AX_CUBIC_ONESIDED = 2 };
 
 /* interval index i with x[i] <= q < x[i+1] after clamping q to [x0, x_{n-1}] */
 static int find_interval(const double *x, int n, real *q)
@@ -403,21 +418,25 @@ static int find_interval(const double *x, int n, real *q)
 }
 
 /* Interpolation weights along one axis.  Writes node indices idx[] and
- * weights w[] (n_taps = 2 or 4).  cubic: Lagrange on the four nodes
+ * weights w[] (n_taps = 2 or 4).  AX_CUBIC: Lagrange on the four nodes
  * i-1..i+2 around interval i (actual node positions); falls back to linear
  * on (i, i+1) when the interval lies in the protected zone (i < n_protect-1)
- * or when the four-node stencil would leave the grid. */
-static int axis_weights(const double *x, int n, real q, int cubic, int n_protect,
+ * or when the four-node stencil would leave the grid.  AX_CUBIC_ONESIDED:
+ * Lagrange on the four nodes s..s+3 with s = i-1 moved into [0, n-4]. */
+static int axis_weights(const double *x, int n, real q, int rule, int n_protect,
                         int *idx, real *w)
 {
     int i = find_interval(x, n, &q);
-    if (cubic && i >= 1 && i + 2 <= n - 1 && i >= n_protect - 1) {
+    int s0 = -1;
+    if (rule == AX_CUBIC && i >= 1 && i + 2 <= n - 1 && i >= n_protect - 1) s0 = i - 1;
+    if (rule == AX_CUBIC_ONESIDED && n >= 4) s0 = i - 1 < 0 ? 0 : (i - 1 > n - 4 ? n - 4 : i - 1);
+    if (s0 >= 0) {
         for (int a = 0; a < 4; a++) {
-            int ka = i - 1 + a;
+            int ka = s0 + a;
             real l = 1.0;
             for (int b = 0; b < 4; b++) {
                 if (b == a) continue;
-                int kb = i - 1 + b;
+                int kb = s0 + b;
                 l *= (q - x[kb]) / (x[ka] - x[kb]);
             }
             idx[a] = ka;
@@ -437,10 +456,15 @@ real orc_atm_interp(const orc_atm *A, real logT, real logg, real mu, real E_keV)
 {
     int iT[4], ig[4], im[4], ie[4];
     real wT[4], wg[4], wm[4], we[4];
-    int nT = axis_weights(A->logT, A->nT, logT, 0, 0, iT, wT);
-    int ng = axis_weights(A->logg, A->ng, logg, 0, 0, ig, wg);
-    int nm = axis_weights(A->mu, A->nmu, mu, 1, A->n_protect, im, wm);
-    int ne = axis_weights(A->lnE, A->nE, r_log(E_keV), 1, 0, ie, we);
+    const int st = A->strategy;
+    const int cubic_all = st == ORC_INTERP_A || st == ORC_INTERP_B;
+    const int rTg = cubic_all ? AX_CUBIC_ONESIDED : (st == ORC_INTERP_C ? AX_CUBIC : AX_LINEAR);
+    const int rmE = cubic_all ? AX_CUBIC_ONESIDED : AX_CUBIC;
+    const int prot = cubic_all ? 0 : A->n_protect;
+    int nT = axis_weights(A->logT, A->nT, logT, rTg, 0, iT, wT);
+    int ng = axis_weights(A->logg, A->ng, logg, rTg, 0, ig, wg);
+    int nm = axis_weights(A->mu, A->nmu, mu, rmE, prot, im, wm);
+    int ne = axis_weights(A->lnE, A->nE, r_log(E_keV), rmE, 0, ie, we);
     real v = 0.0;
     for (int a = 0; a < nT; a++)
         for (int b = 0; b < ng; b++)
@@ -449,6 +473,7 @@ real orc_atm_interp(const orc_atm *A, real logT, real logg, real mu, real E_keV)
                     size_t k = (((size_t)iT[a] * A->ng + ig[b]) * A->nmu + im[c]) * A->nE + ie[d];
                     v += wT[a] * wg[b] * wm[c] * we[d] * (double)A->I[k];
                 }
+    if (st == ORC_INTERP_B && RE(v) < 0.0) v = 0.0;
     return v;
 }
 

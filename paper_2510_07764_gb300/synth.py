@@ -148,6 +148,7 @@ class Workload:
     sigma_ism: Optional[np.ndarray] = None  # [nE] float32, cm^2
     counts: Optional[np.ndarray] = None     # [sum_b n_phase_b, nc] int32
     tau: float = 1.0                        # exposure scale: lambda = tau * C
+    interp: str = "d"                       # atmosphere interpolation strategy (Sect. 4): d, a, b, c
 
     @property
     def nc(self) -> int:

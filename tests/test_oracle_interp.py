@@ -115,3 +115,92 @@ def test_negative_overshoot_is_kept(orc, table):
     A = orc.Atm(t)
     m = t.mu[5] + 0.5 * (t.mu[6] - t.mu[5])   # interval 5: stencil 4..7 sees the step
     assert A.interp(t.logT[1], t.logg[1], m, math.exp(t.lnE[4])) < 0.0
+
+
+# ---- the other strategies of Sect. 4 (a: cubic everywhere, one-sided at the
+# edges; b: a with negatives clipped; c: cubic everywhere with the linear edge
+# and protected-zone rules of the method)
+def poly4(t, seed):
+    """A table that is a cubic in each of (logT, logg, mu, ln E)."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (4, 4))
+
+    def P(lt, lg, mu, lnE):
+        x = [(lt - 6.0) / 0.8, (lg - 14.2) / 0.5, mu,
+             (lnE - t.lnE[0]) / (t.lnE[-1] - t.lnE[0])]
+        v = 1.0
+        for a in range(4):
+            v = v * sum(c[a, i] * x[a] ** i for i in range(4))
+        return 3.0 + v
+    T4, G4, M4, E4 = np.meshgrid(t.logT, t.logg, t.mu, t.lnE, indexing="ij")
+    t.I = np.ascontiguousarray(P(T4, G4, M4, E4).astype(np.float32))
+    return P
+
+
+def test_strategy_a_reproduces_cubics_everywhere(orc, synth):
+    """One-sided four-node stencils are exact for cubics up to the table edges,
+    including the small-mu intervals the method protects."""
+    t = synth.atm_table(n_T=6, n_g=5, n_mu=12, n_E=14)
+    P = poly4(t, 11)
+    A = orc.Atm(t, "a")
+    rng = np.random.default_rng(12)
+    for _ in range(300):
+        q = [rng.uniform(ax[0], ax[-1]) for ax in (t.logT, t.logg, t.mu, t.lnE)]
+        assert A.interp(q[0], q[1], q[2], math.exp(q[3])) == pytest.approx(P(*q), abs=2e-5)
+
+
+def test_strategy_c_cubic_inside_linear_at_edges(orc, synth):
+    t = synth.atm_table(n_T=6, n_g=5, n_mu=12, n_E=14)
+    P = poly4(t, 13)
+    A = orc.Atm(t, "c")
+    D = orc.Atm(t, "d")
+    rng = np.random.default_rng(14)
+    for _ in range(300):
+        q = [rng.uniform(ax[1], ax[-2]) for ax in (t.logT, t.logg, t.lnE)]
+        m = rng.uniform(t.mu[3], t.mu[-2])
+        assert A.interp(q[0], q[1], m, math.exp(q[2])) == pytest.approx(P(q[0], q[1], m, q[2]),
+                                                                       abs=2e-5)
+    # protected small-mu zone and the ln E edges: the method's linear rules,
+    # so with logT and logg on nodes (where cubic and linear agree) c equals d
+    for _ in range(100):
+        lt, lg = t.logT[2], t.logg[3]
+        m = rng.uniform(t.mu[0], t.mu[3])
+        le = rng.uniform(t.lnE[0], t.lnE[1])
+        assert A.interp(lt, lg, m, math.exp(le)) == pytest.approx(
+            D.interp(lt, lg, m, math.exp(le)), rel=1e-12, abs=1e-12)
+
+
+def test_strategy_b_clips_what_a_overshoots(orc, synth):
+    """A table with a sharp drop toward mu -> 0 (steep limb darkening): the
+    one-sided cubic undershoots below zero between the first nodes, the clipped
+    variant returns max(a, 0), and the method's protected linear zone stays
+    between the node values."""
+    t = synth.atm_table(n_T=5, n_g=4, n_mu=12, n_E=10)
+    mu = t.mu
+    prof = np.where(mu < mu[2], 0.0, 1.0) + 0.0 * mu
+    prof[2] = 0.02
+    t.I = np.ascontiguousarray(np.broadcast_to(prof[None, None, :, None], t.I.shape)
+                               .astype(np.float32))
+    Aa, Ab, Ad = orc.Atm(t, "a"), orc.Atm(t, "b"), orc.Atm(t, "d")
+    lt, lg, E = t.logT[1], t.logg[1], math.exp(t.lnE[4])
+    ms = np.linspace(mu[0], mu[4], 200)
+    va = np.array([Aa.interp(lt, lg, m, E) for m in ms])
+    vb = np.array([Ab.interp(lt, lg, m, E) for m in ms])
+    vd = np.array([Ad.interp(lt, lg, m, E) for m in ms])
+    assert va.min() < -1e-3
+    assert np.array_equal(vb, np.maximum(va, 0.0))
+    prot = ms <= mu[3]
+    assert vd[prot].min() >= 0.0 and vd[prot].max() <= 1.0 + 1e-6
+
+
+@pytest.mark.parametrize("strategy", ["a", "b", "c", "d"])
+def test_every_strategy_returns_node_values(orc, synth, strategy):
+    t = synth.atm_table(n_T=5, n_g=4, n_mu=10, n_E=12)
+    rng = np.random.default_rng(21)
+    t.I = np.ascontiguousarray(rng.uniform(-1.0, 2.0, t.I.shape).astype(np.float32))
+    A = orc.Atm(t, strategy)
+    for _ in range(60):
+        i = [rng.integers(0, len(ax)) for ax in (t.logT, t.logg, t.mu, t.lnE)]
+        v = float(t.I[i[0], i[1], i[2], i[3]])
+        got = A.interp(t.logT[i[0]], t.logg[i[1]], t.mu[i[2]], math.exp(t.lnE[i[3]]))
+        assert got == pytest.approx(max(v, 0.0) if strategy == "b" else v, abs=1e-12)
