@@ -98,6 +98,29 @@ ppm_status ppm_build_lens(ppm_ctx *ctx, const ppm_lens_spec *spec, void *stream)
 ppm_status ppm_get_lens(ppm_ctx *ctx, double *Ca, double *LF, double *TD);
 
 /* ------------------------------------------------------------------------
+ * Atmosphere interpolation strategy (Sect. 4, the four schemes compared on
+ * the paper's two interpolation tests).  Applies to every later call of the
+ * context; the default is PPM_INTERP_MIXED.
+ *   PPM_INTERP_MIXED        the method's scheme: linear in logT and logg,
+ *                           cubic Lagrange in mu and ln E, linear where the
+ *                           centred four-node stencil would leave the grid
+ *                           and on the protected small-mu intervals;
+ *   PPM_INTERP_CUBIC        cubic Lagrange in all four axes, the stencil moved
+ *                           inside the grid at the edges (one-sided);
+ *   PPM_INTERP_CUBIC_CLIP   as PPM_INTERP_CUBIC, negative interpolants set to 0;
+ *   PPM_INTERP_CUBIC_LINEAR_EDGES  cubic in all four axes with the linear
+ *                           edge and protected-zone rules of the method.
+ * Returns PPM_EINVAL for any other value.
+ * ------------------------------------------------------------------------ */
+enum {
+    PPM_INTERP_MIXED = 0,
+    PPM_INTERP_CUBIC = 1,
+    PPM_INTERP_CUBIC_CLIP = 2,
+    PPM_INTERP_CUBIC_LINEAR_EDGES = 3
+};
+ppm_status ppm_set_interpolation(ppm_ctx *ctx, int strategy);
+
+/* ------------------------------------------------------------------------
  * Atmosphere table (Sect. 2.5 and 4): specific intensity I(E', mu; T, g) in
  * keV cm^-2 s^-1 keV^-1 sr^-1, host array I[nT][ng][nmu][nE] (float32,
  * linear intensity), with node positions logT[nT], logg[ng] (uniform grids),

@@ -160,6 +160,12 @@ class Context:
                                             _dp(mu), len(mu), _dp(lnE), len(lnE),
                                             int(t.n_protect)))
 
+    def set_interpolation(self, strategy: str = "d"):
+        """Atmosphere interpolation strategy of Sect. 4: "d" (the method's mixed
+        scheme, default), "a" (cubic everywhere), "b" (a, clipped at zero),
+        "c" (cubic everywhere with linear edges)."""
+        self._check(_abi.ppm_set_interpolation(self.h, _abi.INTERP[strategy]))
+
     def set_energies(self, E_keV):
         E = np.ascontiguousarray(E_keV, dtype=np.float64)
         self._check(_abi.ppm_set_energies(self.h, _dp(E), len(E)))
@@ -177,6 +183,7 @@ class Context:
             self.build_lens(w.lens)
         if w.atm is not None:
             self.set_atmosphere(w.atm)
+        self.set_interpolation(getattr(w, "interp", "d"))
         self.set_energies(w.E_keV)
         if w.R is not None:
             self.set_response(w.R, w.sigma_ism)

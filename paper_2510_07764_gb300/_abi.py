@@ -20,7 +20,11 @@ STATUS_NAMES = ["PPM_OK", "PPM_EINVAL", "PPM_ERANGE", "PPM_ENOMEM", "PPM_ECUDA",
 EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm_get_lens",
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
            "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
-           "ppm_profile_noalloc", "ppm_loglike_grad"]
+           "ppm_profile_noalloc", "ppm_loglike_grad", "ppm_set_interpolation"]
+
+# interpolation strategies of Sect. 4 (PPM_INTERP_* in ppm.h), keyed by the
+# paper's panel letters
+INTERP = {"d": 0, "a": 1, "b": 2, "c": 3}
 
 
 class ppm_lens_spec(C.Structure):
@@ -76,6 +80,7 @@ def lib() -> C.CDLL:
         "ppm_get_lens": (i, [vp, vp, vp, vp]),
         "ppm_set_atmosphere": (i, [vp, vp, vp, i, vp, i, vp, i, vp, i, i]),
         "ppm_set_energies": (i, [vp, vp, i]),
+        "ppm_set_interpolation": (i, [vp, i]),
         "ppm_set_response": (i, [vp, vp, i, i, vp]),
         "ppm_profile": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
         "ppm_profile_noalloc": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
@@ -120,6 +125,10 @@ def ppm_get_lens(ctx, Ca, LF, TD) -> int:
 
 def ppm_set_atmosphere(ctx, I, logT, nT, logg, ng, mu, nmu, lnE, nE, n_protect) -> int:
     return lib().ppm_set_atmosphere(ctx, I, logT, nT, logg, ng, mu, nmu, lnE, nE, n_protect)
+
+
+def ppm_set_interpolation(ctx, strategy: int) -> int:
+    return lib().ppm_set_interpolation(ctx, strategy)
 
 
 def ppm_set_energies(ctx, E, nE) -> int:

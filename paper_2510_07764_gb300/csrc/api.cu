@@ -78,6 +78,7 @@ struct ppm_ctx {
     // atmosphere
     bool atm_ready = false;
     int nT = 0, ng = 0, nmu = 0, nEt = 0, n_protect = 0, nmu_pad = 0;
+    int interp = kInterpD;  // interpolation strategy (Sect. 4)
     double lnE0_t = 0.0, dlnE_t = 0.0;
     DevBuf d_I, d_logT, d_logg, d_mu;
     // energies
@@ -329,6 +330,15 @@ ppm_status ppm_set_atmosphere(ppm_ctx *ctx, const float *I, const double *logT, 
     ctx->nmu_pad = pad; ctx->lnE0_t = lnE[0]; ctx->dlnE_t = d;
     ctx->atm_ready = true;
     ctx->energy_dirty = true;
+    return PPM_OK;
+}
+
+ppm_status ppm_set_interpolation(ppm_ctx *ctx, int strategy)
+{
+    if (!ctx) return PPM_EINVAL;
+    if (strategy < PPM_INTERP_MIXED || strategy > PPM_INTERP_CUBIC_LINEAR_EDGES)
+        return fail(ctx, PPM_EINVAL, "unknown interpolation strategy %d", strategy);
+    ctx->interp = strategy;
     return PPM_OK;
 }
 
@@ -618,7 +628,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     L->ca_min = s.calpha_min; L->ca_max = s.calpha_max; L->n_calpha = s.n_calpha;
     L->Ca = ctx->d_Ca.as<double>(); L->LF = ctx->d_LF.as<double>(); L->TD = ctx->d_TD.as<double>();
     A->nT = ctx->nT; A->ng = ctx->ng; A->nmu = ctx->nmu; A->nE = ctx->nEt;
-    A->n_protect = ctx->n_protect; A->nmu_pad = ctx->nmu_pad;
+    A->n_protect = ctx->n_protect; A->nmu_pad = ctx->nmu_pad; A->strategy = ctx->interp;
     A->I = ctx->d_I.as<float>(); A->logT = ctx->d_logT.as<double>();
     A->logg = ctx->d_logg.as<double>(); A->mu = ctx->d_mu.as<float>();
     A->lnE0 = ctx->lnE0_t; A->dlnE = ctx->dlnE_t;
@@ -1094,7 +1104,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     Ld.Ca = ctx->d_Ca.as<double>(); Ld.LF = ctx->d_LF.as<double>(); Ld.TD = ctx->d_TD.as<double>();
     AtmDev A;
     A.nT = ctx->nT; A.ng = ctx->ng; A.nmu = ctx->nmu; A.nE = ctx->nEt;
-    A.n_protect = ctx->n_protect; A.nmu_pad = ctx->nmu_pad;
+    A.n_protect = ctx->n_protect; A.nmu_pad = ctx->nmu_pad; A.strategy = ctx->interp;
     A.I = ctx->d_I.as<float>(); A.logT = ctx->d_logT.as<double>();
     A.logg = ctx->d_logg.as<double>(); A.mu = ctx->d_mu.as<float>();
     A.lnE0 = ctx->lnE0_t; A.dlnE = ctx->dlnE_t;

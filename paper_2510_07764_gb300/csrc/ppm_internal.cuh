@@ -45,8 +45,17 @@ struct LensDev {
     const double *Ca, *LF, *TD;
 };
 
+// Interpolation strategies of Sect. 4 (PPM_INTERP_* in ppm.h):
+//   D (0) the method's mixed scheme: linear in logT, logg; cubic in mu and
+//         ln E, linear at the edges and on the protected small-mu intervals;
+//   A (1) cubic in all four axes, one-sided four-node stencils at the edges;
+//   B (2) A with negative interpolants clipped to zero;
+//   C (3) cubic in all four axes with D's linear edge / protected-zone rules.
+enum : int { kInterpD = 0, kInterpA = 1, kInterpB = 2, kInterpC = 3 };
+
 struct AtmDev {
     int nT, ng, nmu, nE, n_protect, nmu_pad;
+    int strategy;            // kInterp*
     const float *I;          // [nT][ng][nmu][nE]
     const double *logT;      // [nT]
     const double *logg;      // [ng]
@@ -73,10 +82,12 @@ struct Item {
 struct RingRec {
     int visible;    // 1 if the ring contributes
     int n_active;   // active elements (compacted at the front of the slots)
-    int iT, ig;     // lower (logT, logg) corner of the atmosphere cell
-    float wT, wg;   // weights of the upper corners
+    int iT, ig;     // first (logT, logg) node of the ring's interpolation stencil
+    int tT, tg;     // stencil taps along logT and logg (2 linear, 4 cubic)
     float kT;       // keV (blackbody emission)
     float pad;
+    float wT[4], wg[4];    // stencil weights
+    float dwT[4], dwg[4];  // their derivatives d/dlogT, d/dlogg (0 where clamped)
 };
 
 struct Params {

@@ -52,17 +52,50 @@ __device__ double td_lookup(const LensDev &L, double u, double ca)
            tu * ((1.0 - tc) * L.TD[k10] + tc * L.TD[k10 + 1]);
 }
 
-__device__ int axis_cell(const double *x, int n, double q, float *w)
+// Stencil of one table axis at q (FP64): first node, taps, weights and their
+// derivatives with respect to q.  rule 0: linear; 1: cubic Lagrange on the
+// centred four nodes, linear where they would leave the grid; 2: cubic on
+// four nodes moved inside the grid (one-sided at the edges).  q is clamped
+// to the grid first (the clamped end has zero derivative).
+__device__ int axis_stencil(const double *x, int n, double q, int rule, int *taps, float *w,
+                            float *dw)
 {
+    bool clamped = false;
+    if (q <= x[0]) { q = x[0]; clamped = true; }
+    if (q >= x[n - 1]) { q = x[n - 1]; clamped = true; }
     int lo = 0, hi = n - 1;
-    if (q <= x[0]) { *w = 0.0f; return 0; }
-    if (q >= x[n - 1]) { *w = 1.0f; return n - 2; }
     while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
+        const int mid = (lo + hi) >> 1;
         if (x[mid] <= q) lo = mid; else hi = mid;
     }
-    *w = (float)((q - x[lo]) / (x[lo + 1] - x[lo]));
-    return lo;
+    if (lo > n - 2) lo = n - 2;
+    int s0 = -1;
+    if (rule == 1 && lo >= 1 && lo + 2 <= n - 1) s0 = lo - 1;
+    if (rule == 2 && n >= 4) s0 = min(max(lo - 1, 0), n - 4);
+    for (int a = 0; a < 4; ++a) w[a] = dw[a] = 0.0f;
+    if (s0 < 0) {
+        const double h = x[lo + 1] - x[lo];
+        const double t = (q - x[lo]) / h;
+        w[0] = (float)(1.0 - t);
+        w[1] = (float)t;
+        dw[0] = clamped ? 0.0f : (float)(-1.0 / h);
+        dw[1] = clamped ? 0.0f : (float)(1.0 / h);
+        *taps = 2;
+        return lo;
+    }
+    for (int a = 0; a < 4; ++a) {
+        double den = 1.0, prod = 1.0, der = 0.0;
+        for (int b = 0; b < 4; ++b) {
+            if (b == a) continue;
+            den *= x[s0 + a] - x[s0 + b];
+            der = der * (q - x[s0 + b]) + prod;
+            prod *= q - x[s0 + b];
+        }
+        w[a] = (float)(prod / den);
+        dw[a] = clamped ? 0.0f : (float)(der / den);
+    }
+    *taps = 4;
+    return s0;
 }
 
 __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L, AtmDev A,
@@ -264,12 +297,15 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         RingRec rec;
         rec.visible = (G.ok && s_vis0 && n_active > 0) ? 1 : 0;
         rec.n_active = n_active;
-        rec.iT = 0; rec.ig = 0; rec.wT = 0.0f; rec.wg = 0.0f;
+        rec.iT = 0; rec.ig = 0; rec.tT = 0; rec.tg = 0;
+        for (int a = 0; a < 4; ++a) rec.wT[a] = rec.wg[a] = rec.dwT[a] = rec.dwg[a] = 0.0f;
         const double lt = p.logT[sidx];
         rec.kT = (float)(kKB_KEVK * pow(10.0, lt));
         if (p.emission == 1) {
-            rec.iT = axis_cell(A.logT, A.nT, lt, &rec.wT);
-            rec.ig = axis_cell(A.logg, A.ng, G.logg, &rec.wg);
+            // logT / logg: linear for D, cubic for C, one-sided cubic for A and B
+            const int rule = A.strategy == kInterpD ? 0 : (A.strategy == kInterpC ? 1 : 2);
+            rec.iT = axis_stencil(A.logT, A.nT, lt, rule, &rec.tT, rec.wT, rec.dwT);
+            rec.ig = axis_stencil(A.logg, A.ng, G.logg, rule, &rec.tg, rec.wg, rec.dwg);
         }
         rec.pad = 0.0f;
         recs[g] = rec;

@@ -11,7 +11,7 @@
 // of the bridged invisible points are first folded onto their two end
 // points, and that of point n_fp onto point 0 (the reverse of the fill).
 // Ring-level terms: the element azimuths (spot azimuth and the ring's
-// half-width), the logg cell weight and the logT cell weight.
+// half-width), and the ring's logg and logT through the atmosphere stencil.
 #include "ppm_internal.cuh"
 
 namespace ppm {
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kTBlock) k_template_bwd(Params p, PlanDev plan
             for (int w = 0; w < kTBlock / 32; ++w) t[d] += red[w][d];
         }
         const float *tail = ra + 4 * (n_fp + 1);
-        const double sgs = tail[0], sgss = tail[1], gWT = tail[2], gWg = tail[3], s_ref = tail[4];
+        const double sgs = tail[0], sgss = tail[1], gT = tail[2], gG = tail[3], s_ref = tail[4];
         double gazim = 0.0, glogT = 0.0;
         if (G.ok) {
             // element azimuths s_m = (phic - half + (m + 1/2) 2 half / n_phi) / 2 pi
@@ -350,16 +350,13 @@ __global__ void __launch_bounds__(kTBlock) k_template_bwd(Params p, PlanDev plan
             for (int d = 0; d < ND; ++d) t[d] += ghalf * G.half.d[d];
         }
         if (p.emission == 1) {
-            // cell weights: w = (q - node_lo) / (node_hi - node_lo), constant when clamped
-            const double lt = p.logT[sidx];
-            const double T0 = A.logT[rec.iT], T1 = A.logT[rec.iT + 1];
-            if (lt > T0 && lt < T1) glogT = gWT / (T1 - T0);
-            const double g0 = A.logg[rec.ig], g1 = A.logg[rec.ig + 1];
-            if (G.logg.v > g0 && G.logg.v < g1)
-                for (int d = 0; d < ND; ++d) t[d] += gWg * G.logg.d[d] / (g1 - g0);
+            // the tail carries dlogL/dlogT and dlogL/dlogg of the ring (the
+            // stencil-weight derivatives, zero where clamped, are in the slabs)
+            glogT = gT;
+            for (int d = 0; d < ND; ++d) t[d] += gG * G.logg.d[d];
         } else {
             // blackbody: the tail carries dlogL/dkT; kT = k_B 10^logT
-            glogT = gWT * (double)rec.kT * log(10.0);
+            glogT = gT * (double)rec.kT * log(10.0);
         }
         out[0] = t[0];
         out[1] = t[1];

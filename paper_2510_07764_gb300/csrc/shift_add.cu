@@ -82,6 +82,7 @@ struct PairW {
     bool on;               // contributes (active element, visible phase)
 };
 
+template <bool ONESIDED>
 __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, const float *ph,
                                               const float *mun, int n_fp, int top,
                                               const AtmDev &A, float inv_dlnE)
@@ -107,8 +108,10 @@ __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, c
     }
     float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int s0;
-    if (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1) {
-        s0 = i - 1;
+    // A, B (ONESIDED): cubic on four nodes moved inside the grid; C, D:
+    // centred cubic, linear on the protected small-mu intervals and at the edges
+    if (ONESIDED || (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1)) {
+        s0 = ONESIDED ? min(max(i - 1, 0), nmu - 4) : i - 1;
         const float x0 = mun[s0], x1 = mun[s0 + 1], x2 = mun[s0 + 2], x3 = mun[s0 + 3];
         w[0] = (mu - x1) * (mu - x2) * (mu - x3) / ((x0 - x1) * (x0 - x2) * (x0 - x3));
         w[1] = (mu - x0) * (mu - x2) * (mu - x3) / ((x1 - x0) * (x1 - x2) * (x1 - x3));
@@ -130,7 +133,7 @@ __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, c
 
 // general evaluation (table edges / clamping) of the contracted spectrum at p
 __device__ __noinline__ float eval_general(const PairW &P, const float *slab, int Pm, int nE_t,
-                                           float p)
+                                           float p, bool onesided)
 {
     if (p <= 0.0f) return contract4(slab, P.s0, P.w0, P.w1, P.w2, P.w3);
     if (p >= (float)(nE_t - 1))
@@ -138,6 +141,20 @@ __device__ __noinline__ float eval_general(const PairW &P, const float *slab, in
     const float q = floorf(p);
     const int qi = (int)q;
     const float t = p - q;
+    if (onesided && !(qi >= 1 && qi + 2 <= nE_t - 1)) {
+        // cubic on the four nodes s..s+3 inside the grid, evaluated at x = p - s
+        const int s = min(max(qi - 1, 0), nE_t - 4);
+        const float x = p - (float)s;
+        float y[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) y[a] = contract4(slab, (s + a) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
+        // Lagrange basis on the nodes 0, 1, 2, 3
+        const float l0 = -(x - 1.0f) * (x - 2.0f) * (x - 3.0f) * (1.0f / 6.0f);
+        const float l1 = x * (x - 2.0f) * (x - 3.0f) * 0.5f;
+        const float l2 = -x * (x - 1.0f) * (x - 3.0f) * 0.5f;
+        const float l3 = x * (x - 1.0f) * (x - 2.0f) * (1.0f / 6.0f);
+        return l0 * y[0] + l1 * y[1] + l2 * y[2] + l3 * y[3];
+    }
     if (qi >= 1 && qi + 2 <= nE_t - 1) {
         const float a = contract4(slab, (qi - 1) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
         const float b = contract4(slab, qi * Pm + P.s0, P.w0, P.w1, P.w2, P.w3);
@@ -154,11 +171,12 @@ __device__ __noinline__ float eval_general(const PairW &P, const float *slab, in
 }
 
 // weights of a pair for the slow path (kept out of line: it is rarely taken)
+template <bool ONESIDED>
 __device__ __noinline__ PairW pair_weights_slow(float s, float phi_out, const float *ph,
                                                 const float *mun, int n_fp, int top,
                                                 const AtmDev &A, float inv_dlnE)
 {
-    return pair_weights(true, s, phi_out, ph, mun, n_fp, top, A, inv_dlnE);
+    return pair_weights<ONESIDED>(true, s, phi_out, ph, mun, n_fp, top, A, inv_dlnE);
 }
 
 // dot product of a mu stencil row with its weights (four consecutive words)
@@ -166,6 +184,23 @@ __device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, flo
                                       float w3)
 {
     return fmaf(w3, q[3], fmaf(w2, q[2], fmaf(w1, q[1], w0 * q[0])));
+}
+
+// Slab of a (logT, logg) stencil with tT x tg taps (4 x 4 for the cubic
+// strategies A, B, C), transposed to [E][mu]; kept out of line (per ring).
+__device__ __noinline__ void stage_slab_stencil(const AtmDev &A, const RingRec *rp,
+                                                const float *I0, int plane, int Pm, float *slab,
+                                                int tid)
+{
+    const int tT = rp->tT, tg = rp->tg;
+    for (int idx = tid; idx < plane; idx += kSABlock) {
+        float v = 0.0f;
+        for (int a = 0; a < tT; ++a)
+            for (int c = 0; c < tg; ++c)
+                v = fmaf(rp->wT[a] * rp->wg[c], __ldg(I0 + ((size_t)a * A.ng + c) * plane + idx), v);
+        const int m = idx / A.nE, n = idx - m * A.nE;
+        slab[n * Pm + m] = v;
+    }
 }
 
 // component e & 1 of a packed pair
@@ -177,7 +212,9 @@ __device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, flo
 // the slot sum run as paired FP32 instructions (FADD2/FFMA2).  Interval
 // shifts stay per slot: a slot's 32 lanes are neighbouring elements and
 // shift together, so the branch is nearly warp-uniform.
-template <int NP>
+// MODE: 0 = centred stencils with the linear rules (strategies C, D);
+// 1 = one-sided cubic stencils (A); 2 = one-sided and clipped at zero (B)
+template <int NP, int MODE>
 __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi_out,
                                           const float *sel, const float *ph, const float *mun,
                                           const float *slab, int Pm, int n_fp, int top,
@@ -186,6 +223,7 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
                                           float lz_safe, float *frow)
 {
     constexpr int NS = 2 * NP;
+    constexpr bool ONESIDED = MODE != 0, CLIP = MODE == 2;
     float2 w0[NP], w1[NP], w2[NP], w3[NP], c0[NP], c1[NP], c2[NP], c3[NP], W2[NP], W3[NP], off[NP];
     const float *sp[NS];
     bool slow[NS];
@@ -193,8 +231,8 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
 #pragma unroll
     for (int e = 0; e < NS; ++e) {
         const int m = g0 + lane + 32 * e;
-        const PairW P = pair_weights(m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, ph, mun,
-                                     n_fp, top, A, inv_dlnE);
+        const PairW P = pair_weights<ONESIDED>(m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, ph,
+                                               mun, n_fp, top, A, inv_dlnE);
         const bool fast = P.on && sliding && (pk0 + P.lz >= 1.0f) && (pkl + P.lz < nEm2);
         slow[e] = P.on && !fast;
         // lanes outside the sliding window run it with zero weights
@@ -254,9 +292,12 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
             }
             float2 v[NP];
 #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            for (int p = 0; p < NP; ++p) {
                 v[p] = __ffma2_rn(t[p], __ffma2_rn(t[p], __ffma2_rn(t[p], c3[p], c2[p]), c1[p]),
                                   c0[p]);
+                // strategy B: F_p >= 0, so clipping F_p I clips I
+                if (CLIP) v[p] = make_float2(fmaxf(v[p].x, 0.0f), fmaxf(v[p].y, 0.0f));
+            }
             if (NP == 2) {
                 const float2 u = __fadd2_rn(v[0], v[NP - 1]);
                 acc[s] = u.x + u.y;
@@ -270,11 +311,13 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
             for (int e = 0; e < NS; ++e) {
                 if (slow[e]) {
                     const int m = g0 + lane + 32 * e;
-                    const PairW P =
-                        pair_weights_slow(sel[m], phi_out, ph, mun, n_fp, top, A, inv_dlnE);
+                    const PairW P = pair_weights_slow<ONESIDED>(sel[m], phi_out, ph, mun, n_fp, top,
+                                                                A, inv_dlnE);
 #pragma unroll
-                    for (int k = 0; k < kEC; ++k)
-                        acc[k] += eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz);
+                    for (int k = 0; k < kEC; ++k) {
+                        const float v = eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz, ONESIDED);
+                        acc[k] += CLIP ? fmaxf(v, 0.0f) : v;
+                    }
                 }
             }
         }
@@ -284,7 +327,7 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
 }
 #undef PPM_C
 
-template <int EMIS>
+template <int EMIS, int MODE>
 __global__ void __launch_bounds__(kSABlock, 2)
     k_shift_add(Params p, PlanDev plan, AtmDev A, EnergyDev en, Layout lay,
                 const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
@@ -323,7 +366,10 @@ __global__ void __launch_bounds__(kSABlock, 2)
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;
-        const RingRec rec = recs[ring];
+        // the scalar fields of the ring record (its weight arrays are read in place)
+        const RingRec *rp = recs + ring;
+        struct { int visible, n_active, iT, ig, tT, tg; float kT; } rec = {
+            rp->visible, rp->n_active, rp->iT, rp->ig, rp->tT, rp->tg, rp->kT};
         if (!rec.visible) continue;
         __syncthreads();  // previous ring finished with the staged data
         {
@@ -333,33 +379,38 @@ __global__ void __launch_bounds__(kSABlock, 2)
             for (int i = tid; i < rec.n_active; i += blockDim.x) sm[lay.elems + i] = esrc[i];
             if (EMIS == 1) {
                 const int plane = A.nmu * A.nE;
-                const float *I00 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
-                const float *I01 = I00 + plane;
-                const float *I10 = I00 + (size_t)A.ng * plane;
+                const float *I0 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
+                const bool lin2 = rec.tT == 2 && rec.tg == 2;
+                const float w00 = rp->wT[0] * rp->wg[0], w01 = rp->wT[0] * rp->wg[1];
+                const float w10 = rp->wT[1] * rp->wg[0], w11 = rp->wT[1] * rp->wg[1];
+                const float *I01 = I0 + plane;
+                const float *I10 = I0 + (size_t)A.ng * plane;
                 const float *I11 = I10 + plane;
-                const float wT = rec.wT, wg = rec.wg;
-                const float w00 = (1.0f - wT) * (1.0f - wg), w01 = (1.0f - wT) * wg;
-                const float w10 = wT * (1.0f - wg), w11 = wT * wg;
                 float *slab = sm + lay.slab;
                 constexpr int U = 4;  // loads in flight per thread
-                for (int base = tid; base < plane; base += U * kSABlock) {
-                    float v[U];
+                if (lin2) {
+                    // (logT, logg) bilinear (strategy D): four planes
+                    for (int base = tid; base < plane; base += U * kSABlock) {
+                        float v[U];
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int idx = base + u * kSABlock;
-                        v[u] = 0.0f;
-                        if (idx < plane)
-                            v[u] = w00 * __ldg(I00 + idx) + w01 * __ldg(I01 + idx) +
-                                   w10 * __ldg(I10 + idx) + w11 * __ldg(I11 + idx);
-                    }
+                        for (int u = 0; u < U; ++u) {
+                            const int idx = base + u * kSABlock;
+                            v[u] = 0.0f;
+                            if (idx < plane)
+                                v[u] = w00 * __ldg(I0 + idx) + w01 * __ldg(I01 + idx) +
+                                       w10 * __ldg(I10 + idx) + w11 * __ldg(I11 + idx);
+                        }
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int idx = base + u * kSABlock;
-                        if (idx < plane) {
-                            const int m = idx / A.nE, n = idx - m * A.nE;
-                            slab[n * Pm + m] = v[u];
+                        for (int u = 0; u < U; ++u) {
+                            const int idx = base + u * kSABlock;
+                            if (idx < plane) {
+                                const int m = idx / A.nE, n = idx - m * A.nE;
+                                slab[n * Pm + m] = v[u];
+                            }
                         }
                     }
+                } else {
+                    stage_slab_stencil(A, rp, I0, plane, Pm, slab, tid);
                 }
             }
         }
@@ -379,12 +430,12 @@ __global__ void __launch_bounds__(kSABlock, 2)
             if constexpr (EMIS == 1) {
                 for (int g0 = 0; g0 < n_act;) {
                     if (n_act - g0 > 64) {
-                        atm_group<2>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
+                        atm_group<2, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
                                      A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
                                      Fblk + jl * nEpad);
                         g0 += 128;
                     } else {
-                        atm_group<1>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
+                        atm_group<1, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
                                      A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
                                      Fblk + jl * nEpad);
                         g0 += 64;
@@ -535,19 +586,19 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
     lay.total = off;
     const size_t bytes = (size_t)off * sizeof(float);
     cudaError_t e;
-    if (p.emission == 1) {
-        e = cudaFuncSetAttribute(k_shift_add<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
-        if (e != cudaSuccess) return e;
-        k_shift_add<1><<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl,
-                                                              elems, status, partials);
-    } else {
-        e = cudaFuncSetAttribute(k_shift_add<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
-        if (e != cudaSuccess) return e;
-        k_shift_add<0><<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl,
-                                                              elems, status, partials);
-    }
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bytes);
+        if (r != cudaSuccess) return r;
+        kern<<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, status,
+                                                    partials);
+        return cudaSuccess;
+    };
+    if (p.emission == 0) e = go(k_shift_add<0, 0>);
+    else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1>);
+    else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2>);
+    else e = go(k_shift_add<1, 0>);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -8,14 +8,15 @@
 //     sF  = sum_k A_k I_k                 -> dlogL/dF_p
 //     sZ  = sum_k A_k dI/dt_k             -> dlogL/dz_p  (t = table position in ln E)
 //     sMu = sum_k A_k dI/dmu_k            -> dlogL/dmu_p
-//     sT  = sum_k A_k dI/dw_T,k           -> dlogL/d(logT cell weight)
-//     sG  = sum_k A_k dI/dw_g,k           -> dlogL/d(logg cell weight)
+//     sT  = sum_k A_k dI/dlogT_k          -> dlogL/dlogT of the ring
+//     sG  = sum_k A_k dI/dlogg_k          -> dlogL/dlogg of the ring
 // from four sliding interval cubics (intensity, mu-derivative weights, and the
-// two slab derivatives staged alongside the slab), then scatters them onto
+// slab's derivatives with respect to logT and logg, staged alongside it
+// from the derivatives of the ring's stencil weights), then scatters them onto
 // the ring's template adjoints through the linear phase interpolation,
 // including the dependence of the interpolation weight on phi_o and on the
 // element azimuth.  The per-ring record (floats):
-//     gF[n_fp+1] gZ[n_fp+1] gMu[n_fp+1] gPh[n_fp+1] | sum gs | sum gs*(s - s_ref) | gWT | gWg
+//     gF[n_fp+1] gZ[n_fp+1] gMu[n_fp+1] gPh[n_fp+1] | sum gs | sum gs*(s - s_ref) | gT | gg
 //     | s_ref | 0 0 0
 // where gs is the adjoint of an element's azimuth / 2 pi and the second
 // tail sum is taken about s_ref (the ring's first active element), which
@@ -144,8 +145,9 @@ __device__ __forceinline__ PairB pair_bwd(bool on, float s, float phi_out, const
     }
     float wv[4] = {0.f, 0.f, 0.f, 0.f}, dv[4] = {0.f, 0.f, 0.f, 0.f};
     int s0;
-    if (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1) {
-        s0 = i - 1;
+    const bool onesided = A.strategy == kInterpA || A.strategy == kInterpB;
+    if (onesided || (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1)) {
+        s0 = onesided ? min(max(i - 1, 0), nmu - 4) : i - 1;
         float x4[4] = {mun[s0], mun[s0 + 1], mun[s0 + 2], mun[s0 + 3]};
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -186,7 +188,8 @@ struct Quint {
 
 // general evaluation at table position p (edges / clamping), all five values
 __device__ __noinline__ Quint bwd_general(const PairB &P, const float *S, const float *ST,
-                                          const float *SG, int Pm, int nE_t, float p)
+                                          const float *SG, int Pm, int nE_t, float p,
+                                          bool onesided)
 {
     Quint Q;
     int q0, qn;
@@ -199,6 +202,34 @@ __device__ __noinline__ Quint bwd_general(const PairB &P, const float *S, const 
         q0 = (int)q;
         t = p - q;
         cubic = q0 >= 1 && q0 + 2 <= nE_t - 1;
+        if (onesided && !cubic) {
+            // cubic on the four nodes s..s+3 inside the grid (strategies A, B):
+            // Lagrange basis at x = p - s and its derivative
+            const int s = min(max(q0 - 1, 0), nE_t - 4);
+            const float x = p - (float)s;
+            const float l[4] = {-(x - 1.0f) * (x - 2.0f) * (x - 3.0f) * (1.0f / 6.0f),
+                                x * (x - 2.0f) * (x - 3.0f) * 0.5f,
+                                -x * (x - 1.0f) * (x - 3.0f) * 0.5f,
+                                x * (x - 1.0f) * (x - 2.0f) * (1.0f / 6.0f)};
+            const float dl[4] = {
+                -((x - 2.0f) * (x - 3.0f) + (x - 1.0f) * (x - 3.0f) + (x - 1.0f) * (x - 2.0f)) *
+                    (1.0f / 6.0f),
+                ((x - 2.0f) * (x - 3.0f) + x * (x - 3.0f) + x * (x - 2.0f)) * 0.5f,
+                -((x - 1.0f) * (x - 3.0f) + x * (x - 3.0f) + x * (x - 1.0f)) * 0.5f,
+                ((x - 1.0f) * (x - 2.0f) + x * (x - 2.0f) + x * (x - 1.0f)) * (1.0f / 6.0f)};
+            Q.I = Q.dI = Q.Im = Q.It = Q.Ig = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float *r = S + (s + a) * Pm + P.s0;
+                const float yi = dot4(r, P.w0, P.w1, P.w2, P.w3);
+                Q.I = fmaf(l[a], yi, Q.I);
+                Q.dI = fmaf(dl[a], yi, Q.dI);
+                Q.Im = fmaf(l[a], dot4(r, P.v0, P.v1, P.v2, P.v3), Q.Im);
+                Q.It = fmaf(l[a], dot4(ST + (s + a) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3), Q.It);
+                Q.Ig = fmaf(l[a], dot4(SG + (s + a) * Pm + P.s0, P.w0, P.w1, P.w2, P.w3), Q.Ig);
+            }
+            return Q;
+        }
     }
     qn = q0;
     auto node = [&](const float *B, int n, float a0, float a1, float a2, float a3) {
@@ -242,7 +273,7 @@ __device__ __noinline__ Quint bwd_general(const PairB &P, const float *S, const 
     return Q;
 }
 
-template <int EMIS>
+template <int EMIS, bool CLIP>
 __global__ void __launch_bounds__(kBwdBlock, 1)
     k_shift_add_bwd(Params p, PlanDev plan, AtmDev A, EnergyDev en, BLayout lay,
                     const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
@@ -279,23 +310,25 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
         if (EMIS == 1) {
             for (int i = tid; i < A.nmu; i += blockDim.x) sm[lay.munodes + i] = A.mu[i];
             const int plane = A.nmu * A.nE;
-            const float *I00 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
-            const float *I01 = I00 + plane;
-            const float *I10 = I00 + (size_t)A.ng * plane;
-            const float *I11 = I10 + plane;
-            const float wT = rec.wT, wg = rec.wg;
+            const float *I0 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
             const int Pm = A.nmu_pad;
             for (int idx = tid; idx < plane; idx += blockDim.x) {
-                const float a = __ldg(I00 + idx), c = __ldg(I01 + idx);
-                const float d = __ldg(I10 + idx), e = __ldg(I11 + idx);
+                // the forward slab (the forward's stencil weights) and its
+                // derivatives with respect to logT and logg
+                float v = 0.0f, vT = 0.0f, vG = 0.0f;
+                const RingRec *rp = recs + ring;  // stencil weights (read in place)
+                for (int a = 0; a < rec.tT; ++a)
+                    for (int c = 0; c < rec.tg; ++c) {
+                        const float I = __ldg(I0 + ((size_t)a * A.ng + c) * plane + idx);
+                        v = fmaf(rp->wT[a] * rp->wg[c], I, v);
+                        vT = fmaf(rp->dwT[a] * rp->wg[c], I, vT);
+                        vG = fmaf(rp->wT[a] * rp->dwg[c], I, vG);
+                    }
                 const int m = idx / A.nE, n = idx - m * A.nE;
                 const int o = n * Pm + m;
-                // the forward slab with the forward's corner weights, and its
-                // derivatives with respect to the two cell weights
-                sm[lay.slab + o] = (1.0f - wT) * (1.0f - wg) * a + (1.0f - wT) * wg * c +
-                                   wT * (1.0f - wg) * d + wT * wg * e;
-                sm[lay.slabT + o] = (1.0f - wg) * (d - a) + wg * (e - c);
-                sm[lay.slabG + o] = (1.0f - wT) * (c - a) + wT * (e - d);
+                sm[lay.slab + o] = v;
+                sm[lay.slabT + o] = vT;
+                sm[lay.slabG + o] = vG;
             }
         }
     }
@@ -318,6 +351,7 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
     const float pk0 = spk[0], pkl = spk[nE - 1];
     const float lz_safe = 1.25f - pk0;
     const bool sliding = en.sliding != 0;
+    const bool onesided = A.strategy == kInterpA || A.strategy == kInterpB;
     const int n_act = rec.n_active;
     const float s_ref = sel[0];
     const float inv_kT = 1.0f / rec.kT;
@@ -381,11 +415,14 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                             off -= 1.0f;
                             t -= 1.0f;
                         }
-                        const float2 tt = make_float2(t, t), ak = make_float2(pka.y, pka.y);
+                        const float2 tt = make_float2(t, t);
                         const float2 vIM = horner2(cIM, tt), vTG = horner2(cTG, tt);
+                        // strategy B: max(I, 0) passes no derivative where I <= 0
+                        const float a1 = CLIP ? (vIM.x > 0.0f ? pka.y : 0.0f) : pka.y;
+                        const float2 ak = make_float2(a1, a1);
                         sFM = __ffma2_rn(ak, vIM, sFM);
                         sTG = __ffma2_rn(ak, vTG, sTG);
-                        sZa = fmaf(pka.y, fmaf(t, fmaf(t, d2, d1), cIM.c1.x), sZa);
+                        sZa = fmaf(a1, fmaf(t, fmaf(t, d2, d1), cIM.c1.x), sZa);
                     }
                     sF = sFM.x;
                     sMu = sFM.y;
@@ -394,8 +431,9 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                     sZ = sZa;
                 } else if (P.on) {
                     for (int k = 0; k < nE; ++k) {
-                        const Quint Q = bwd_general(P, S, S + offT, S + offG, Pm, A.nE, spk[k] + P.lz);
-                        const float ak = parow[k].y;
+                        const Quint Q = bwd_general(P, S, S + offT, S + offG, Pm, A.nE,
+                                                    spk[k] + P.lz, onesided);
+                        const float ak = CLIP ? (Q.I > 0.0f ? parow[k].y : 0.0f) : parow[k].y;
                         sF = fmaf(ak, Q.I, sF);
                         sZ = fmaf(ak, Q.dI, sZ);
                         sMu = fmaf(ak, Q.Im, sMu);
@@ -518,17 +556,23 @@ cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const Atm
     if (plan.total_rings <= 0) return cudaSuccess;
     const BwdSizes z = bwd_layout(p.emission, plan, A, en, n_phi_max);
     cudaError_t e;
-    if (p.emission == 1) {
-        e = cudaFuncSetAttribute(k_shift_add_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)z.bytes);
+    if (p.emission == 1 && A.strategy == kInterpB) {
+        e = cudaFuncSetAttribute(k_shift_add_bwd<1, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
         if (e != cudaSuccess) return e;
-        k_shift_add_bwd<1><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
+        k_shift_add_bwd<1, true><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
+            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
+    } else if (p.emission == 1) {
+        e = cudaFuncSetAttribute(k_shift_add_bwd<1, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
+        if (e != cudaSuccess) return e;
+        k_shift_add_bwd<1, false><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
             p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
     } else {
-        e = cudaFuncSetAttribute(k_shift_add_bwd<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)z.bytes);
+        e = cudaFuncSetAttribute(k_shift_add_bwd<0, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
         if (e != cudaSuccess) return e;
-        k_shift_add_bwd<0><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
+        k_shift_add_bwd<0, false><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
             p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
     }
     return cudaGetLastError();

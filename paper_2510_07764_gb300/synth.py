@@ -179,13 +179,18 @@ def mu_nodes(n: int = 67, mu_min: float = 1e-6) -> np.ndarray:
 # atmosphere table
 # --------------------------------------------------------------------------
 def atm_table(n_T: int = 35, n_g: int = 11, n_mu: int = 67, n_E: int = 166,
-              seed: int = SEED) -> AtmTable:
+              seed: int = SEED, steep_limb_mu0: float = 0.0) -> AtmTable:
     """Synthetic NSX-shaped table: blackbody x limb darkening x smooth +-5 %.
 
     I = B_E(E, T) (1 + a mu + b mu^2) (1 + 0.05 p), with
     a = 0.6 - 0.2 (logT - 6) + 0.1 (logg - 14.2), b = -0.25 + 0.05 (logT - 6),
     p a seeded sum of 8 separable low-frequency cosines scaled to max|p| = 1.
     Values below the float32 normal range are flushed to zero.
+
+    steep_limb_mu0 > 0 multiplies I by (1 - exp(-mu / mu0)): a limb drop over
+    the first few mu nodes, the kind of small-mu curvature that makes cubic
+    stencils overshoot (a variant for the interpolation tests of Sect. 4; the
+    default table has none).
     """
     logT = np.linspace(5.1, 6.8, n_T)
     logg = np.linspace(13.7, 14.7, n_g)
@@ -219,6 +224,8 @@ def atm_table(n_T: int = 35, n_g: int = 11, n_mu: int = 67, n_E: int = 166,
     p = p / np.max(np.abs(p))
 
     I = bb * limb * (1.0 + 0.05 * p)
+    if steep_limb_mu0 > 0.0:
+        I = I * -np.expm1(-M4 / steep_limb_mu0)
     I = np.where(np.isfinite(I), I, 0.0)
     I32 = I.astype(np.float32)
     I32[np.abs(I32) < np.finfo(np.float32).tiny] = 0.0
@@ -360,6 +367,23 @@ def crescent_extreme(n_theta: int = 512, n_phi: int = 512, n_phase: int = 256,
     w = Workload("crescent_extreme", inst, lens or LensSpec(), logspace(0.1, 5.215, n_E),
                  atm=atm if atm is not None else atm_table())
     return _with_response(w, n_chan, tau=TAU_TWO_SPOT)
+
+
+def interp_test(case: int = 1, n: int = 32, n_phase: int = 64, n_E: int = 128,
+                atm: Optional[AtmTable] = None, lens: Optional[LensSpec] = None,
+                strategy: str = "d") -> Workload:
+    """The two atmosphere-interpolation tests of Sect. 4 (table tab:interp):
+    one point-like spot (zeta = 0.01) seen close to the limb so that many rays
+    have mu -> 0.  Test 1: spot colatitude 1.983, inclination 0.01; test 2:
+    spot at pi - 0.01, inclination 0.964.  M = 1.4, R_e = 12 km, 600 Hz,
+    T = 1e6 K, D = 150 pc."""
+    th, inc = (1.983, 0.01) if case == 1 else (math.pi - 0.01, 0.964)
+    inst = _instances(1, 1, mass_msun=1.4, radius_km=12.0, spin_hz=600.0, incl_rad=inc,
+                      dist_kpc=0.15, nh_1e20=1.0, colat=th, azim=0.0, zeta=0.01, logT=6.0,
+                      mask_zeta=0.0, n_theta=n, n_phi=n, n_phase=n_phase)
+    return Workload("interp_test_%d" % case, inst, lens or LensSpec(),
+                    logspace(0.1, 5.215, n_E), atm=atm if atm is not None else atm_table(),
+                    interp=strategy)
 
 
 def _compactness(mass_msun, radius_km):

@@ -15,6 +15,7 @@ def context(w, key=None):
     ctx = _ctx_cache[k]
     if w.atm is not None:
         ctx.set_atmosphere(w.atm)
+    ctx.set_interpolation(getattr(w, "interp", "d"))
     ctx.set_energies(w.E_keV)
     if w.R is not None:
         ctx.set_response(w.R, w.sigma_ism)
