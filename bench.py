@@ -58,6 +58,10 @@ def parse():
                     help="parameter vectors of the batch / grad_batch workloads")
     ap.add_argument("--flush-mib", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graph", action="store_true",
+                    help="capture one step in a CUDA graph and time its replays")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the shift-and-add tiles with ppm_autotune before timing")
     return ap.parse_args()
 
 
@@ -163,8 +167,9 @@ def oracle_sample(w, stride):
     w0 = w if w.inst.B == 1 else _single(w, 0)
     t0 = time.perf_counter()
     Ft = oracle.profile(w0, ring_stride=stride)
-    C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
-    oracle.loglike(C, w0.counts, w.tau)
+    if w.R is not None:
+        C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
+        oracle.loglike(C, w0.counts, w.tau)
     dt = time.perf_counter() - t0
     nE = len(w.E_keV)
     total = sum(_work(w.inst, b, nE) for b in range(w.inst.B))
@@ -191,7 +196,8 @@ def cpu_baseline(w, grad_mode=False):
     dt, factor = oracle_sample(w, CPU_RING_STRIDE)
     per_eval = dt * factor / w.inst.B
     mult = fd_evals(w) if grad_mode else 1
-    return {"value": 1.0 / (per_eval * mult), "unit": "grad-evals/s" if grad_mode else "evals/s",
+    unit = "grad-evals/s" if grad_mode else ("evals/s" if w.R is not None else "profile evals/s")
+    return {"value": 1.0 / (per_eval * mult), "unit": unit,
             "cores": 1, "kind": "oracle",
             "sample": "instance 0, every %dth ring, all phases x energies, response and logL; "
                       "%.1f s measured, extrapolated x%.4g by element x phase x energy work%s"
@@ -218,7 +224,7 @@ def run_reference(args, rank, world):
     per_eval = per_step / w.inst.B
     sample = ("instance 0, every %dth ring per step, extrapolated by element x phase x energy "
               "work to the whole workload" % REF_RING_STRIDE)
-    unit = "evals/s"
+    unit = "evals/s" if w.R is not None else "profile evals/s"
     if grad_mode:
         sample += "; x%d evaluations per central-difference gradient" % mult
         unit = "grad-evals/s"
@@ -250,7 +256,11 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.perf_counter() - t0
     dp = ppm.DeviceParams(w.inst, device=dev)
     B = dp.B
-    counts = torch.from_numpy(w.counts).to(dev)
+    # workloads without a response (the small blackbody one) time the
+    # forward profile alone; its result F_t is what the end-to-end leg reads
+    profile_mode = w.R is None
+    counts = None if profile_mode else torch.from_numpy(w.counts).to(dev)
+    Ft = torch.empty((dp.rows, len(w.E_keV)), dtype=torch.float32, device=dev)
     logL = torch.empty(B, dtype=torch.float64, device=dev)
     grad = torch.empty((B, ppm.N_GRAD), dtype=torch.float64, device=dev)
     flush = torch.empty(args.flush_mib * (1 << 20) // 4, dtype=torch.float32, device=dev)
@@ -260,15 +270,33 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             torch.distributed.barrier()
 
-    def step():
-        if grad_mode:
-            ctx.loglike_grad(dp, counts, w.tau, out=logL, grad=grad)
+    def step(stream=None):
+        if profile_mode:
+            ctx.profile(dp, out=Ft, stream=stream)
+        elif grad_mode:
+            ctx.loglike_grad(dp, counts, w.tau, out=logL, grad=grad, stream=stream)
         else:
-            ctx.loglike(dp, counts, w.tau, out=logL)
+            ctx.loglike(dp, counts, w.tau, out=logL, stream=stream)
 
+    tuned = None
+    if args.autotune:
+        tuned = ctx.autotune(dp)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    graph = None
+    if args.graph:
+        # one step captured once; replays re-read parameters and counts from
+        # the same device buffers (the plan and workspace are settled above)
+        s_cap = torch.cuda.Stream()
+        s_cap.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s_cap):
+            step(s_cap)
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
 
     # ---- device-timed steps (inputs resident in HBM; L2 flushed before each)
     gpu_id = None
@@ -288,15 +316,23 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.steps):
         flush.fill_(float(k))
         evs[k][0].record()
-        step()
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
         evs[k][1].record()
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    if graph is not None:
+        # graph replays record no stage events: three direct calls for the breakdown
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
     timing = ctx.get_timing()
     ctx.set_timing(False)
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    n_bad = int((~np.isfinite(logL.cpu().numpy())).sum())
+    n_bad = 0 if profile_mode else int((~np.isfinite(logL.cpu().numpy())).sum())
     fwd_ms = None
     if grad_mode:
         # the forward alone on the same inputs, for the backward / forward ratio
@@ -316,11 +352,12 @@ def run_ours(args, rank, world, local_rank):
     host_inst = w.inst.replace()
     for f, t in pin.items():
         setattr(host_inst, f, t)
-    counts_pin = torch.from_numpy(w.counts).pin_memory()
+    counts_pin = None if profile_mode else torch.from_numpy(w.counts).pin_memory()
     out_pin = torch.empty(B, dtype=torch.float64).pin_memory()
     grad_pin = torch.empty((B, ppm.N_GRAD), dtype=torch.float64).pin_memory()
-    h2d = sum(t.numel() * 8 for t in pin.values()) + counts_pin.numel() * 4
-    d2h = B * 8 * (1 + (ppm.N_GRAD if grad_mode else 0))
+    ft_pin = torch.empty(tuple(Ft.shape), dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 8 for t in pin.values()) + (0 if profile_mode else counts_pin.numel() * 4)
+    d2h = Ft.numel() * 4 if profile_mode else B * 8 * (1 + (ppm.N_GRAD if grad_mode else 0))
     evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in range(args.steps)]
     barrier()
@@ -329,9 +366,16 @@ def run_ours(args, rank, world, local_rank):
         flush.fill_(float(k))
         evs2[k][0].record()
         dp.upload(host_inst, non_blocking=True)
-        counts.copy_(counts_pin, non_blocking=True)
-        step()
-        out_pin.copy_(logL, non_blocking=True)
+        if not profile_mode:
+            counts.copy_(counts_pin, non_blocking=True)
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
+        if profile_mode:
+            ft_pin.copy_(Ft, non_blocking=True)
+        else:
+            out_pin.copy_(logL, non_blocking=True)
         if grad_mode:
             grad_pin.copy_(grad, non_blocking=True)
         evs2[k][1].record()
@@ -375,7 +419,11 @@ def run_ours(args, rank, world, local_rank):
     cfg["l2"] = "flushed before every timed step (%d MiB write)" % args.flush_mib
     cfg["parallelism"] = "replicas x%d" % world
     cfg["setup_s"] = round(setup_s, 3)
-    unit = "grad-evals/s" if grad_mode else "evals/s"
+    cfg["launch"] = "CUDA graph replay" if graph is not None else "direct calls"
+    cfg["tiles"] = ctx.get_tiles()
+    if tuned is not None:
+        cfg["autotuned"] = tuned
+    unit = "grad-evals/s" if grad_mode else ("profile evals/s" if profile_mode else "evals/s")
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -266,6 +266,34 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
                             int *inst_status, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Work decomposition of the shift-and-add and its autotuner (no counterpart
+ * in the paper, whose GPU design assigns one ring per SM, Sect. 2.9).
+ * A work item is (instance, spot, ring group, tile of phase_tile output
+ * phases); ring groups are sized so that the whole call makes about
+ * `waves` waves of two blocks per SM; items run largest first, either one
+ * block per item (persistent = 0) or as a queue drained by two resident
+ * blocks per SM (persistent = 1).  phase_tile = 0 picks 16 or 32 from the
+ * problem size.  The setting applies to later calls of the context.
+ *
+ * ppm_autotune runs the forward profile of (p, res) once per candidate
+ * (phase_tile 16/32 x waves 8/16/32 x persistent 0/1, one untimed and one
+ * timed pass each, synchronising `stream`), keeps the fastest, and returns
+ * it in *best (ms = its time).  Results do not depend on the choice
+ * (the partial sums are added in a fixed order).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int phase_tile;   /* 0 (automatic), 16 or 32 */
+    int waves;        /* 1 .. 256, default 16 */
+    int persistent;   /* 0 or 1 */
+    double ms;        /* ppm_autotune: time of the chosen candidate */
+} ppm_tiles;
+
+ppm_status ppm_set_tiles(ppm_ctx *ctx, const ppm_tiles *t);
+ppm_status ppm_get_tiles(ppm_ctx *ctx, ppm_tiles *t);
+ppm_status ppm_autotune(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, void *stream,
+                        ppm_tiles *best);
+
+/* ------------------------------------------------------------------------
  * Stage timing (no counterpart in the paper; tracing support).  When enabled,
  * every compute call records CUDA events around its stages on the call's
  * stream and counts its kernel launches and the (active element, output

@@ -20,7 +20,8 @@ STATUS_NAMES = ["PPM_OK", "PPM_EINVAL", "PPM_ERANGE", "PPM_ENOMEM", "PPM_ECUDA",
 EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm_get_lens",
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
            "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
-           "ppm_profile_noalloc", "ppm_loglike_grad", "ppm_set_interpolation"]
+           "ppm_profile_noalloc", "ppm_loglike_grad", "ppm_set_interpolation",
+           "ppm_set_tiles", "ppm_get_tiles", "ppm_autotune"]
 
 # interpolation strategies of Sect. 4 (PPM_INTERP_* in ppm.h), keyed by the
 # paper's panel letters
@@ -41,6 +42,11 @@ PARAM_FIELDS = ["mass_msun", "radius_km", "spin_hz", "incl_rad", "dist_kpc", "nh
 class ppm_params(C.Structure):
     _fields_ = [("B", C.c_int), ("n_spots", C.c_int), ("oblate", C.c_int),
                 ("emission", C.c_int)] + [(f, C.c_void_p) for f in PARAM_FIELDS]
+
+
+class ppm_tiles(C.Structure):
+    _fields_ = [("phase_tile", C.c_int), ("waves", C.c_int), ("persistent", C.c_int),
+                ("ms", C.c_double)]
 
 
 class ppm_timing(C.Structure):
@@ -89,6 +95,10 @@ def lib() -> C.CDLL:
         "ppm_loglike_grad": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d,
                                  vp, vp, vp, vp]),
         "ppm_sync": (i, [vp, vp, d]),
+        "ppm_set_tiles": (i, [vp, C.POINTER(ppm_tiles)]),
+        "ppm_get_tiles": (i, [vp, C.POINTER(ppm_tiles)]),
+        "ppm_autotune": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp,
+                             C.POINTER(ppm_tiles)]),
         "ppm_set_timing": (i, [vp, i]),
         "ppm_get_timing": (i, [vp, C.POINTER(ppm_timing)]),
     }
@@ -157,6 +167,18 @@ def ppm_loglike_grad(ctx, params: ppm_params, res: ppm_res, counts, counts_share
                      logL, grad, inst_status, stream) -> int:
     return lib().ppm_loglike_grad(ctx, C.byref(params), C.byref(res), counts, counts_shared,
                                   bkg, tau, logL, grad, inst_status, stream)
+
+
+def ppm_set_tiles(ctx, t: ppm_tiles) -> int:
+    return lib().ppm_set_tiles(ctx, C.byref(t))
+
+
+def ppm_get_tiles(ctx, t: ppm_tiles) -> int:
+    return lib().ppm_get_tiles(ctx, C.byref(t))
+
+
+def ppm_autotune(ctx, params: ppm_params, res: ppm_res, stream, best: ppm_tiles) -> int:
+    return lib().ppm_autotune(ctx, C.byref(params), C.byref(res), stream, C.byref(best))
 
 
 def ppm_sync(ctx, stream, timeout_s: float) -> int:

@@ -89,6 +89,11 @@ struct ppm_ctx {
     // response
     int nc = 0;
     DevBuf d_R, d_sigma, d_Rtc;  // d_Rtc: R split into bf16 hi/lo tiles for the tensor cores
+    // work decomposition of the shift-and-add (ppm_set_tiles / ppm_autotune)
+    int tile_pt = 0;          // output phases per item: 0 = automatic, 16 or 32
+    int tile_waves = 16;      // target waves of 2 blocks per SM (sets the ring-group size)
+    int tile_persistent = 0;  // 1: persistent blocks take items from a queue
+    int *d_queue = nullptr;
     // plan
     std::vector<int> plan_key;
     HostPlan plan;
@@ -199,7 +204,8 @@ ppm_status ppm_create(ppm_ctx **out, int device)
             return PPM_ENOMEM;
         }
     }
-    if (cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMalloc(&ctx->d_queue, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_err, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ctx->d_err, 0, sizeof(unsigned)) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->plan_ev, cudaEventDisableTiming) != cudaSuccess) {
         ppm_destroy(ctx);
@@ -220,6 +226,7 @@ void ppm_destroy(ppm_ctx *ctx)
         b->release();
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_queue) cudaFree(ctx->d_queue);
     if (ctx->d_lfact) cudaFree(ctx->d_lfact);
     if (ctx->d_triples) cudaFree(ctx->d_triples);
     for (auto &pd : ctx->pending) ctx->ev_pool.push_back(pd.a), ctx->ev_pool.push_back(pd.b);
@@ -450,6 +457,8 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(res->n_fp);
     key.push_back(ctx->sm_count);
     key.push_back((int)ctx->E.size());
+    key.push_back(ctx->tile_pt);
+    key.push_back(ctx->tile_waves);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -467,19 +476,21 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         return T;
     };
     int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
+    if (ctx->tile_pt == 16 || ctx->tile_pt == 32) pt = ctx->tile_pt;
     if (const char *env = getenv("PPM_PHASE_TILE")) {
         const int v = atoi(env);
         if (v == 16 || v == 32) pt = v;
     }
     hp.pt = pt;
     // ring groups sized by work (elements x phases x energies), aiming at
-    // ~16 waves of 2 blocks per SM; instances of very different resolution
-    // then give items of comparable cost
+    // tile_waves (default 16) waves of 2 blocks per SM; instances of very
+    // different resolution then give items of comparable cost
     const double nE = (double)ctx->E.size();
     double total = 0.0;
     for (int b = 0; b < B; ++b)
         total += (double)p->n_spots * res->n_theta[b] * res->n_phi[b] * res->n_phase[b] * nE;
-    const double target = std::max(1.0, total / ((double)ctx->sm_count * 2.0 * 16.0));
+    const double target =
+        std::max(1.0, total / ((double)ctx->sm_count * 2.0 * (double)ctx->tile_waves));
     hp.inst.resize(B);
     for (int b = 0; b < B; ++b) {
         InstPlan &ip = hp.inst[b];
@@ -622,6 +633,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     plan->tile_items = reinterpret_cast<const int2 *>(d + b_inst + b_items);
     plan->order = reinterpret_cast<const int *>(
         d + b_inst + b_items + align256(hp.tiles.size() * sizeof(int2)));
+    plan->queue = ctx->tile_persistent ? ctx->d_queue : nullptr;
     const ppm_lens_spec &s = ctx->lens;
     L->u_min = s.u_min; L->u_max = s.u_max; L->n_u = s.n_u;
     L->cpsi_min = s.cpsi_min; L->cpsi_max = s.cpsi_max; L->n_cpsi = s.n_cpsi;
@@ -669,7 +681,7 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
     {
         StageTimer t(ctx, 1, st);
         PPM_CUDA(launch_shift_add(P, plan, A, en, w->recs, w->tmpl, w->elems, w->status,
-                                  w->partials, ctx->plan.n_phi_max, st),
+                                  w->partials, ctx->plan.n_phi_max, st, 2 * ctx->sm_count),
                  "shift-and-add kernel");
         t.done(1);
     }
@@ -845,6 +857,87 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         PPM_CUDA(cudaMemcpyAsync(inst_status, w.status, sizeof(int) * p->B,
                                  cudaMemcpyDeviceToDevice, st),
                  "copy status");
+    ctx->err.clear();
+    return PPM_OK;
+}
+
+ppm_status ppm_set_tiles(ppm_ctx *ctx, const ppm_tiles *t)
+{
+    if (!ctx || !t) return fail(ctx, PPM_EINVAL, "null argument");
+    if (!(t->phase_tile == 0 || t->phase_tile == 16 || t->phase_tile == 32))
+        return fail(ctx, PPM_EINVAL, "phase_tile must be 0, 16 or 32");
+    if (t->waves < 1 || t->waves > 256) return fail(ctx, PPM_EINVAL, "waves must be in [1, 256]");
+    if (t->persistent != 0 && t->persistent != 1)
+        return fail(ctx, PPM_EINVAL, "persistent must be 0 or 1");
+    ctx->tile_pt = t->phase_tile;
+    ctx->tile_waves = t->waves;
+    ctx->tile_persistent = t->persistent;
+    return PPM_OK;
+}
+
+ppm_status ppm_get_tiles(ppm_ctx *ctx, ppm_tiles *t)
+{
+    if (!ctx || !t) return fail(ctx, PPM_EINVAL, "null argument");
+    t->phase_tile = ctx->tile_pt;
+    t->waves = ctx->tile_waves;
+    t->persistent = ctx->tile_persistent;
+    t->ms = 0.0;
+    return PPM_OK;
+}
+
+ppm_status ppm_autotune(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, void *stream,
+                        ppm_tiles *best)
+{
+    if (!ctx) return PPM_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool timing = ctx->timing;
+    ctx->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PPM_CUDA(cudaEventCreate(&e0), "event");
+    PPM_CUDA(cudaEventCreate(&e1), "event");
+    ppm_tiles cur{ctx->tile_pt, ctx->tile_waves, ctx->tile_persistent, 0.0};
+    ppm_tiles top = cur;
+    top.ms = INFINITY;
+    ppm_status s = PPM_OK;
+    const int pts[] = {16, 32}, waves[] = {8, 16, 32}, pers[] = {0, 1};
+    for (int a : pts)
+        for (int wv : waves)
+            for (int q : pers) {
+                if (s != PPM_OK) break;
+                ctx->tile_pt = a;
+                ctx->tile_waves = wv;
+                ctx->tile_persistent = q;
+                Work w;
+                // one untimed pass (plan, workspace), then one timed pass
+                for (int rep = 0; rep < 2 && s == PPM_OK; ++rep) {
+                    if (rep == 1 && cudaEventRecord(e0, st) != cudaSuccess) s = PPM_ECUDA;
+                    if (s == PPM_OK) s = run_profile(ctx, p, res, nullptr, true, st, &w);
+                    if (rep == 1 && s == PPM_OK && cudaEventRecord(e1, st) != cudaSuccess)
+                        s = PPM_ECUDA;
+                }
+                if (s != PPM_OK) break;
+                float ms = 0.0f;
+                if (cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    s = fail(ctx, PPM_ECUDA, "autotune timing failed");
+                    break;
+                }
+                if (ms < top.ms) top = ppm_tiles{a, wv, q, (double)ms};
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->timing = timing;
+    if (s != PPM_OK) {
+        ctx->tile_pt = cur.phase_tile;
+        ctx->tile_waves = cur.waves;
+        ctx->tile_persistent = cur.persistent;
+        return s;
+    }
+    ctx->tile_pt = top.phase_tile;
+    ctx->tile_waves = top.waves;
+    ctx->tile_persistent = top.persistent;
+    if (best) *best = top;
     ctx->err.clear();
     return PPM_OK;
 }
@@ -1096,6 +1189,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     plan.items = reinterpret_cast<const Item *>(dev + L.o_items);
     plan.tile_items = reinterpret_cast<const int2 *>(dev + L.o_tiles);
     plan.order = nullptr;
+    plan.queue = nullptr;
     const ppm_lens_spec &ls = ctx->lens;
     LensDev Ld;
     Ld.u_min = ls.u_min; Ld.u_max = ls.u_max; Ld.n_u = ls.n_u;

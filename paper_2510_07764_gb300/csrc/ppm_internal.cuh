@@ -104,6 +104,7 @@ struct PlanDev {
     const Item *items;
     const int2 *tile_items;  // [sum tiles] item range of (instance, tile)
     const int *order;        // launch order of the items (largest first); null = identity
+    int *queue;              // persistent schedule: next-entry counter (null = one block per item)
 };
 
 // Energy-side arrays (device).
@@ -127,10 +128,11 @@ cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
 
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max);
+// grid_blocks: resident blocks of the persistent schedule (ignored without plan.queue)
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
-                             int n_phi_max, cudaStream_t st);
+                             int n_phi_max, cudaStream_t st, int grid_blocks = 0);
 
 cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
                           const int *status, int total_rows, float *Ft, cudaStream_t st);

@@ -335,7 +335,18 @@ __global__ void __launch_bounds__(kSABlock, 2)
                 float *__restrict__ partials)
 {
     extern __shared__ float sm[];
-    const int item_id = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
+    __shared__ int s_next;
+    // static schedule: block b runs item order[b]; persistent schedule
+    // (plan.queue): blocks take the next entry of the order from a counter
+    for (int slot = blockIdx.x;;) {
+    if (plan.queue) {
+        __syncthreads();  // the previous item's tile has been written out
+        if (threadIdx.x == 0) s_next = atomicAdd(plan.queue, 1);
+        __syncthreads();
+        slot = s_next;
+        if (slot >= plan.n_items) break;
+    }
+    const int item_id = plan.order ? plan.order[slot] : slot;
     const Item it = plan.items[item_id];
     const InstPlan ip = plan.inst[it.b];
     const int n_fp = plan.n_fp;
@@ -492,6 +503,8 @@ __global__ void __launch_bounds__(kSABlock, 2)
     __syncthreads();
     float *dst = partials + (size_t)item_id * pt * nEpad;
     for (int i = tid; i < it.nj * nEpad; i += blockDim.x) dst[i] = Fblk[i];
+    if (!plan.queue) break;
+    }
 }
 
 // F_t[row][k] = (sum over the work items of (instance, phase tile)) / E_k.
@@ -569,9 +582,17 @@ size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
-                             int n_phi_max, cudaStream_t st)
+                             int n_phi_max, cudaStream_t st, int grid_blocks)
 {
     if (plan.n_items <= 0) return cudaSuccess;
+    // persistent schedule: the queue counter must start at zero on the stream
+    if (plan.queue) {
+        cudaError_t e0 = cudaMemsetAsync(plan.queue, 0, sizeof(int), st);
+        if (e0 != cudaSuccess) return e0;
+        grid_blocks = std::max(1, std::min(grid_blocks, plan.n_items));
+    } else {
+        grid_blocks = plan.n_items;
+    }
     Layout lay;
     int off = 0;
     auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
@@ -590,10 +611,11 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (r != cudaSuccess) return r;
-        kern<<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, status,
-                                                    partials);
+        kern<<<grid_blocks, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, status,
+                                                   partials);
         return cudaSuccess;
     };
+    (void)grid_blocks;
     if (p.emission == 0) e = go(k_shift_add<0, 0>);
     else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1>);
     else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2>);

@@ -1,0 +1,102 @@
+"""Batched evaluation machinery: the persistent work-queue schedule, the tile
+autotuner and CUDA-graph capture of a likelihood call."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import context
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(synth, atm, small_lens, B=12):
+    w = synth.atm_two_spot(n_theta=12, n_phi=16, n_phase=32, n_E=64, n_chan=40, atm=atm,
+                           lens=small_lens)
+    inst = w.inst.select(np.zeros(B, dtype=int))
+    inst.n_theta[:] = np.resize([12, 20, 8], B)
+    inst.n_phi[:] = np.resize([16, 24, 12], B)
+    inst.n_phase[:] = np.resize([32, 16, 48], B)
+    inst.incl_rad[:] = np.linspace(0.4, 1.4, B)
+    rows = int(inst.n_phase.sum())
+    rng = np.random.default_rng(3)
+    counts = rng.poisson(20.0, (rows, w.nc)).astype(np.int32)
+    return synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R,
+                          sigma_ism=w.sigma_ism, counts=counts, tau=w.tau)
+
+
+def _profile(ctx, dp):
+    Ft = ctx.profile(dp)
+    ctx.sync()
+    return Ft.cpu().numpy()
+
+
+def test_persistent_schedule_is_bitwise_identical(synth, atm, small_lens):
+    import paper_2510_07764_gb300 as ppm
+    w = _batch(synth, atm, small_lens)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    try:
+        for pt in (16, 32):
+            ctx.set_tiles(pt, 16, False)
+            a = _profile(ctx, dp)
+            ctx.set_tiles(pt, 16, True)
+            b = _profile(ctx, dp)
+            assert np.array_equal(a, b)
+    finally:
+        ctx.set_tiles()
+
+
+def test_autotune_chooses_a_candidate_and_keeps_results(synth, atm, small_lens):
+    import paper_2510_07764_gb300 as ppm
+    w = _batch(synth, atm, small_lens)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    ref = _profile(ctx, dp)
+    try:
+        best = ctx.autotune(dp)
+        assert best["phase_tile"] in (16, 32) and best["waves"] in (8, 16, 32)
+        assert math.isfinite(best["ms"]) and best["ms"] > 0.0
+        assert ctx.get_tiles()["phase_tile"] == best["phase_tile"]
+        got = _profile(ctx, dp)
+        # a different decomposition only regroups the FP32 partial sums
+        m = np.abs(ref) > 1e-6 * np.abs(ref).max()
+        assert np.max(np.abs(got[m] / ref[m] - 1.0)) < 1e-5
+    finally:
+        ctx.set_tiles()
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_cuda_graph_replay_follows_parameter_updates(synth, atm, small_lens, persistent):
+    """ppm_loglike captured once in a CUDA graph and replayed after the
+    parameter tensors are overwritten in place gives the direct call's result."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    w = _batch(synth, atm, small_lens, B=6)
+    ctx = context(w)
+    ctx.set_tiles(0, 16, persistent)
+    try:
+        dp = ppm.DeviceParams(w.inst)
+        cnt = torch.from_numpy(w.counts).cuda()
+        out = torch.empty(dp.B, dtype=torch.float64, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for _ in range(2):   # plan, workspace and kernel attributes settle before capture
+                ctx.loglike(dp, cnt, w.tau, out=out, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            ctx.loglike(dp, cnt, w.tau, out=out, stream=s)
+        th0 = dp.theta()
+        for k in range(3):
+            th = th0.clone()
+            th[:, 2] += 0.05 * k          # inclination
+            th[:, 0] += 0.02 * k          # mass
+            dp.set_theta(th)
+            g.replay()
+            torch.cuda.synchronize()
+            got = out.cpu().numpy().copy()
+            ref = ctx.loglike(dp, cnt, w.tau).cpu().numpy()
+            assert np.array_equal(got, ref)
+    finally:
+        ctx.set_tiles()
