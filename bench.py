@@ -65,11 +65,29 @@ def parse():
     return ap.parse_args()
 
 
-def make_workload(args):
+def make_workload(args, rank: int = 0):
+    """The workload of one rank.  Batched workloads draw their own parameter
+    vectors per rank (seed offset by the rank: weak scaling over independent
+    instances); single-instance workloads are replicas."""
     from paper_2510_07764_gb300 import synth
-    if args.batch is not None and args.workload in ("batch", "grad_batch"):
-        return synth.WORKLOADS[args.workload](B=args.batch)
+    if args.workload in ("batch", "grad_batch"):
+        kw = {"seed": synth.SEED + (1 if args.workload == "grad_batch" else 0) + rank}
+        if args.batch is not None:
+            kw["B"] = args.batch
+        return synth.WORKLOADS[args.workload](**kw)
     return synth.WORKLOADS[args.workload]()
+
+
+def max_over_ranks(values, device=None):
+    """Element-wise maximum of a list of floats over all ranks (the job's
+    time is its slowest rank's); identity without torch.distributed."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
 
 
 def workload_desc(w):
@@ -248,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = make_workload(args)
+    w = make_workload(args, rank)
     grad_mode = args.workload == "grad_batch"
     ctx = ppm.Context(local_rank)
     t0 = time.perf_counter()
@@ -383,10 +401,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     e2e_ms = sum(a.elapsed_time(b) for a, b in evs2)
 
-    if dist:
-        t = torch.tensor([dev_ms, e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dev_ms, e2e_ms = float(t[0]), float(t[1])
+    dev_ms, e2e_ms = max_over_ranks([dev_ms, e2e_ms], device=dev)
     if rank != 0:
         return
     units = world * args.steps * B
