@@ -150,6 +150,21 @@ ppm_status ppm_set_energies(ppm_ctx *ctx, const double *E_keV, int nE);
 ppm_status ppm_set_response(ppm_ctx *ctx, const float *R, int nE, int nc,
                             const float *sigma_ism);
 
+/* Response from a fine detector grid (Sect. 2.7, the down-sampling matrix
+ * DS and Eq. RSP): Ne detector energy bins [E_lo[e], E_hi[e]] (host, keV,
+ * E_lo < E_hi), the fine response Rf[Ne][nc] (host row-major float32:
+ * effective area x redistribution, per bin) and sigma_ism[nE] on the model
+ * grid.  The library builds, in FP64 on the host,
+ *   DS[i][e] = integral over [E_lo[e], E_hi[e]] of the piecewise-linear
+ *              interpolant on the model grid that is 1 at E_i and 0 at the
+ *              other nodes (constant beyond the grid ends),
+ *   R[i][c]  = sum_e DS[i][e] Rf[e][c],
+ * and installs R as ppm_set_response does (the attenuation ATT_i stays a
+ * per-instance factor applied at run time).  1 <= Ne <= 1<<20; nE is the
+ * model grid size set by ppm_set_energies.  Copied; synchronous. */
+ppm_status ppm_set_response_fine(ppm_ctx *ctx, const double *E_lo, const double *E_hi, int Ne,
+                                 const float *Rf, int nc, const float *sigma);
+
 /* ------------------------------------------------------------------------
  * Parameter vectors: structure of arrays of DEVICE pointers, B instances.
  * Per instance (length B): mass_msun, radius_km (equatorial), spin_hz,

@@ -380,3 +380,24 @@ def grad_tangent(w, b: int = 0):
         e[j] = 1.0
         g[j] = loglike_tangent(w, e, b)[1]
     return g
+
+
+# ---------------------------------------------------------------------------
+# response down-sampling (Sect. 2.7, matrix DS)
+# ---------------------------------------------------------------------------
+def downsample_matrix(E_model, E_lo, E_hi) -> np.ndarray:
+    """DS[i, e] = integral over detector bin e of the linear interpolant on
+    E_model that is 1 at node i and 0 at the others (np.interp: constant
+    beyond the ends).  Written from the definition: the bin is cut at every
+    model node inside it, where the integrand is linear, and each piece is
+    integrated exactly by its midpoint value."""
+    Eo = np.asarray(E_model, dtype=np.float64)
+    n = len(Eo)
+    eye = np.eye(n)
+    DS = np.zeros((n, len(E_lo)))
+    for e, (a, b) in enumerate(zip(E_lo, E_hi)):
+        cuts = np.unique(np.concatenate([[a, b], Eo[(Eo > a) & (Eo < b)]]))
+        for x0, x1 in zip(cuts[:-1], cuts[1:]):
+            mid = 0.5 * (x0 + x1)
+            DS[:, e] += (x1 - x0) * np.array([np.interp(mid, Eo, eye[i]) for i in range(n)])
+    return DS

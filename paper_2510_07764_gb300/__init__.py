@@ -177,6 +177,17 @@ class Context:
         self._check(_abi.ppm_set_response(self.h, _dp(R), R.shape[0], R.shape[1], _dp(sg)))
         self.nc = R.shape[1]
 
+    def set_response_fine(self, E_lo, E_hi, Rf, sigma):
+        """Response from a fine detector grid through the down-sampling matrix
+        (see ppm_set_response_fine); Rf is [Ne, nc]."""
+        lo = np.ascontiguousarray(E_lo, dtype=np.float64)
+        hi = np.ascontiguousarray(E_hi, dtype=np.float64)
+        Rf = np.ascontiguousarray(Rf, dtype=np.float32)
+        sg = np.ascontiguousarray(sigma, dtype=np.float32)
+        self._check(_abi.ppm_set_response_fine(self.h, _dp(lo), _dp(hi), len(lo), _dp(Rf),
+                                               Rf.shape[1], _dp(sg)))
+        self.nc = Rf.shape[1]
+
     def setup(self, w, build_lens: bool = True):
         """Load every table of a synthetic workload (``synth.Workload``)."""
         if build_lens:

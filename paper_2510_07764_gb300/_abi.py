@@ -21,7 +21,7 @@ EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
            "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
            "ppm_profile_noalloc", "ppm_loglike_grad", "ppm_set_interpolation",
-           "ppm_set_tiles", "ppm_get_tiles", "ppm_autotune"]
+           "ppm_set_tiles", "ppm_get_tiles", "ppm_autotune", "ppm_set_response_fine"]
 
 # interpolation strategies of Sect. 4 (PPM_INTERP_* in ppm.h), keyed by the
 # paper's panel letters
@@ -88,6 +88,7 @@ def lib() -> C.CDLL:
         "ppm_set_energies": (i, [vp, vp, i]),
         "ppm_set_interpolation": (i, [vp, i]),
         "ppm_set_response": (i, [vp, vp, i, i, vp]),
+        "ppm_set_response_fine": (i, [vp, vp, vp, i, vp, i, vp]),
         "ppm_profile": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
         "ppm_profile_noalloc": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, vp, vp]),
         "ppm_loglike": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d, vp, vp,
@@ -147,6 +148,10 @@ def ppm_set_energies(ctx, E, nE) -> int:
 
 def ppm_set_response(ctx, R, nE, nc, sigma) -> int:
     return lib().ppm_set_response(ctx, R, nE, nc, sigma)
+
+
+def ppm_set_response_fine(ctx, E_lo, E_hi, Ne, Rf, nc, sigma) -> int:
+    return lib().ppm_set_response_fine(ctx, E_lo, E_hi, Ne, Rf, nc, sigma)
 
 
 def ppm_profile(ctx, params: ppm_params, res: ppm_res, Ft, inst_status, stream) -> int:

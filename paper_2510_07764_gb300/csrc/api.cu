@@ -384,6 +384,58 @@ ppm_status ppm_set_response(ppm_ctx *ctx, const float *R, int nE, int nc, const 
     return PPM_OK;
 }
 
+// Down-sampling matrix row block: DS[i][e] for the model grid x[0..n) and one
+// detector bin [a, b].  The basis function of node i is the piecewise-linear
+// hat on x, continued as a constant beyond the two ends.  Closed-form
+// integrals of the linear pieces; adds into ds[i].
+static void ds_bin(const double *x, int n, double a, double b, double *ds)
+{
+    if (!(b > a)) return;
+    if (n == 1) { ds[0] += b - a; return; }
+    if (a < x[0]) ds[0] += std::min(b, x[0]) - a;
+    if (b > x[n - 1]) ds[n - 1] += b - std::max(a, x[n - 1]);
+    const double lo = std::max(a, x[0]), hi = std::min(b, x[n - 1]);
+    if (!(hi > lo)) return;
+    int j = (int)(std::upper_bound(x, x + n, lo) - x) - 1;
+    j = std::min(std::max(j, 0), n - 2);
+    for (; j < n - 1 && x[j] < hi; ++j) {
+        const double x0 = std::max(lo, x[j]), x1 = std::min(hi, x[j + 1]);
+        if (!(x1 > x0)) continue;
+        const double h = x[j + 1] - x[j];
+        const double r0 = x[j + 1] - x0, r1 = x[j + 1] - x1;   // distances to the right node
+        const double l0 = x0 - x[j], l1 = x1 - x[j];           // distances to the left node
+        ds[j] += (r0 * r0 - r1 * r1) / (2.0 * h);
+        ds[j + 1] += (l1 * l1 - l0 * l0) / (2.0 * h);
+    }
+}
+
+ppm_status ppm_set_response_fine(ppm_ctx *ctx, const double *E_lo, const double *E_hi, int Ne,
+                                 const float *Rf, int nc, const float *sigma)
+{
+    if (!ctx || !E_lo || !E_hi || !Rf || !sigma) return fail(ctx, PPM_EINVAL, "null argument");
+    const int nE = (int)ctx->E.size();
+    if (nE < 1) return fail(ctx, PPM_EINVAL, "energy grid not set");
+    if (Ne < 1 || Ne > (1 << 20)) return fail(ctx, PPM_EINVAL, "need 1 <= Ne <= 1048576");
+    if (nc < 1 || nc > 4096) return fail(ctx, PPM_EINVAL, "need 1 <= nc <= 4096");
+    for (int e = 0; e < Ne; ++e)
+        if (!(E_hi[e] > E_lo[e]) || !std::isfinite(E_lo[e]) || !std::isfinite(E_hi[e]))
+            return fail(ctx, PPM_EINVAL, "detector bin %d: need finite E_lo < E_hi", e);
+    std::vector<double> R((size_t)nE * nc, 0.0), ds(nE);
+    for (int e = 0; e < Ne; ++e) {
+        std::fill(ds.begin(), ds.end(), 0.0);
+        ds_bin(ctx->E.data(), nE, E_lo[e], E_hi[e], ds.data());
+        const float *rf = Rf + (size_t)e * nc;
+        for (int i = 0; i < nE; ++i) {
+            if (ds[i] == 0.0) continue;
+            double *r = R.data() + (size_t)i * nc;
+            for (int c = 0; c < nc; ++c) r[c] += ds[i] * (double)rf[c];
+        }
+    }
+    std::vector<float> Rs(R.size());
+    for (size_t q = 0; q < R.size(); ++q) Rs[q] = (float)R[q];
+    return ppm_set_response(ctx, Rs.data(), nE, nc, sigma);
+}
+
 // ---------------------------------------------------------------------------
 // planning and launch
 // ---------------------------------------------------------------------------

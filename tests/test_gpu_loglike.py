@@ -131,3 +131,33 @@ def test_tensor_core_and_fp32_paths_agree_on_a_batch(synth, atm, small_lens):
     for b in range(24):
         d = w2.counts[rows_of(w2, b)]
         assert abs(ll_tc[b] - ll_32[b]) <= 1e-4 * np.sum(np.abs(d - mc_32[rows_of(w2, b)])) + 1e-6
+
+
+def test_fine_grid_response_through_downsampling(orc, synth, atm, small_lens):
+    """ppm_set_response_fine (the library's FP64 DS x Rf) against the oracle's
+    down-sampling matrix applied to the same fine response: same model counts
+    and logL as installing the oracle's product with ppm_set_response."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = synth.atm_two_spot(n_theta=10, n_phi=16, n_phase=32, n_E=48, n_chan=40, atm=atm,
+                           lens=small_lens)
+    rng = np.random.default_rng(9)
+    edges = np.linspace(0.08, 5.6, 301)          # 300 detector bins, past both grid ends
+    lo, hi = edges[:-1], edges[1:]
+    mid = 0.5 * (lo + hi)
+    Rf = (np.exp(-0.5 * ((mid[:, None] - np.linspace(0.1, 5.5, 40)[None, :]) / 0.08) ** 2)
+          * (1000.0 + 200.0 * rng.standard_normal(1)[0])).astype(np.float32)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    mc1 = torch.empty((dp.rows, 40), dtype=torch.float32, device="cuda")
+    mc2 = torch.empty_like(mc1)
+    ctx.set_response_fine(lo, hi, Rf, w.sigma_ism)
+    ll1 = ctx.loglike(dp, cnt, w.tau, model_counts=mc1).cpu().numpy()
+    R = (orc.downsample_matrix(w.E_keV, lo, hi) @ Rf.astype(np.float64)).astype(np.float32)
+    ctx.set_response(R, w.sigma_ism)
+    ll2 = ctx.loglike(dp, cnt, w.tau, model_counts=mc2).cpu().numpy()
+    ctx.set_response(w.R, w.sigma_ism)
+    assert max_rel(mc1.cpu().numpy(), mc2.cpu().numpy()) < 1e-6
+    assert abs(ll1[0] - ll2[0]) <= 1e-6 * abs(ll2[0])

@@ -68,3 +68,46 @@ def test_chi2_approximates_minus_two_delta_loglike(orc):
     chi2_d = np.sum((d - d_model) ** 2 / d_model) - np.sum((d - m) ** 2 / m)
     assert -2 * dlnL == pytest.approx(chi2_d, rel=0.02)
     assert chi2 > 0
+
+
+def _fine_grid(E, n=150, seed=4):
+    rng = np.random.default_rng(seed)
+    edges = np.sort(rng.uniform(E[0] * 0.8, E[-1] * 1.1, n + 1))
+    return edges[:-1], edges[1:]
+
+
+def test_downsample_partition_of_unity(orc):
+    """The basis functions sum to one everywhere, so each detector bin's
+    column of DS sums to the bin width (bins inside and beyond the grid)."""
+    E = np.geomspace(0.2, 5.0, 40)
+    lo, hi = _fine_grid(E)
+    DS = orc.downsample_matrix(E, lo, hi)
+    np.testing.assert_allclose(DS.sum(axis=0), hi - lo, rtol=1e-12)
+    assert np.all(DS >= 0.0)
+
+
+def test_downsample_integrates_linear_functions_exactly(orc):
+    """Inside the grid the interpolant of a linear function is the function,
+    so sum_i f(E_i) DS[i, e] is its exact integral over the bin."""
+    E = np.geomspace(0.2, 5.0, 40)
+    lo, hi = _fine_grid(E, seed=7)
+    keep = (lo > E[0]) & (hi < E[-1])
+    DS = orc.downsample_matrix(E, lo[keep], hi[keep])
+    f = lambda x: 3.0 - 0.7 * x
+    exact = 3.0 * (hi - lo)[keep] - 0.35 * (hi[keep] ** 2 - lo[keep] ** 2)
+    np.testing.assert_allclose(f(E) @ DS, exact, rtol=1e-12, atol=1e-14)
+
+
+def test_downsample_matches_quadrature(orc):
+    """Against scipy's adaptive quadrature of np.interp of the unit vectors."""
+    from scipy.integrate import quad
+    E = np.geomspace(0.2, 5.0, 12)
+    lo, hi = np.array([0.1, 0.33, 1.0, 4.7]), np.array([0.25, 0.61, 1.02, 6.0])
+    DS = orc.downsample_matrix(E, lo, hi)
+    eye = np.eye(len(E))
+    for i in range(len(E)):
+        for e in range(len(lo)):
+            pts = E[(E > lo[e]) & (E < hi[e])]
+            q, _ = quad(lambda x: np.interp(x, E, eye[i]), lo[e], hi[e],
+                        points=pts if len(pts) else None, epsabs=1e-13)
+            assert DS[i, e] == pytest.approx(q, abs=1e-12)
