@@ -186,15 +186,23 @@ typedef struct {
     const double *mask_colat, *mask_azim, *mask_zeta;
 } ppm_params;
 
-/* Per-instance resolution: HOST arrays of length B.  Each spot is covered by
- * n_theta rings uniform in colatitude over its angular extent, each ring by
- * n_phi elements uniform over the spot's azimuthal width (1 <= n_theta <=
- * 4096, 1 <= n_phi <= 4096); n_phase output phases j / n_phase (1 <= n_phase
- * <= 4096).  n_fp fine template phases per ring (8 <= n_fp <= 1024; the
- * paper uses 192). */
+/* Per-instance resolution: HOST arrays of length B, and the surface grid.
+ * grid = PPM_GRID_SPOT: each spot is covered by n_theta rings uniform in
+ * colatitude over its angular extent, each ring by n_phi elements uniform
+ * over the spot's azimuthal width (1 <= n_theta <= 4096, 1 <= n_phi <= 4096).
+ * grid = PPM_GRID_HEALPIX (Sect. 2.6): the whole surface is the HEALPix mesh
+ * with N_side = n_theta[b] (1 <= N_side <= 1024; 4 N_side - 1 rings of up
+ * to 4 N_side equal-area pixels, n_phi ignored); a spot is the set of pixels
+ * whose centres lie within zeta of its centre and outside its mask.  The
+ * mesh does not move with the spot, so spot geometry enters only through
+ * which pixels are selected (ppm_loglike_grad rejects this grid).
+ * n_phase output phases j / n_phase (1 <= n_phase <= 4096).  n_fp fine
+ * template phases per ring (8 <= n_fp <= 1024; the paper uses 192). */
+enum { PPM_GRID_SPOT = 0, PPM_GRID_HEALPIX = 1 };
 typedef struct {
     const int *n_theta, *n_phi, *n_phase;
     int n_fp;
+    int grid;   /* PPM_GRID_SPOT or PPM_GRID_HEALPIX */
 } ppm_res;
 
 /* ------------------------------------------------------------------------

@@ -76,7 +76,8 @@ class InstC(C.Structure):
                 ("logT", C.c_double * 2), ("mask_colat", C.c_double * 2),
                 ("mask_azim", C.c_double * 2), ("mask_zeta", C.c_double * 2),
                 ("n_spots", C.c_int), ("oblate", C.c_int), ("emission", C.c_int),
-                ("n_theta", C.c_int), ("n_phi", C.c_int), ("n_phase", C.c_int), ("n_fp", C.c_int)]
+                ("n_theta", C.c_int), ("n_phi", C.c_int), ("n_phase", C.c_int), ("n_fp", C.c_int),
+                ("grid", C.c_int)]
 
 
 def lib():
@@ -251,6 +252,7 @@ def inst_c(inst, b: int = 0) -> InstC:
     c.n_spots = inst.n_spots; c.oblate = inst.oblate; c.emission = inst.emission
     c.n_theta = int(inst.n_theta[b]); c.n_phi = int(inst.n_phi[b])
     c.n_phase = int(inst.n_phase[b]); c.n_fp = int(inst.n_fp)
+    c.grid = int(getattr(inst, "grid", 0))
     return c
 
 

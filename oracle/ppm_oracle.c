@@ -492,6 +492,7 @@ typedef struct {
     real mass_msun, radius_km, spin_hz, incl_rad, dist_kpc, nh_1e20;
     real colat[2], azim[2], zeta[2], logT[2], mask_colat[2], mask_azim[2], mask_zeta[2];
     int n_spots, oblate, emission, n_theta, n_phi, n_phase, n_fp;
+    int grid;  /* 0: spot-bounding grid; 1: HEALPix whole-surface mesh, N_side = n_theta */
 } orc_inst;
 
 typedef struct {
@@ -586,6 +587,85 @@ static int element_active(const orc_inst *in, int spot, real theta_r, real phi_r
     double cd = cos(theta) * cos(RE(in->mask_colat[spot])) +
                 sin(theta) * sin(RE(in->mask_colat[spot])) * cos(phi - RE(in->mask_azim[spot]));
     return !(cd > cos(mz));
+}
+
+/* One ring of a spot's elements: colatitude, the cos(theta) width and the
+ * azimuth step whose product is the element's solid angle, the first element
+ * azimuth, the element count, and whether element membership needs the
+ * emitter-cap test (the HEALPix mesh is not aligned with the spot).
+ *
+ * grid 0 (reading of the element grid): ring_of_spot above.
+ * grid 1 (Sect. 2.6, the HEALPix scheme of Gorski et al. 2005 with
+ * N = N_side): ring i = 1 .. 4N-1 has
+ *   z = 1 - i^2/(3N^2) and 4i pixels                (i < N),
+ *   z = 4/3 - 2i/(3N) and 4N pixels                 (N <= i <= 3N),
+ *   z = -(1 - (4N-i)^2/(3N^2)) and 4(4N-i) pixels   (i > 3N);
+ * pixel j = 1 .. n of a polar ring sits at phi = (pi/2)(j - 1/2)/i' (i' = i
+ * or 4N-i), of an equatorial ring at phi = (pi/2N)(j - s/2) with
+ * s = (i - N + 1) mod 2; every pixel has solid angle pi / (3 N^2).  A pixel
+ * belongs to the spot when its centre is within zeta of the spot centre
+ * and outside the mask (Sect. 2.6: the spot is selected on the mesh). */
+typedef struct {
+    real theta, dcos, dphi, phi0, half;
+    int n_el, cap_test, ok;
+} orc_ringdef;
+
+static int ring_count(const orc_inst *in)
+{
+    return in->grid == 1 ? 4 * in->n_theta - 1 : in->n_theta;
+}
+
+static void ring_def(const orc_inst *in, int spot, int r, orc_ringdef *d)
+{
+    if (in->grid != 1) {
+        ring_of_spot(in, spot, r, &d->theta, &d->dcos, &d->half);
+        d->dphi = 2.0 * d->half / in->n_phi;
+        d->phi0 = 0.0;
+        d->n_el = in->n_phi;
+        d->cap_test = 0;
+        d->ok = RE(d->half) > 0.0;
+        return;
+    }
+    const int N = in->n_theta, i = r + 1;
+    const double NN = (double)N;
+    double z, phi0;
+    int n;
+    if (i < N || i > 3 * N) {
+        const int ip = i < N ? i : 4 * N - i;
+        const double zz = 1.0 - (double)ip * ip / (3.0 * NN * NN);
+        z = i < N ? zz : -zz;
+        n = 4 * ip;
+        phi0 = 0.25 * ORC_PI / ip;
+    } else {
+        z = 4.0 / 3.0 - 2.0 * i / (3.0 * NN);
+        n = 4 * N;
+        const int sh = (i - N + 1) % 2;
+        phi0 = 0.5 * ORC_PI / NN * (1.0 - 0.5 * sh);
+    }
+    d->theta = acos(z);
+    d->n_el = n;
+    d->dphi = 2.0 * ORC_PI / n;
+    d->dcos = (ORC_PI / (3.0 * NN * NN)) / d->dphi;
+    d->phi0 = phi0;
+    d->half = ORC_PI;
+    d->cap_test = 1;
+    /* rings that cannot reach the cap are skipped (a decision only) */
+    d->ok = fabs(RE(d->theta) - RE(in->colat[spot])) <= RE(in->zeta[spot]) + 1e-12;
+}
+
+/* azimuth of element m of a ring */
+static real ring_phi(const orc_inst *in, int spot, const orc_ringdef *d, int m)
+{
+    if (in->grid != 1) return in->azim[spot] - d->half + (m + 0.5) * d->dphi;
+    return d->phi0 + m * d->dphi;
+}
+
+/* emitter-cap membership of a mesh element (a decision only, real parts) */
+static int inside_cap(const orc_inst *in, int spot, real theta_r, real phi_r)
+{
+    double th = RE(theta_r), ph = RE(phi_r), tc = RE(in->colat[spot]);
+    double cd = cos(th) * cos(tc) + sin(th) * sin(tc) * cos(ph - RE(in->azim[spot]));
+    return cd >= cos(RE(in->zeta[spot]));
 }
 
 /* =====================================================================
@@ -711,7 +791,7 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
                 const int *ksel, int nk, int ring_stride, real *Ft)
 {
     if (in->n_spots < 1 || in->n_spots > 2 || in->n_theta < 1 || in->n_phi < 1 ||
-        in->n_phase < 1 || in->n_fp < 2 || nE < 1)
+        in->n_phase < 1 || in->n_fp < 2 || nE < 1 || in->grid < 0 || in->grid > 1)
         return ORC_EINVAL;
     if (in->emission == 1 && A == NULL) return ORC_EINVAL;
     if (ring_stride < 1) ring_stride = 1;
@@ -733,23 +813,25 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
             status = ORC_ERANGE;
             break;
         }
-        for (int r = 0; r < in->n_theta; r += ring_stride) {
-            real theta, dcos, half;
-            ring_of_spot(in, sp, r, &theta, &dcos, &half);
-            if (!(RE(half) > 0.0)) continue;
+        for (int r = 0; r < ring_count(in); r += ring_stride) {
+            orc_ringdef rd;
+            ring_def(in, sp, r, &rd);
+            if (!rd.ok) continue;
+            const real theta = rd.theta;
             orc_ring rg;
-            ring_geom(&s, theta, dcos, &rg);
+            ring_geom(&s, theta, rd.dcos, &rg);
             if (in->emission == 1 &&
                 (RE(rg.logg) < A->logg[0] || RE(rg.logg) > A->logg[A->ng - 1])) {
                 status = ORC_ERANGE;
                 break;
             }
-            real dphi = 2.0 * half / in->n_phi;
+            const real dphi = rd.dphi;
             int tv = ring_template(&s, &rg, dphi, L, n_fp, F, z, ph, mu);
             if (tv < 0) { status = ORC_ERANGE; break; }
             if (tv == 0) continue;
-            for (int m = 0; m < in->n_phi; m++) {
-                real phia = in->azim[sp] - half + (m + 0.5) * dphi;
+            for (int m = 0; m < rd.n_el; m++) {
+                real phia = ring_phi(in, sp, &rd, m);
+                if (rd.cap_test && !inside_cap(in, sp, theta, phia)) continue;
                 if (!element_active(in, sp, theta, phia)) continue;
                 real sm = phia / (2.0 * ORC_PI);
                 for (int jj = 0; jj < NJ; jj++) {
@@ -784,20 +866,23 @@ int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
 {
     orc_star s;
     star_init(in, &s);
-    real theta, dcos, half;
-    ring_of_spot(in, spot, r, &theta, &dcos, &half);
+    orc_ringdef rd;
+    ring_def(in, spot, r, &rd);
+    const real theta = rd.theta, dphi = rd.dphi;
+    const real half = rd.half;
     orc_ring rg;
-    ring_geom(&s, theta, dcos, &rg);
-    real dphi = 2.0 * half / in->n_phi;
+    ring_geom(&s, theta, rd.dcos, &rg);
     int nact = 0;
-    for (int m = 0; m < in->n_phi; m++)
-        nact += element_active(in, spot, theta, in->azim[spot] - half + (m + 0.5) * dphi);
+    for (int m = 0; m < rd.n_el; m++) {
+        const real phia = ring_phi(in, spot, &rd, m);
+        nact += (!rd.cap_test || inside_cap(in, spot, theta, phia)) &&
+                element_active(in, spot, theta, phia);
+    }
     int n = in->n_fp + 1;
     real *t = (real *)malloc(sizeof(real) * 4 * n);
-    int st = RE(half) > 0.0 ? ring_template(&s, &rg, dphi, L, in->n_fp, t, t + n, t + 2 * n,
-                                            t + 3 * n)
-                            : 0;
-    for (int i = 0; i < n && RE(half) > 0.0; i++) {
+    int st = rd.ok ? ring_template(&s, &rg, dphi, L, in->n_fp, t, t + n, t + 2 * n, t + 3 * n)
+                   : 0;
+    for (int i = 0; i < n && rd.ok; i++) {
         F[i] = RE(t[i]); z[i] = RE(t[n + i]); phio[i] = RE(t[2 * n + i]); mu[i] = RE(t[3 * n + i]);
     }
     free(t);

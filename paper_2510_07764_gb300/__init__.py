@@ -64,8 +64,9 @@ class DeviceParams:
         self.n_phase = np.ascontiguousarray(inst.n_phase, dtype=np.int32)
         self.n_fp = int(inst.n_fp)
         ip = C.POINTER(C.c_int)
+        self.grid = int(getattr(inst, "grid", 0))
         self.res = _abi.ppm_res(self.n_theta.ctypes.data_as(ip), self.n_phi.ctypes.data_as(ip),
-                                self.n_phase.ctypes.data_as(ip), self.n_fp)
+                                self.n_phase.ctypes.data_as(ip), self.n_fp, self.grid)
         self.rows = int(self.n_phase.sum())
 
     def upload(self, inst, non_blocking: bool = False):

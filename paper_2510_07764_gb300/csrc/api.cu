@@ -96,6 +96,7 @@ struct ppm_ctx {
     int *d_queue = nullptr;
     // plan
     std::vector<int> plan_key;
+    int plan_grid = 0;
     HostPlan plan;
     DevBuf d_plan;
     void *h_pinned = nullptr;
@@ -472,6 +473,16 @@ static ppm_status refresh_energies(ppm_ctx *ctx)
     return PPM_OK;
 }
 
+// rings per spot and element slots per ring of instance b
+static int rings_per_spot(const ppm_res *res, int b)
+{
+    return res->grid == PPM_GRID_HEALPIX ? 4 * res->n_theta[b] - 1 : res->n_theta[b];
+}
+static int slots_per_ring(const ppm_res *res, int b)
+{
+    return res->grid == PPM_GRID_HEALPIX ? 4 * res->n_theta[b] : res->n_phi[b];
+}
+
 static ppm_status check_params(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res)
 {
     if (!p || !res) return fail(ctx, PPM_EINVAL, "null params or res");
@@ -487,7 +498,15 @@ static ppm_status check_params(ppm_ctx *ctx, const ppm_params *p, const ppm_res 
     if (!res->n_theta || !res->n_phi || !res->n_phase)
         return fail(ctx, PPM_EINVAL, "null resolution array");
     if (res->n_fp < 8 || res->n_fp > kMaxFp) return fail(ctx, PPM_EINVAL, "need 8 <= n_fp <= 1024");
+    if (res->grid != PPM_GRID_SPOT && res->grid != PPM_GRID_HEALPIX)
+        return fail(ctx, PPM_EINVAL, "grid must be PPM_GRID_SPOT or PPM_GRID_HEALPIX");
     for (int b = 0; b < p->B; ++b) {
+        if (res->grid == PPM_GRID_HEALPIX) {
+            if (res->n_theta[b] < 1 || res->n_theta[b] > 1024 || res->n_phase[b] < 1 ||
+                res->n_phase[b] > 4096)
+                return fail(ctx, PPM_EINVAL, "instance %d: need 1 <= N_side <= 1024", b);
+            continue;
+        }
         if (res->n_theta[b] < 1 || res->n_theta[b] > 4096 || res->n_phi[b] < 1 ||
             res->n_phi[b] > 4096 || res->n_phase[b] < 1 || res->n_phase[b] > 4096)
             return fail(ctx, PPM_EINVAL, "instance %d: resolution out of range", b);
@@ -511,6 +530,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back((int)ctx->E.size());
     key.push_back(ctx->tile_pt);
     key.push_back(ctx->tile_waves);
+    key.push_back(res->grid);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -524,7 +544,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     auto ring_tiles = [&](int pt) {
         long long T = 0;
         for (int b = 0; b < B; ++b)
-            T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + pt - 1) / pt);
+            T += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + pt - 1) / pt);
         return T;
     };
     int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
@@ -540,14 +560,15 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     const double nE = (double)ctx->E.size();
     double total = 0.0;
     for (int b = 0; b < B; ++b)
-        total += (double)p->n_spots * res->n_theta[b] * res->n_phi[b] * res->n_phase[b] * nE;
+        total += (double)p->n_spots * rings_per_spot(res, b) * slots_per_ring(res, b) *
+                 res->n_phase[b] * nE;
     const double target =
         std::max(1.0, total / ((double)ctx->sm_count * 2.0 * (double)ctx->tile_waves));
     hp.inst.resize(B);
     for (int b = 0; b < B; ++b) {
         InstPlan &ip = hp.inst[b];
-        ip.n_theta = res->n_theta[b];
-        ip.n_phi = res->n_phi[b];
+        ip.n_theta = rings_per_spot(res, b);
+        ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
         ip.ring0 = hp.total_rings;
         ip.elem0 = (int)hp.total_elems;
@@ -611,6 +632,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     PPM_CUDA(cudaEventRecord(ctx->plan_ev, st), "plan event");
     ctx->plan = std::move(hp);
     ctx->plan_key = std::move(key);
+    ctx->plan_grid = res->grid;
     return PPM_OK;
 }
 
@@ -679,6 +701,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     const size_t b_items = align256(hp.items.size() * sizeof(Item));
     char *d = ctx->d_plan.as<char>();
     plan->B = p->B; plan->n_fp = n_fp; plan->n_items = (int)hp.items.size(); plan->pt = hp.pt;
+    plan->grid = ctx->plan_grid;
     plan->total_rings = hp.total_rings;
     plan->inst = reinterpret_cast<const InstPlan *>(d);
     plan->items = reinterpret_cast<const Item *>(d + b_inst);
@@ -844,6 +867,8 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     ppm_status s = check_loglike_args(ctx, p, res, counts, counts_shared, tau, logL);
     if (s != PPM_OK) return s;
     if (!grad) return fail(ctx, PPM_EINVAL, "null grad");
+    if (res && res->grid != PPM_GRID_SPOT)
+        return fail(ctx, PPM_EINVAL, "the gradient needs the spot grid (PPM_GRID_SPOT)");
     if ((s = check_params(ctx, p, res)) != PPM_OK) return s;
     if ((s = refresh_energies(ctx)) != PPM_OK) return s;
     DeviceGuard g(ctx->device);
@@ -1100,15 +1125,16 @@ void noalloc_sizes(const ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, 
     L->n_items = L->n_tiles = L->total_rings = L->total_rows = L->n_phi_max = 0;
     L->total_elems = 0;
     for (int b = 0; b < p->B; ++b) {
+        const int nr = rings_per_spot(res, b), ns = slots_per_ring(res, b);
         const int tiles = (res->n_phase[b] + pt - 1) / pt;
-        const int gb = std::min(g, res->n_theta[b]);
-        const int groups = (res->n_theta[b] + gb - 1) / gb;
+        const int gb = std::min(g, nr);
+        const int groups = (nr + gb - 1) / gb;
         L->n_tiles += tiles;
         L->n_items += tiles * p->n_spots * groups;
-        L->total_rings += p->n_spots * res->n_theta[b];
+        L->total_rings += p->n_spots * nr;
         L->total_rows += res->n_phase[b];
-        L->total_elems += (size_t)p->n_spots * res->n_theta[b] * res->n_phi[b];
-        L->n_phi_max = std::max(L->n_phi_max, res->n_phi[b]);
+        L->total_elems += (size_t)p->n_spots * nr * ns;
+        L->n_phi_max = std::max(L->n_phi_max, ns);
     }
     const int nE = (int)ctx->E.size();
     L->nEpad = (nE + kEC - 1) / kEC * kEC;
@@ -1155,13 +1181,13 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     long long T32 = 0;
     int max_theta = 1;
     for (int b = 0; b < p->B; ++b) {
-        T32 += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + kPT - 1) / kPT);
-        max_theta = std::max(max_theta, res->n_theta[b]);
+        T32 += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + kPT - 1) / kPT);
+        max_theta = std::max(max_theta, rings_per_spot(res, b));
     }
     const int pt = T32 < (long long)ctx->sm_count * 16 ? 16 : kPT;
     long long T = 0;
     for (int b = 0; b < p->B; ++b)
-        T += (long long)p->n_spots * res->n_theta[b] * ((res->n_phase[b] + pt - 1) / pt);
+        T += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + pt - 1) / pt);
     int g = (int)std::max<long long>(1, T / std::max<long long>((long long)ctx->sm_count * 12, 1));
     NoAllocPlan L;
     for (;;) {
@@ -1186,8 +1212,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     size_t elems = 0;
     for (int b = 0; b < p->B; ++b) {
         InstPlan &ip = hi[b];
-        ip.n_theta = res->n_theta[b];
-        ip.n_phi = res->n_phi[b];
+        ip.n_theta = rings_per_spot(res, b);
+        ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
         ip.ring0 = rings;
         ip.elem0 = (int)elems;
@@ -1235,7 +1261,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     P.colat = p->colat; P.azim = p->azim; P.zeta = p->zeta; P.logT = p->logT;
     P.mask_colat = p->mask_colat; P.mask_azim = p->mask_azim; P.mask_zeta = p->mask_zeta;
     PlanDev plan;
-    plan.B = p->B; plan.n_fp = res->n_fp; plan.n_items = L.n_items;
+    plan.B = p->B; plan.n_fp = res->n_fp; plan.n_items = L.n_items; plan.grid = res->grid;
     plan.total_rings = L.total_rings; plan.pt = L.pt;
     plan.inst = reinterpret_cast<const InstPlan *>(dev + L.o_inst);
     plan.items = reinterpret_cast<const Item *>(dev + L.o_items);

@@ -99,6 +99,7 @@ struct Params {
 
 struct PlanDev {
     int B, n_fp, n_items, total_rings;
+    int grid;  // PPM_GRID_SPOT or PPM_GRID_HEALPIX (InstPlan.n_theta = 4 N_side - 1 rings)
     int pt;  // output phases per work item
     const InstPlan *inst;
     const Item *items;

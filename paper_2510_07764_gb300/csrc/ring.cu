@@ -20,7 +20,8 @@ namespace {
 struct RingGeo {
     double theta, st, ct, half, dphi, R, u, sq1u, cos_eta, sin_eta, logg, beta, gamma;
     double area, dt_obl, nu, sini, cosi, phic, mask_c, mask_ct, mask_st, mask_phi;
-    int ok, has_mask;
+    double phi0, cap_c, cap_ct, cap_st;  // HEALPix mesh: first azimuth, emitter cap
+    int ok, has_mask, n_el;
 };
 
 __device__ bool lens_lookup(const LensDev &L, double u, double cpsi, double *ca, double *lf)
@@ -125,20 +126,49 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         const double x = GM / (kC * kC * Re);
         const double o2 = p.oblate ? Obar * Obar * (-0.788 + 1.030 * x) : 0.0;
         const double g0 = GM / (Re * Re) / sqrt(1.0 - Rs / Re);
-        // ring of the spot's bounding grid
         const double tc = p.colat[sidx], zt = p.zeta[sidx];
-        const double lo = fmax(tc - zt, 0.0), hi = fmin(tc + zt, kPI);
-        const double dth = (hi - lo) / ip.n_theta;
-        const double th = lo + (r + 0.5) * dth;
-        const double dcos = cos(lo + r * dth) - cos(lo + (r + 1) * dth);
+        double th, dcos, half;
+        if (plan.grid == 1) {
+            // HEALPix ring r + 1 of N_side = (rings + 1) / 4 (Gorski et al. 2005):
+            // z, pixel count and first azimuth; every pixel has solid angle pi/(3 N^2)
+            const int N = (ip.n_theta + 1) / 4, i = r + 1;
+            const double NN = (double)N;
+            double z;
+            if (i < N || i > 3 * N) {
+                const int ipl = i < N ? i : 4 * N - i;
+                const double zz = 1.0 - (double)ipl * ipl / (3.0 * NN * NN);
+                z = i < N ? zz : -zz;
+                G.n_el = 4 * ipl;
+                G.phi0 = 0.25 * kPI / ipl;
+            } else {
+                z = 4.0 / 3.0 - 2.0 * i / (3.0 * NN);
+                G.n_el = 4 * N;
+                G.phi0 = 0.5 * kPI / NN * (1.0 - 0.5 * ((i - N + 1) % 2));
+            }
+            th = acos(z);
+            G.dphi = 2.0 * kPI / G.n_el;
+            dcos = (kPI / (3.0 * NN * NN)) / G.dphi;
+            // rings that cannot reach the emitter cap hold no pixel of the spot
+            half = fabs(th - tc) <= zt + 1e-12 ? kPI : 0.0;
+            G.cap_c = cos(zt);
+            G.cap_ct = cos(tc);
+            G.cap_st = sin(tc);
+        } else {
+            // ring of the spot's bounding grid
+            const double lo = fmax(tc - zt, 0.0), hi = fmin(tc + zt, kPI);
+            const double dth = (hi - lo) / ip.n_theta;
+            th = lo + (r + 0.5) * dth;
+            dcos = cos(lo + r * dth) - cos(lo + (r + 1) * dth);
+            const double num = cos(zt) - cos(th) * cos(tc), den = sin(th) * sin(tc);
+            if (den <= 0.0) half = num <= 0.0 ? kPI : 0.0;
+            else half = acos(fmin(fmax(num / den, -1.0), 1.0));
+            G.n_el = ip.n_phi;
+            G.dphi = 2.0 * half / ip.n_phi;
+            G.phi0 = 0.0;
+        }
         double st, ct;
         sincos(th, &st, &ct);
-        const double num = cos(zt) - ct * cos(tc), den = st * sin(tc);
-        double half;
-        if (den <= 0.0) half = num <= 0.0 ? kPI : 0.0;
-        else half = acos(fmin(fmax(num / den, -1.0), 1.0));
         G.theta = th; G.st = st; G.ct = ct; G.half = half;
-        G.dphi = 2.0 * half / ip.n_phi;
         // shape, slope, gravity, speed
         const double R = Re * (1.0 + o2 * ct * ct);
         const double u = Rs / R;
@@ -264,14 +294,20 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (threadIdx.x == 0) s_base = 0;
         __syncthreads();
-        for (int m0 = 0; m0 < ip.n_phi; m0 += blockDim.x) {
+        for (int m0 = 0; m0 < G.n_el; m0 += blockDim.x) {
             const int m = m0 + threadIdx.x;
             bool act = false;
             double phia = 0.0;
-            if (m < ip.n_phi) {
-                phia = G.phic - G.half + (m + 0.5) * G.dphi;
-                act = true;
-                if (G.has_mask) {
+            if (m < G.n_el) {
+                if (plan.grid == 1) {
+                    // mesh pixel: inside the emitter cap (FP64, as in the oracle)
+                    phia = G.phi0 + m * G.dphi;
+                    act = G.ct * G.cap_ct + G.st * G.cap_st * cos(phia - G.phic) >= G.cap_c;
+                } else {
+                    phia = G.phic - G.half + (m + 0.5) * G.dphi;
+                    act = true;
+                }
+                if (act && G.has_mask) {
                     const double cd = G.ct * G.mask_ct + G.st * G.mask_st * cos(phia - G.mask_phi);
                     act = !(cd > G.mask_c);
                 }

@@ -75,6 +75,7 @@ class Instances:
     oblate: int          # 0 = Schwarzschild+Doppler sphere, 1 = oblate Schwarzschild
     emission: int        # 0 = analytic isotropic blackbody, 1 = atmosphere table
     n_fp: int = 192
+    grid: int = 0        # 0 = spot-bounding grid; 1 = HEALPix mesh with N_side = n_theta
 
     @property
     def B(self) -> int:
