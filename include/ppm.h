@@ -203,6 +203,9 @@ typedef struct {
     const int *n_theta, *n_phi, *n_phase;
     int n_fp;
     int grid;   /* PPM_GRID_SPOT or PPM_GRID_HEALPIX */
+    int phase_sub;  /* 1, 2, 4, 8 or 16 point samples per output phase bin: bin j is
+                       the mean of samples at (j + (q + 1/2)/S - 1/2) / n_phase; 1 = the
+                       point sample j / n_phase (Sect. 2.8.3) */
 } ppm_res;
 
 /* ------------------------------------------------------------------------

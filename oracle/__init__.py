@@ -77,7 +77,7 @@ class InstC(C.Structure):
                 ("mask_azim", C.c_double * 2), ("mask_zeta", C.c_double * 2),
                 ("n_spots", C.c_int), ("oblate", C.c_int), ("emission", C.c_int),
                 ("n_theta", C.c_int), ("n_phi", C.c_int), ("n_phase", C.c_int), ("n_fp", C.c_int),
-                ("grid", C.c_int)]
+                ("grid", C.c_int), ("phase_sub", C.c_int)]
 
 
 def lib():
@@ -253,6 +253,7 @@ def inst_c(inst, b: int = 0) -> InstC:
     c.n_theta = int(inst.n_theta[b]); c.n_phi = int(inst.n_phi[b])
     c.n_phase = int(inst.n_phase[b]); c.n_fp = int(inst.n_fp)
     c.grid = int(getattr(inst, "grid", 0))
+    c.phase_sub = int(getattr(inst, "phase_sub", 1))
     return c
 
 

@@ -493,6 +493,7 @@ typedef struct {
     real colat[2], azim[2], zeta[2], logT[2], mask_colat[2], mask_azim[2], mask_zeta[2];
     int n_spots, oblate, emission, n_theta, n_phi, n_phase, n_fp;
     int grid;  /* 0: spot-bounding grid; 1: HEALPix whole-surface mesh, N_side = n_theta */
+    int phase_sub;  /* sub-samples per output phase bin (reading: 1 = point samples) */
 } orc_inst;
 
 typedef struct {
@@ -791,8 +792,10 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
                 const int *ksel, int nk, int ring_stride, real *Ft)
 {
     if (in->n_spots < 1 || in->n_spots > 2 || in->n_theta < 1 || in->n_phi < 1 ||
-        in->n_phase < 1 || in->n_fp < 2 || nE < 1 || in->grid < 0 || in->grid > 1)
+        in->n_phase < 1 || in->n_fp < 2 || nE < 1 || in->grid < 0 || in->grid > 1 ||
+        in->phase_sub < 1)
         return ORC_EINVAL;
+    const int S = in->phase_sub;
     if (in->emission == 1 && A == NULL) return ORC_EINVAL;
     if (ring_stride < 1) ring_stride = 1;
     int NJ = jsel ? nj : in->n_phase;
@@ -836,19 +839,26 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
                 real sm = phia / (2.0 * ORC_PI);
                 for (int jj = 0; jj < NJ; jj++) {
                     int j = jsel ? jsel[jj] : jj;
-                    double phi_out = (double)j / (double)in->n_phase;
-                    real phip = frac1(phi_out + sm + 1.0 - ph[0]) + ph[0];
-                    real Fp, zp, mup;
-                    template_at(ph, F, z, mu, n_fp, phip, &Fp, &zp, &mup);
-                    if (RE(Fp) == 0.0) continue;
-                    for (int kk = 0; kk < NK; kk++) {
-                        int k = ksel ? ksel[kk] : kk;
-                        double E = E_keV[k];
-                        real Ep = zp * E;
-                        real I = (in->emission == 1)
-                                       ? orc_atm_interp(A, logT, rg.logg, mup, Ep)
-                                       : orc_bb_intensity(Ep, kT);
-                        Ft[(size_t)jj * NK + kk] += Fp * I / E;
+                    /* reading: phase bin j is centred on j / n_phase; with
+                     * phase_sub = S its value is the mean of S point samples
+                     * at the centres of its S equal sub-intervals */
+                    for (int q = 0; q < S; q++) {
+                        double phi_out = S == 1 ? (double)j / (double)in->n_phase
+                                                : ((double)j + ((q + 0.5) / S - 0.5)) /
+                                                      (double)in->n_phase;
+                        real phip = frac1(phi_out + sm + 1.0 - ph[0]) + ph[0];
+                        real Fp, zp, mup;
+                        template_at(ph, F, z, mu, n_fp, phip, &Fp, &zp, &mup);
+                        if (RE(Fp) == 0.0) continue;
+                        for (int kk = 0; kk < NK; kk++) {
+                            int k = ksel ? ksel[kk] : kk;
+                            double E = E_keV[k];
+                            real Ep = zp * E;
+                            real I = (in->emission == 1)
+                                           ? orc_atm_interp(A, logT, rg.logg, mup, Ep)
+                                           : orc_bb_intensity(Ep, kT);
+                            Ft[(size_t)jj * NK + kk] += Fp * I / E / (double)S;
+                        }
                     }
                 }
             }

@@ -65,8 +65,10 @@ class DeviceParams:
         self.n_fp = int(inst.n_fp)
         ip = C.POINTER(C.c_int)
         self.grid = int(getattr(inst, "grid", 0))
+        self.phase_sub = int(getattr(inst, "phase_sub", 1))
         self.res = _abi.ppm_res(self.n_theta.ctypes.data_as(ip), self.n_phi.ctypes.data_as(ip),
-                                self.n_phase.ctypes.data_as(ip), self.n_fp, self.grid)
+                                self.n_phase.ctypes.data_as(ip), self.n_fp, self.grid,
+                                self.phase_sub)
         self.rows = int(self.n_phase.sum())
 
     def upload(self, inst, non_blocking: bool = False):

@@ -59,7 +59,8 @@ class ppm_timing(C.Structure):
 
 class ppm_res(C.Structure):
     _fields_ = [("n_theta", C.POINTER(C.c_int)), ("n_phi", C.POINTER(C.c_int)),
-                ("n_phase", C.POINTER(C.c_int)), ("n_fp", C.c_int), ("grid", C.c_int)]
+                ("n_phase", C.POINTER(C.c_int)), ("n_fp", C.c_int), ("grid", C.c_int),
+                ("phase_sub", C.c_int)]
 
 
 _lib = None

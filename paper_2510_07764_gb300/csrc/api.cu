@@ -500,6 +500,9 @@ static ppm_status check_params(ppm_ctx *ctx, const ppm_params *p, const ppm_res 
     if (res->n_fp < 8 || res->n_fp > kMaxFp) return fail(ctx, PPM_EINVAL, "need 8 <= n_fp <= 1024");
     if (res->grid != PPM_GRID_SPOT && res->grid != PPM_GRID_HEALPIX)
         return fail(ctx, PPM_EINVAL, "grid must be PPM_GRID_SPOT or PPM_GRID_HEALPIX");
+    if (!(res->phase_sub == 1 || res->phase_sub == 2 || res->phase_sub == 4 ||
+          res->phase_sub == 8 || res->phase_sub == 16))
+        return fail(ctx, PPM_EINVAL, "phase_sub must be 1, 2, 4, 8 or 16");
     for (int b = 0; b < p->B; ++b) {
         if (res->grid == PPM_GRID_HEALPIX) {
             if (res->n_theta[b] < 1 || res->n_theta[b] > 1024 || res->n_phase[b] < 1 ||
@@ -531,6 +534,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(ctx->tile_pt);
     key.push_back(ctx->tile_waves);
     key.push_back(res->grid);
+    key.push_back(res->phase_sub);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -544,7 +548,8 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     auto ring_tiles = [&](int pt) {
         long long T = 0;
         for (int b = 0; b < B; ++b)
-            T += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + pt - 1) / pt);
+            T += (long long)p->n_spots * rings_per_spot(res, b) *
+                 ((res->n_phase[b] * res->phase_sub + pt - 1) / pt);
         return T;
     };
     int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
@@ -561,7 +566,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     double total = 0.0;
     for (int b = 0; b < B; ++b)
         total += (double)p->n_spots * rings_per_spot(res, b) * slots_per_ring(res, b) *
-                 res->n_phase[b] * nE;
+                 res->n_phase[b] * res->phase_sub * nE;
     const double target =
         std::max(1.0, total / ((double)ctx->sm_count * 2.0 * (double)ctx->tile_waves));
     hp.inst.resize(B);
@@ -570,16 +575,18 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
         ip.n_theta = rings_per_spot(res, b);
         ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
+        ip.n_sub = res->phase_sub;
+        const int nq = ip.n_phase * ip.n_sub;  // point samples (pt is a multiple of n_sub)
         ip.ring0 = hp.total_rings;
         ip.elem0 = (int)hp.total_elems;
         ip.row0 = hp.total_rows;
-        ip.tiles = (ip.n_phase + pt - 1) / pt;
+        ip.tiles = (nq + pt - 1) / pt;
         ip.tile0 = (int)hp.tiles.size();
         hp.total_rings += p->n_spots * ip.n_theta;
         hp.total_elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
         hp.total_rows += ip.n_phase;
         hp.n_phi_max = std::max(hp.n_phi_max, ip.n_phi);
-        const double ring_cost = (double)ip.n_phi * std::min(pt, ip.n_phase) * nE;
+        const double ring_cost = (double)ip.n_phi * std::min(pt, nq) * nE;
         const int gb = (int)std::min<double>(ip.n_theta, std::max(1.0, std::floor(target / ring_cost)));
         for (int t = 0; t < ip.tiles; ++t) {
             const int begin = (int)hp.items.size();
@@ -587,7 +594,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
                 for (int r0 = 0; r0 < ip.n_theta; r0 += gb) {
                     Item it;
                     it.b = b; it.spot = s; it.r0 = r0; it.r1 = std::min(r0 + gb, ip.n_theta);
-                    it.j0 = t * pt; it.nj = std::min(pt, ip.n_phase - t * pt);
+                    it.j0 = t * pt; it.nj = std::min(pt, nq - t * pt);
                     hp.items.push_back(it);
                 }
             hp.tiles.push_back(make_int2(begin, (int)hp.items.size()));
@@ -1126,7 +1133,7 @@ void noalloc_sizes(const ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, 
     L->total_elems = 0;
     for (int b = 0; b < p->B; ++b) {
         const int nr = rings_per_spot(res, b), ns = slots_per_ring(res, b);
-        const int tiles = (res->n_phase[b] + pt - 1) / pt;
+        const int tiles = (res->n_phase[b] * res->phase_sub + pt - 1) / pt;
         const int gb = std::min(g, nr);
         const int groups = (nr + gb - 1) / gb;
         L->n_tiles += tiles;
@@ -1181,13 +1188,15 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     long long T32 = 0;
     int max_theta = 1;
     for (int b = 0; b < p->B; ++b) {
-        T32 += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + kPT - 1) / kPT);
+        T32 += (long long)p->n_spots * rings_per_spot(res, b) *
+               ((res->n_phase[b] * res->phase_sub + kPT - 1) / kPT);
         max_theta = std::max(max_theta, rings_per_spot(res, b));
     }
     const int pt = T32 < (long long)ctx->sm_count * 16 ? 16 : kPT;
     long long T = 0;
     for (int b = 0; b < p->B; ++b)
-        T += (long long)p->n_spots * rings_per_spot(res, b) * ((res->n_phase[b] + pt - 1) / pt);
+        T += (long long)p->n_spots * rings_per_spot(res, b) *
+             ((res->n_phase[b] * res->phase_sub + pt - 1) / pt);
     int g = (int)std::max<long long>(1, T / std::max<long long>((long long)ctx->sm_count * 12, 1));
     NoAllocPlan L;
     for (;;) {
@@ -1215,10 +1224,12 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
         ip.n_theta = rings_per_spot(res, b);
         ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
+        ip.n_sub = res->phase_sub;
+        const int nq = ip.n_phase * ip.n_sub;
         ip.ring0 = rings;
         ip.elem0 = (int)elems;
         ip.row0 = rows;
-        ip.tiles = (ip.n_phase + pt - 1) / pt;
+        ip.tiles = (nq + pt - 1) / pt;
         ip.tile0 = tiles;
         rings += p->n_spots * ip.n_theta;
         elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
@@ -1230,7 +1241,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
                 for (int r0 = 0; r0 < ip.n_theta; r0 += gb) {
                     Item &it = hit[items++];
                     it.b = b; it.spot = sp; it.r0 = r0; it.r1 = std::min(r0 + gb, ip.n_theta);
-                    it.j0 = t * pt; it.nj = std::min(pt, ip.n_phase - t * pt);
+                    it.j0 = t * pt; it.nj = std::min(pt, nq - t * pt);
                 }
             ht[tiles++] = make_int2(begin, items);
         }

@@ -66,11 +66,12 @@ struct AtmDev {
 // Per-instance plan entry (host-built).
 struct InstPlan {
     int n_theta, n_phi, n_phase;
+    int n_sub;   // point samples per output phase (the items run n_phase * n_sub of them)
     int ring0;   // first global ring index
     int elem0;   // first element slot (rings of this instance use n_phi slots each)
     int row0;    // first F_t row
     int tile0;   // first entry in the tile-range table
-    int tiles;   // ceil(n_phase / pt)
+    int tiles;   // ceil(n_phase * n_sub / pt)
 };
 
 // One shift-and-add work item: rings [r0, r1) of one spot, phases [j0, j0+nj).

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         rec.pad = 0.0f;
         recs[g] = rec;
         if (triples && rec.visible)
-            atomicAdd(triples, (unsigned long long)n_active * ip.n_phase * nE);
+            atomicAdd(triples, (unsigned long long)n_active * ip.n_phase * ip.n_sub * nE);
     }
 }
 

@@ -370,7 +370,9 @@ __global__ void __launch_bounds__(kSABlock, 2)
 
     int top = 1;
     while (top * 2 <= n_fp) top *= 2;
-    const float inv_nphase = 1.0f / (float)ip.n_phase;
+    // point sample q of the instance: phase (q - (S - 1)/2) / (n_phase S)
+    const float inv_nphase = 1.0f / (float)(ip.n_phase * ip.n_sub);
+    const float q_half = 0.5f * (float)(ip.n_sub - 1);
     const float inv_dlnE = (EMIS == 1) ? (float)(1.0 / A.dlnE) : 0.0f;
     const int Pm = A.nmu_pad;
     const bool inst_ok = status[it.b] == 0;
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
         const bool sliding = en.sliding != 0;
 
         for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
-            const float phi_out = (float)(it.j0 + jl) * inv_nphase;
+            const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
             if constexpr (EMIS == 1) {
                 for (int g0 = 0; g0 < n_act;) {
                     if (n_act - g0 > 64) {
@@ -524,12 +526,14 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
     const int warp = threadIdx.x >> 5;
     const int b = find_instance_by_row(plan.inst, plan.B, row);
     const InstPlan ip = plan.inst[b];
-    const int j = row - ip.row0;
-    const int tile = j / pt, jl = j - tile * pt;
+    // output phase j gathers its n_sub point samples (rows of one tile)
+    const int q0 = (row - ip.row0) * ip.n_sub;
+    const int tile = q0 / pt, jl0 = q0 - tile * pt;
     const int2 rng = plan.tile_items[ip.tile0 + tile];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (4 * k4 < nEpad) {
-        const float4 *base = reinterpret_cast<const float4 *>(partials + (size_t)jl * nEpad) + k4;
+    for (int sub = 0; sub < ip.n_sub && 4 * k4 < nEpad; ++sub) {
+        const float4 *base =
+            reinterpret_cast<const float4 *>(partials + (size_t)(jl0 + sub) * nEpad) + k4;
         const size_t stride4 = (size_t)pt * nEpad / 4;
         int i = rng.x + warp;
         for (; i + 8 < rng.y; i += 16) {
@@ -550,7 +554,7 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
             const float4 v = red[w][threadIdx.x];
             s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
         }
-        const float sc = (float)(1.0 / kFluxScale);
+        const float sc = (float)(1.0 / kFluxScale) / (float)ip.n_sub;
         const bool ok = status[b] == 0;
         const float vals[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll

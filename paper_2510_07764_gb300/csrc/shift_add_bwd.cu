@@ -336,7 +336,12 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
 
     int top = 1;
     while (top * 2 <= n_fp) top *= 2;
-    const float inv_nphase = 1.0f / (float)ip.n_phase;
+    // point samples q = 0 .. n_phase n_sub - 1 at (q - (S - 1)/2) / (n_phase S);
+    // each carries 1/S of its output phase's adjoint
+    const float inv_nphase = 1.0f / (float)(ip.n_phase * ip.n_sub);
+    const float q_half = 0.5f * (float)(ip.n_sub - 1);
+    const float inv_sub = 1.0f / (float)ip.n_sub;
+    const int n_q = ip.n_phase * ip.n_sub;
     const float inv_dlnE = EMIS == 1 ? (float)(1.0 / A.dlnE) : 0.0f;
     const int Pm = A.nmu_pad;
     const int offT = lay.slabT - lay.slab, offG = lay.slabG - lay.slab;
@@ -359,14 +364,14 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
     float *gF = adj, *gZ = adj + (n_fp + 1), *gM = adj + 2 * (n_fp + 1), *gP = adj + 3 * (n_fp + 1);
     float lane_gs = 0.0f, lane_gss = 0.0f, lane_T = 0.0f, lane_G = 0.0f;
 
-    for (int j = warp; j < ip.n_phase; j += kBwdBlock / 32) {
-        const float *asrc = Aadj + (size_t)(ip.row0 + j) * nEpad;
+    for (int j = warp; j < n_q; j += kBwdBlock / 32) {
+        const float *asrc = Aadj + (size_t)(ip.row0 + j / ip.n_sub) * nEpad;
         for (int k = lane; k < nEpad; k += 32) {
             arow[2 * k] = spk[k];
-            arow[2 * k + 1] = asrc[k];
+            arow[2 * k + 1] = asrc[k] * inv_sub;
         }
         __syncwarp();
-        const float phi_out = (float)j * inv_nphase;
+        const float phi_out = ((float)j - q_half) * inv_nphase;
         for (int g0 = 0; g0 < n_act; g0 += 32) {
             const int m = g0 + lane;
             const bool on = m < n_act;

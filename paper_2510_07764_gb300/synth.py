@@ -76,6 +76,7 @@ class Instances:
     emission: int        # 0 = analytic isotropic blackbody, 1 = atmosphere table
     n_fp: int = 192
     grid: int = 0        # 0 = spot-bounding grid; 1 = HEALPix mesh with N_side = n_theta
+    phase_sub: int = 1   # point samples per output phase bin (1, 2, 4, 8 or 16)
 
     @property
     def B(self) -> int:

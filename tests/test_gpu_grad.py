@@ -167,3 +167,12 @@ def test_grad_full_size_directional(synth, atm):
         fd = (lls[0] - lls[1]) / (2 * h)
         gv = float(np.dot(g, v.cpu().numpy()))
         assert abs(gv - fd) <= 1e-2 * abs(fd) + 1e-3 * float(np.sum(np.abs(g * v.cpu().numpy())))
+
+
+def test_grad_with_phase_sub_samples(orc, synth, atm, small_lens):
+    w = visible_two_cap(synth, atm, small_lens, n_theta=10, n_phi=12, n_phase=16, n_E=40,
+                        n_chan=20)
+    w.inst.phase_sub = 4
+    ll, g, st = gpu_grad(w)
+    assert st[0] == 0
+    _check(g[0, :13], orc.grad_tangent(w))

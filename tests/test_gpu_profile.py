@@ -162,3 +162,14 @@ def test_coarse_energy_grid_general_path(orc, synth, atm, small_lens):
                            lens=small_lens)
     got, _ = gpu_profile(w)
     assert max_rel(got, orc.profile(w)) < TOL_ATM
+
+
+@pytest.mark.parametrize("S", [2, 4, 16])
+def test_phase_sub_samples_match_oracle(orc, synth, atm, small_lens, S):
+    """Output phase bins averaged over S point samples (ppm_res.phase_sub)."""
+    w = synth.atm_two_spot(n_theta=12, n_phi=16, n_phase=24, n_E=40, n_chan=8, atm=atm,
+                           lens=small_lens)
+    w.inst.phase_sub = S
+    Ft, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(Ft, orc.profile(w)) < 1e-3

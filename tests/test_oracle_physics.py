@@ -244,3 +244,27 @@ def test_flat_space_light_curve_time_domain(orc, synth):
         ref[:, k] = np.interp(out, ext_a, ext_f)
     scale = ref.max(axis=0)
     assert np.max(np.abs(F - ref) / scale) < 1e-5
+
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_phase_sub_samples_are_azimuth_shifted_point_samples(orc, synth, atm, small_lens, S):
+    """A phase bin with S sub-samples at offsets ((q + 1/2)/S - 1/2)/N is the
+    mean of S point-sample profiles whose spots (and masks) are turned by
+    2 pi times those offsets: the element grid moves with the azimuth."""
+    w = synth.atm_two_spot(n_theta=8, n_phi=12, n_phase=16, n_E=10, n_chan=4, atm=atm,
+                           lens=small_lens)
+    w.inst.phase_sub = S
+    F = orc.profile(w)
+    N = int(w.inst.n_phase[0])
+    acc = np.zeros_like(F)
+    for q in range(S):
+        d = 2 * math.pi * ((q + 0.5) / S - 0.5) / N
+        v = _two_spot(synth, atm, small_lens)
+        v.inst.n_phi[:] = 12
+        v.inst.n_theta[:] = 8
+        v.inst.n_phase[:] = 16
+        v.E_keV = w.E_keV
+        v.inst.azim[:] = w.inst.azim + d
+        v.inst.mask_azim[:] = w.inst.mask_azim + d
+        acc += orc.profile(v)
+    np.testing.assert_allclose(F, acc / S, rtol=1e-9, atol=1e-12 * np.abs(F).max())
