@@ -343,6 +343,13 @@ typedef struct {
 ppm_status ppm_set_timing(ppm_ctx *ctx, int enable);
 ppm_status ppm_get_timing(ppm_ctx *ctx, ppm_timing *out);
 
+/* FP32 FMA throughput of device `device` in TFLOP/s (no counterpart in the
+ * paper; measurement support for the FP32 roofline of the shift-and-add):
+ * 8 independent FMA chains per thread, scalar FFMA (paired = 0) or packed
+ * FFMA2 (paired = 1), 8 blocks of 256 threads per SM, timed with CUDA events
+ * on `stream` (synchronised).  Allocates and frees 16 KB of device memory. */
+ppm_status ppm_fp32_peak(int device, int paired, void *stream, double *tflops);
+
 /* Wait for `stream` with a bounded host-side poll (timeout_s > 0), then report
  * any device-side invariant failure recorded since the last ppm_sync
  * (PPM_ENOTREADY, with a message) and clear it.  Returns PPM_ETIMEOUT if the

@@ -21,7 +21,8 @@ EXPORTS = ["ppm_create", "ppm_destroy", "ppm_last_error", "ppm_build_lens", "ppm
            "ppm_set_atmosphere", "ppm_set_energies", "ppm_set_response", "ppm_profile",
            "ppm_loglike", "ppm_sync", "ppm_set_timing", "ppm_get_timing",
            "ppm_profile_noalloc", "ppm_loglike_grad", "ppm_set_interpolation",
-           "ppm_set_tiles", "ppm_get_tiles", "ppm_autotune", "ppm_set_response_fine"]
+           "ppm_set_tiles", "ppm_get_tiles", "ppm_autotune", "ppm_set_response_fine",
+           "ppm_fp32_peak"]
 
 # interpolation strategies of Sect. 4 (PPM_INTERP_* in ppm.h), keyed by the
 # paper's panel letters
@@ -97,6 +98,7 @@ def lib() -> C.CDLL:
         "ppm_loglike_grad": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp, i, vp, d,
                                  vp, vp, vp, vp]),
         "ppm_sync": (i, [vp, vp, d]),
+        "ppm_fp32_peak": (i, [i, i, vp, C.POINTER(d)]),
         "ppm_set_tiles": (i, [vp, C.POINTER(ppm_tiles)]),
         "ppm_get_tiles": (i, [vp, C.POINTER(ppm_tiles)]),
         "ppm_autotune": (i, [vp, C.POINTER(ppm_params), C.POINTER(ppm_res), vp,
@@ -185,6 +187,12 @@ def ppm_get_tiles(ctx, t: ppm_tiles) -> int:
 
 def ppm_autotune(ctx, params: ppm_params, res: ppm_res, stream, best: ppm_tiles) -> int:
     return lib().ppm_autotune(ctx, C.byref(params), C.byref(res), stream, C.byref(best))
+
+
+def ppm_fp32_peak(device: int, paired: int, stream):
+    v = C.c_double()
+    st = lib().ppm_fp32_peak(device, paired, stream, C.byref(v))
+    return st, v.value
 
 
 def ppm_sync(ctx, stream, timeout_s: float) -> int:

@@ -12,7 +12,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libppm.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 SOURCES = ["api.cu", "lens.cu", "ring.cu", "shift_add.cu", "loglike.cu", "resp_tc.cu",
-           "shift_add_bwd.cu", "ring_bwd.cu", "grad.cu"]
+           "shift_add_bwd.cu", "ring_bwd.cu", "grad.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "--ftz=true", "-Xcompiler", "-fPIC",
                 "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "ppm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(ppm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(ppm_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -24,7 +24,7 @@ def libppm():
 
 def test_header_declares_the_hot_path(libppm):
     names = declared_functions()
-    for required in ["ppm_build_lens", "ppm_profile", "ppm_loglike"]:
+    for required in ["ppm_build_lens", "ppm_profile", "ppm_loglike", "ppm_loglike_grad"]:
         assert required in names
 
 

@@ -100,3 +100,13 @@ def test_cuda_graph_replay_follows_parameter_updates(synth, atm, small_lens, per
             assert np.array_equal(got, ref)
     finally:
         ctx.set_tiles()
+
+
+def test_fp32_fma_microbenchmark():
+    import torch
+    from paper_2510_07764_gb300 import _abi, _stream_handle
+    for paired in (0, 1):
+        st, tf = _abi.ppm_fp32_peak(0, paired, _stream_handle(torch.cuda.current_stream()))
+        assert st == 0
+        # a GB300 sustains tens of TFLOP/s of FP32 FMA; the derived peak is 80.5
+        assert 10.0 < tf < 200.0, (paired, tf)
