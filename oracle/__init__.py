@@ -77,7 +77,8 @@ class InstC(C.Structure):
                 ("mask_azim", C.c_double * 2), ("mask_zeta", C.c_double * 2),
                 ("n_spots", C.c_int), ("oblate", C.c_int), ("emission", C.c_int),
                 ("n_theta", C.c_int), ("n_phi", C.c_int), ("n_phase", C.c_int), ("n_fp", C.c_int),
-                ("grid", C.c_int), ("phase_sub", C.c_int)]
+                ("grid", C.c_int), ("phase_sub", C.c_int),
+                ("logT_map", C.POINTER(C.c_double))]
 
 
 def lib():
@@ -254,6 +255,11 @@ def inst_c(inst, b: int = 0) -> InstC:
     c.n_phase = int(inst.n_phase[b]); c.n_fp = int(inst.n_fp)
     c.grid = int(getattr(inst, "grid", 0))
     c.phase_sub = int(getattr(inst, "phase_sub", 1))
+    tmap = getattr(inst, "logT_map", None)
+    if tmap is not None:
+        arr = np.ascontiguousarray(tmap[b], dtype=np.float64)
+        c._keep = arr   # the struct points into it
+        c.logT_map = arr.ctypes.data_as(C.POINTER(C.c_double))
     return c
 
 

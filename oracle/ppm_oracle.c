@@ -494,6 +494,11 @@ typedef struct {
     int n_spots, oblate, emission, n_theta, n_phi, n_phase, n_fp;
     int grid;  /* 0: spot-bounding grid; 1: HEALPix whole-surface mesh, N_side = n_theta */
     int phase_sub;  /* sub-samples per output phase bin (reading: 1 = point samples) */
+    /* full-surface temperature map (Sect. 2.6): log10 T_eff per HEALPix pixel
+     * in ring order (grid 1 only), or NULL; a pixel with a non-finite or
+     * non-positive value emits nothing.  With a map the spot parameters are
+     * not used: every mesh pixel is a candidate and carries its own T. */
+    const double *logT_map;
 } orc_inst;
 
 typedef struct {
@@ -651,7 +656,18 @@ static void ring_def(const orc_inst *in, int spot, int r, orc_ringdef *d)
     d->half = ORC_PI;
     d->cap_test = 1;
     /* rings that cannot reach the cap are skipped (a decision only) */
-    d->ok = fabs(RE(d->theta) - RE(in->colat[spot])) <= RE(in->zeta[spot]) + 1e-12;
+    d->ok = in->logT_map != NULL ||
+            fabs(RE(d->theta) - RE(in->colat[spot])) <= RE(in->zeta[spot]) + 1e-12;
+}
+
+/* pixels of the HEALPix rings before ring r (0-based), i.e. the ring-order
+ * index of the ring's first pixel */
+static size_t ring_first_pixel(const orc_inst *in, int r)
+{
+    const int N = in->n_theta;
+    size_t n = 0;
+    for (int k = 1; k <= r; k++) n += (size_t)(k < N ? 4 * k : (k > 3 * N ? 4 * (4 * N - k) : 4 * N));
+    return n;
 }
 
 /* azimuth of element m of a ring */
@@ -797,6 +813,8 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
         return ORC_EINVAL;
     const int S = in->phase_sub;
     if (in->emission == 1 && A == NULL) return ORC_EINVAL;
+    const int use_map = in->logT_map != NULL;
+    if (use_map && in->grid != 1) return ORC_EINVAL;
     if (ring_stride < 1) ring_stride = 1;
     int NJ = jsel ? nj : in->n_phase;
     int NK = ksel ? nk : nE;
@@ -809,10 +827,11 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
     real *ph = (real *)malloc(sizeof(real) * (n_fp + 1));
     real *mu = (real *)malloc(sizeof(real) * (n_fp + 1));
     int status = ORC_OK;
-    for (int sp = 0; sp < in->n_spots && status == ORC_OK; sp++) {
-        real logT = in->logT[sp];
+    for (int sp = 0; sp < (use_map ? 1 : in->n_spots) && status == ORC_OK; sp++) {
+        real logT = use_map ? 6.0 : in->logT[sp];   /* a map sets it per pixel */
         real kT = KB_KEVK * r_pow(10.0, logT);
-        if (in->emission == 1 && (RE(logT) < A->logT[0] || RE(logT) > A->logT[A->nT - 1])) {
+        if (!use_map && in->emission == 1 &&
+            (RE(logT) < A->logT[0] || RE(logT) > A->logT[A->nT - 1])) {
             status = ORC_ERANGE;
             break;
         }
@@ -832,10 +851,22 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
             int tv = ring_template(&s, &rg, dphi, L, n_fp, F, z, ph, mu);
             if (tv < 0) { status = ORC_ERANGE; break; }
             if (tv == 0) continue;
-            for (int m = 0; m < rd.n_el; m++) {
+            const size_t pix0 = use_map ? ring_first_pixel(in, r) : 0;
+            for (int m = 0; m < rd.n_el && status == ORC_OK; m++) {
                 real phia = ring_phi(in, sp, &rd, m);
-                if (rd.cap_test && !inside_cap(in, sp, theta, phia)) continue;
-                if (!element_active(in, sp, theta, phia)) continue;
+                if (use_map) {
+                    const double lt = in->logT_map[pix0 + m];
+                    if (!(isfinite(lt) && lt > 0.0)) continue;  /* dark pixel */
+                    if (in->emission == 1 && (lt < A->logT[0] || lt > A->logT[A->nT - 1])) {
+                        status = ORC_ERANGE;
+                        break;
+                    }
+                    logT = lt;
+                    kT = KB_KEVK * r_pow(10.0, logT);
+                } else {
+                    if (rd.cap_test && !inside_cap(in, sp, theta, phia)) continue;
+                    if (!element_active(in, sp, theta, phia)) continue;
+                }
                 real sm = phia / (2.0 * ORC_PI);
                 for (int jj = 0; jj < NJ; jj++) {
                     int j = jsel ? jsel[jj] : jj;

@@ -77,6 +77,7 @@ class Instances:
     n_fp: int = 192
     grid: int = 0        # 0 = spot-bounding grid; 1 = HEALPix mesh with N_side = n_theta
     phase_sub: int = 1   # point samples per output phase bin (1, 2, 4, 8 or 16)
+    logT_map: Optional[np.ndarray] = None  # [B, 12 N_side^2] log10 T per HEALPix pixel (grid 1)
 
     @property
     def B(self) -> int:
