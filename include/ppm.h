@@ -184,6 +184,14 @@ typedef struct {
     const double *mass_msun, *radius_km, *spin_hz, *incl_rad, *dist_kpc, *nh_1e20;
     const double *colat, *azim, *zeta, *logT;
     const double *mask_colat, *mask_azim, *mask_zeta;
+    /* Full-surface temperature map (Sect. 2.6), or NULL: DEVICE log10 T_eff per
+     * HEALPix pixel in ring order, 12 N_side(b)^2 values per instance,
+     * instances concatenated.  Needs grid = PPM_GRID_HEALPIX, n_spots = 1 and
+     * the default interpolation strategy; a pixel with a non-finite or
+     * non-positive value emits nothing, the spot parameters (colat, azim,
+     * zeta, logT, masks) are not used.  Not differentiated (ppm_loglike_grad
+     * and ppm_profile_noalloc reject it). */
+    const double *logT_map;
 } ppm_params;
 
 /* Per-instance resolution: HOST arrays of length B, and the surface grid.

@@ -55,6 +55,11 @@ class DeviceParams:
         self.emission = int(inst.emission)
         self.t = {f: torch.empty(getattr(inst, f).size, dtype=torch.float64, device=device)
                   for f in _abi.PARAM_FIELDS}
+        tmap = getattr(inst, "logT_map", None)
+        # full-surface temperature map (HEALPix ring order, instances concatenated)
+        self.t_map = None if tmap is None else torch.from_numpy(
+            np.ascontiguousarray(np.concatenate([np.asarray(tmap[b], dtype=np.float64).ravel()
+                                                 for b in range(inst.B)]))).to(device)
         self.upload(inst)
         self._res_arrays(inst)
 
@@ -109,6 +114,7 @@ class DeviceParams:
         p.B, p.n_spots, p.oblate, p.emission = self.B, self.n_spots, self.oblate, self.emission
         for f in _abi.PARAM_FIELDS:
             setattr(p, f, self.t[f].data_ptr())
+        p.logT_map = None if self.t_map is None else self.t_map.data_ptr()
         return p
 
 

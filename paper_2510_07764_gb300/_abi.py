@@ -42,7 +42,8 @@ PARAM_FIELDS = ["mass_msun", "radius_km", "spin_hz", "incl_rad", "dist_kpc", "nh
 
 class ppm_params(C.Structure):
     _fields_ = [("B", C.c_int), ("n_spots", C.c_int), ("oblate", C.c_int),
-                ("emission", C.c_int)] + [(f, C.c_void_p) for f in PARAM_FIELDS]
+                ("emission", C.c_int)] + [(f, C.c_void_p) for f in PARAM_FIELDS] + \
+               [("logT_map", C.c_void_p)]
 
 
 class ppm_tiles(C.Structure):

@@ -495,6 +495,14 @@ static ppm_status check_params(ppm_ctx *ctx, const ppm_params *p, const ppm_res 
                           p->mask_colat, p->mask_azim, p->mask_zeta};
     for (const void *q : ptrs)
         if (!q) return fail(ctx, PPM_EINVAL, "null parameter array");
+    if (p->logT_map) {
+        if (res && res->grid != PPM_GRID_HEALPIX)
+            return fail(ctx, PPM_EINVAL, "a temperature map needs grid = PPM_GRID_HEALPIX");
+        if (p->n_spots != 1) return fail(ctx, PPM_EINVAL, "a temperature map needs n_spots = 1");
+        if (p->emission == 1 && ctx->interp != kInterpD)
+            return fail(ctx, PPM_EINVAL,
+                        "a temperature map needs the default interpolation strategy");
+    }
     if (!res->n_theta || !res->n_phi || !res->n_phase)
         return fail(ctx, PPM_EINVAL, "null resolution array");
     if (res->n_fp < 8 || res->n_fp > kMaxFp) return fail(ctx, PPM_EINVAL, "need 8 <= n_fp <= 1024");
@@ -535,6 +543,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(ctx->tile_waves);
     key.push_back(res->grid);
     key.push_back(res->phase_sub);
+    key.push_back(p->logT_map ? 1 : 0);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -570,12 +579,15 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     const double target =
         std::max(1.0, total / ((double)ctx->sm_count * 2.0 * (double)ctx->tile_waves));
     hp.inst.resize(B);
+    long long pix = 0;  // temperature-map offset (HEALPix: 12 N^2 pixels per instance)
     for (int b = 0; b < B; ++b) {
         InstPlan &ip = hp.inst[b];
         ip.n_theta = rings_per_spot(res, b);
         ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
         ip.n_sub = res->phase_sub;
+        ip.pix0 = (int)pix;
+        if (res->grid == PPM_GRID_HEALPIX) pix += 12LL * res->n_theta[b] * res->n_theta[b];
         const int nq = ip.n_phase * ip.n_sub;  // point samples (pt is a multiple of n_sub)
         ip.ring0 = hp.total_rings;
         ip.elem0 = (int)hp.total_elems;
@@ -600,7 +612,8 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
             hp.tiles.push_back(make_int2(begin, (int)hp.items.size()));
         }
     }
-    if (hp.total_elems > (size_t)INT32_MAX) return fail(ctx, PPM_EINVAL, "problem too large");
+    if (hp.total_elems > (size_t)INT32_MAX || pix > (long long)INT32_MAX)
+        return fail(ctx, PPM_EINVAL, "problem too large");
     // launch order: largest items first (longest-processing-time heuristic)
     hp.order.resize(hp.items.size());
     {
@@ -648,6 +661,7 @@ struct Work {
     int *status;
     RingRec *recs;
     float *tmpl, *elems, *partials, *Ft;
+    float2 *elemx;  // temperature maps only
     double *row_ll;
     // gradient only
     float *lambda, *Aadj, *ringadj;
@@ -666,6 +680,7 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     const size_t o_recs = take((size_t)hp.total_rings * sizeof(RingRec));
     const size_t o_tmpl = take((size_t)hp.total_rings * 4 * (n_fp + 1) * sizeof(float));
     const size_t o_elems = take(hp.total_elems * sizeof(float));
+    const size_t o_elemx = take(p->logT_map ? hp.total_elems * sizeof(float2) : 0);
     const size_t o_part = take((size_t)hp.items.size() * hp.pt * ctx->nEpad * sizeof(float));
     const size_t o_ft = take(need_ft ? (size_t)hp.total_rows * ctx->E.size() * sizeof(float) : 0);
     const size_t o_ll = take(need_ft ? (size_t)hp.total_rows * ct * sizeof(double) : 0);
@@ -684,6 +699,7 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     w->recs = reinterpret_cast<RingRec *>(base + o_recs);
     w->tmpl = reinterpret_cast<float *>(base + o_tmpl);
     w->elems = reinterpret_cast<float *>(base + o_elems);
+    w->elemx = p->logT_map ? reinterpret_cast<float2 *>(base + o_elemx) : nullptr;
     w->partials = reinterpret_cast<float *>(base + o_part);
     w->Ft = reinterpret_cast<float *>(base + o_ft);
     w->row_ll = reinterpret_cast<double *>(base + o_ll);
@@ -703,6 +719,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     P->incl_rad = p->incl_rad; P->dist_kpc = p->dist_kpc; P->nh_1e20 = p->nh_1e20;
     P->colat = p->colat; P->azim = p->azim; P->zeta = p->zeta; P->logT = p->logT;
     P->mask_colat = p->mask_colat; P->mask_azim = p->mask_azim; P->mask_zeta = p->mask_zeta;
+    P->logT_map = p->logT_map;
     const HostPlan &hp = ctx->plan;
     const size_t b_inst = align256(hp.inst.size() * sizeof(InstPlan));
     const size_t b_items = align256(hp.items.size() * sizeof(Item));
@@ -756,14 +773,16 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
     {
         StageTimer t(ctx, 0, st);
         PPM_CUDA(launch_ring(P, plan, L, A, w->recs, w->tmpl, w->elems, w->status, ctx->d_err,
-                             ctx->timing ? ctx->d_triples : nullptr, (int)ctx->E.size(), st),
+                             ctx->timing ? ctx->d_triples : nullptr, (int)ctx->E.size(), st,
+                             w->elemx),
                  "ring kernel");
         t.done(1);
     }
     {
         StageTimer t(ctx, 1, st);
         PPM_CUDA(launch_shift_add(P, plan, A, en, w->recs, w->tmpl, w->elems, w->status,
-                                  w->partials, ctx->plan.n_phi_max, st, 2 * ctx->sm_count),
+                                  w->partials, ctx->plan.n_phi_max, st, 2 * ctx->sm_count,
+                                  w->elemx),
                  "shift-and-add kernel");
         t.done(1);
     }
@@ -876,6 +895,8 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     if (!grad) return fail(ctx, PPM_EINVAL, "null grad");
     if (res && res->grid != PPM_GRID_SPOT)
         return fail(ctx, PPM_EINVAL, "the gradient needs the spot grid (PPM_GRID_SPOT)");
+    if (p && p->logT_map)
+        return fail(ctx, PPM_EINVAL, "the gradient does not support temperature maps");
     if ((s = check_params(ctx, p, res)) != PPM_OK) return s;
     if ((s = refresh_energies(ctx)) != PPM_OK) return s;
     DeviceGuard g(ctx->device);
@@ -1171,6 +1192,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     if (!Ft) return fail(ctx, PPM_EINVAL, "null Ft");
     ppm_status s = check_params(ctx, p, res);
     if (s != PPM_OK) return s;
+    if (p->logT_map)
+        return fail(ctx, PPM_EINVAL, "ppm_profile_noalloc does not support temperature maps");
     if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
         return fail(ctx, PPM_EINVAL, "device index beyond %d", kNoAllocMaxDevices);
     DeviceGuard guard(ctx->device);
@@ -1224,6 +1247,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
         ip.n_theta = rings_per_spot(res, b);
         ip.n_phi = slots_per_ring(res, b);
         ip.n_phase = res->n_phase[b];
+        ip.pix0 = 0;
         ip.n_sub = res->phase_sub;
         const int nq = ip.n_phase * ip.n_sub;
         ip.ring0 = rings;
@@ -1271,6 +1295,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     P.incl_rad = p->incl_rad; P.dist_kpc = p->dist_kpc; P.nh_1e20 = p->nh_1e20;
     P.colat = p->colat; P.azim = p->azim; P.zeta = p->zeta; P.logT = p->logT;
     P.mask_colat = p->mask_colat; P.mask_azim = p->mask_azim; P.mask_zeta = p->mask_zeta;
+    P.logT_map = nullptr;
     PlanDev plan;
     plan.B = p->B; plan.n_fp = res->n_fp; plan.n_items = L.n_items; plan.grid = res->grid;
     plan.total_rings = L.total_rings; plan.pt = L.pt;

@@ -67,6 +67,7 @@ struct AtmDev {
 struct InstPlan {
     int n_theta, n_phi, n_phase;
     int n_sub;   // point samples per output phase (the items run n_phase * n_sub of them)
+    int pix0;    // first pixel of the instance in the temperature map (HEALPix ring order)
     int ring0;   // first global ring index
     int elem0;   // first element slot (rings of this instance use n_phi slots each)
     int row0;    // first F_t row
@@ -86,7 +87,7 @@ struct RingRec {
     int iT, ig;     // first (logT, logg) node of the ring's interpolation stencil
     int tT, tg;     // stencil taps along logT and logg (2 linear, 4 cubic)
     float kT;       // keV (blackbody emission)
-    float pad;
+    int map;        // 1: per-element temperatures (map); iT .. iT + tT - 1 are the logT cells used
     float wT[4], wg[4];    // stencil weights
     float dwT[4], dwg[4];  // their derivatives d/dlogT, d/dlogg (0 where clamped)
 };
@@ -96,6 +97,7 @@ struct Params {
     const double *mass_msun, *radius_km, *spin_hz, *incl_rad, *dist_kpc, *nh_1e20;
     const double *colat, *azim, *zeta, *logT;
     const double *mask_colat, *mask_azim, *mask_zeta;
+    const double *logT_map;   // per-pixel log10 T (HEALPix ring order) or null
 };
 
 struct PlanDev {
@@ -123,10 +125,12 @@ struct EnergyDev {
 cudaError_t launch_lens_build(const LensDev &L, double dalpha, double *psi_scratch,
                               double *list_scratch, int j_cap, cudaStream_t st);
 
+// elemx: per element (weight of the upper logT node or kT, logT cell as int
+// bits) for temperature maps; may be null without a map
 cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
                         const AtmDev &A, RingRec *recs, float *tmpl, float *elems,
                         int *status, unsigned *err, unsigned long long *triples, int nE,
-                        cudaStream_t st);
+                        cudaStream_t st, float2 *elemx = nullptr);
 
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max);
@@ -134,7 +138,8 @@ size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
-                             int n_phi_max, cudaStream_t st, int grid_blocks = 0);
+                             int n_phi_max, cudaStream_t st, int grid_blocks = 0,
+                             const float2 *elemx = nullptr);
 
 cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
                           const int *status, int total_rows, float *Ft, cudaStream_t st);

@@ -99,10 +99,20 @@ __device__ int axis_stencil(const double *x, int n, double q, int rule, int *tap
     return s0;
 }
 
+// ring-order index of the first pixel of HEALPix ring i (1-based), N = N_side
+__device__ __forceinline__ long long healpix_first_pixel(int N, int i)
+{
+    const long long n = N;
+    if (i < N) return 2LL * i * (i - 1);
+    if (i <= 3 * N) return 2LL * n * (n - 1) + (long long)(i - N) * 4 * n;
+    const long long k = 4LL * N - i;
+    return 12LL * n * n - 2 * k * (k + 1);
+}
+
 __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L, AtmDev A,
                                              RingRec *recs, float *tmpl, float *elems,
                                              int *status, unsigned *err,
-                                             unsigned long long *triples, int nE)
+                                             unsigned long long *triples, int nE, float2 *elemx)
 {
     const int g = blockIdx.x;
     const int b = find_instance_by_ring(plan.inst, plan.B, g);
@@ -114,7 +124,8 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
 
     __shared__ double sF[kMaxFp + 1], sZ[kMaxFp + 1], sPh[kMaxFp + 1], sMu[kMaxFp + 1];
     __shared__ RingGeo G;
-    __shared__ int s_inv_min, s_inv_max, s_vis0, s_base, s_wsum[8];
+    __shared__ int s_inv_min, s_inv_max, s_vis0, s_base, s_wsum[8], s_cmin, s_cmax;
+    const bool use_map = p.logT_map != nullptr;  // (HEALPix mesh only)
 
     if (threadIdx.x == 0) {
         const double GM = p.mass_msun[b] * kGM_SUN;
@@ -148,8 +159,9 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             th = acos(z);
             G.dphi = 2.0 * kPI / G.n_el;
             dcos = (kPI / (3.0 * NN * NN)) / G.dphi;
-            // rings that cannot reach the emitter cap hold no pixel of the spot
-            half = fabs(th - tc) <= zt + 1e-12 ? kPI : 0.0;
+            // rings that cannot reach the emitter cap hold no pixel of the spot;
+            // with a temperature map every ring is a candidate
+            half = (use_map || fabs(th - tc) <= zt + 1e-12) ? kPI : 0.0;
             G.cap_c = cos(zt);
             G.cap_ct = cos(tc);
             G.cap_st = sin(tc);
@@ -203,19 +215,24 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         G.mask_st = sin(p.mask_colat[sidx]);
         G.mask_phi = p.mask_azim[sidx];
         // range checks (per-instance status)
-        bool in_range = u >= L.u_min && u <= L.u_max && zt > 0.0 && zt <= kPI && tc >= 0.0 &&
-                        tc <= kPI && D > 0.0 && nu >= 0.0 && G.beta < 1.0 && Re > Rs &&
-                        p.incl_rad[b] >= 0.0 && p.incl_rad[b] <= kPI && isfinite(G.area);
+        bool in_range = u >= L.u_min && u <= L.u_max && D > 0.0 && nu >= 0.0 &&
+                        G.beta < 1.0 && Re > Rs && p.incl_rad[b] >= 0.0 &&
+                        p.incl_rad[b] <= kPI && isfinite(G.area);
+        if (!use_map) in_range = in_range && zt > 0.0 && zt <= kPI && tc >= 0.0 && tc <= kPI;
         if (p.emission == 1) {
-            const double lt = p.logT[sidx];
-            in_range = in_range && lt >= A.logT[0] && lt <= A.logT[A.nT - 1] &&
-                       G.logg >= A.logg[0] && G.logg <= A.logg[A.ng - 1];
+            in_range = in_range && G.logg >= A.logg[0] && G.logg <= A.logg[A.ng - 1];
+            if (!use_map) {
+                const double lt = p.logT[sidx];
+                in_range = in_range && lt >= A.logT[0] && lt <= A.logT[A.nT - 1];
+            }
         }
         if (!in_range) atomicMax(&status[b], (int)PPM_ERANGE);
         G.ok = in_range && half > 0.0;
         s_inv_min = n_fp;
         s_inv_max = 0;
         s_vis0 = 0;
+        s_cmin = 1 << 30;
+        s_cmax = -1;
     }
     __syncthreads();
 
@@ -291,6 +308,9 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
     int n_active = 0;
     if (G.ok) {
         float *ep = elems + (size_t)ip.elem0 + (size_t)local * ip.n_phi;
+        float2 *xp = use_map ? elemx + (size_t)ip.elem0 + (size_t)local * ip.n_phi : nullptr;
+        const long long pix_first =
+            use_map ? (long long)ip.pix0 + healpix_first_pixel((ip.n_theta + 1) / 4, r + 1) : 0;
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (threadIdx.x == 0) s_base = 0;
         __syncthreads();
@@ -298,7 +318,28 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             const int m = m0 + threadIdx.x;
             bool act = false;
             double phia = 0.0;
-            if (m < G.n_el) {
+            float2 xv = make_float2(0.0f, 0.0f);
+            if (m < G.n_el && use_map) {
+                // temperature map: the pixel's own log T; dark where not finite or <= 0
+                phia = G.phi0 + m * G.dphi;
+                const double lt = p.logT_map[pix_first + m];
+                act = isfinite(lt) && lt > 0.0;
+                if (act && p.emission == 1) {
+                    if (lt < A.logT[0] || lt > A.logT[A.nT - 1]) {
+                        atomicMax(&status[b], (int)PPM_ERANGE);
+                        act = false;
+                    } else {
+                        int taps;
+                        float w[4], dw[4];
+                        const int c = axis_stencil(A.logT, A.nT, lt, 0, &taps, w, dw);
+                        xv = make_float2(w[1], __int_as_float(c));
+                        atomicMin(&s_cmin, c);
+                        atomicMax(&s_cmax, c);
+                    }
+                } else if (act) {
+                    xv = make_float2((float)(kKB_KEVK * pow(10.0, lt)), 0.0f);
+                }
+            } else if (m < G.n_el) {
                 if (plan.grid == 1) {
                     // mesh pixel: inside the emitter cap (FP64, as in the oracle)
                     phia = G.phi0 + m * G.dphi;
@@ -317,7 +358,11 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             __syncthreads();
             int off = s_base;
             for (int w = 0; w < wid; ++w) off += s_wsum[w];
-            if (act) ep[off + __popc(bal & ((1u << lane) - 1u))] = (float)(phia / (2.0 * kPI));
+            if (act) {
+                const int slot = off + __popc(bal & ((1u << lane) - 1u));
+                ep[slot] = (float)(phia / (2.0 * kPI));
+                if (use_map) xp[slot] = xv;
+            }
             __syncthreads();
             if (threadIdx.x == 0) {
                 int tot = 0;
@@ -343,7 +388,13 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             rec.iT = axis_stencil(A.logT, A.nT, lt, rule, &rec.tT, rec.wT, rec.dwT);
             rec.ig = axis_stencil(A.logg, A.ng, G.logg, rule, &rec.tg, rec.wg, rec.dwg);
         }
-        rec.pad = 0.0f;
+        rec.map = use_map ? 1 : 0;
+        if (use_map && p.emission == 1) {
+            // the logT cells used by the ring's pixels
+            rec.iT = s_cmax >= 0 ? s_cmin : 0;
+            rec.tT = s_cmax >= 0 ? s_cmax - s_cmin + 1 : 0;
+            rec.ig = axis_stencil(A.logg, A.ng, G.logg, 0, &rec.tg, rec.wg, rec.dwg);
+        }
         recs[g] = rec;
         if (triples && rec.visible)
             atomicAdd(triples, (unsigned long long)n_active * ip.n_phase * ip.n_sub * nE);
@@ -354,11 +405,11 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
 
 cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L, const AtmDev &A,
                         RingRec *recs, float *tmpl, float *elems, int *status, unsigned *err,
-                        unsigned long long *triples, int nE, cudaStream_t st)
+                        unsigned long long *triples, int nE, cudaStream_t st, float2 *elemx)
 {
     if (plan.total_rings <= 0) return cudaSuccess;
     k_ring<<<plan.total_rings, 256, 0, st>>>(p, plan, L, A, recs, tmpl, elems, status, err,
-                                             triples, nE);
+                                             triples, nE, elemx);
     return cudaGetLastError();
 }
 

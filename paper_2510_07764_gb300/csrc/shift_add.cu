@@ -509,6 +509,235 @@ __global__ void __launch_bounds__(kSABlock, 2)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Full-surface temperature maps (Sect. 2.6): every element has its own logT.
+// One element per lane (scalar code).  For each logT cell used by a ring the
+// two logg-interpolated table planes of the cell are staged and an element's
+// spectrum is (1 - w) I_lo + w I_hi with its own weight w, i.e. each node is
+// contracted against both planes with the mu weights scaled by (1 - w) and w.
+// The analytic blackbody uses each element's kT.  Same items, partial tiles
+// and reduction as k_shift_add.
+// ---------------------------------------------------------------------------
+struct MapLayout {
+    int tmpl, elems, cs, cw, munodes, slab, slab2, pk, E, E3, fblk, total;
+};
+
+template <int EMIS>
+__global__ void __launch_bounds__(kSABlock, 1)
+    k_shift_add_map(Params p, PlanDev plan, AtmDev A, EnergyDev en, MapLayout lay,
+                    const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
+                    const float *__restrict__ elems, const float2 *__restrict__ elemx,
+                    const int *__restrict__ status, float *__restrict__ partials)
+{
+    extern __shared__ float sm[];
+    __shared__ int s_wsum[kSABlock / 32], s_cnt;
+    const int item_id = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
+    const Item it = plan.items[item_id];
+    const InstPlan ip = plan.inst[it.b];
+    const int n_fp = plan.n_fp, pt = plan.pt, nEpad = en.nEpad, nE = en.nE;
+    const int nch = nEpad / kEC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *Fblk = sm + lay.fblk;
+    float *spk = sm + lay.pk, *sE = sm + lay.E, *sE3 = sm + lay.E3;
+    float *cs = sm + lay.cs, *cw = sm + lay.cw;
+    for (int i = tid; i < pt * nEpad; i += blockDim.x) Fblk[i] = 0.0f;
+    for (int i = tid; i < nEpad; i += blockDim.x) {
+        spk[i] = en.pk[i];
+        sE[i] = en.E[i];
+        sE3[i] = en.E3[i];
+    }
+    if (EMIS == 1)
+        for (int i = tid; i < A.nmu; i += blockDim.x) sm[lay.munodes + i] = A.mu[i];
+    int top = 1;
+    while (top * 2 <= n_fp) top *= 2;
+    const float inv_nphase = 1.0f / (float)(ip.n_phase * ip.n_sub);
+    const float q_half = 0.5f * (float)(ip.n_sub - 1);
+    const float inv_dlnE = (EMIS == 1) ? (float)(1.0 / A.dlnE) : 0.0f;
+    const int Pm = A.nmu_pad;
+    const bool inst_ok = status[it.b] == 0;
+    const float *ph = sm + lay.tmpl;
+    const float *mun = sm + lay.munodes;
+    const float *S0 = sm + lay.slab, *S1 = sm + lay.slab2;
+    const float pk0 = spk[0], pkl = spk[nE - 1];
+    const float lz_safe = 1.25f - pk0;
+    const bool sliding = en.sliding != 0;
+
+    for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
+        const int ring = ip.ring0 + it.spot * ip.n_theta + r;
+        const RingRec *rp = recs + ring;
+        if (!rp->visible) continue;
+        const int n_act = rp->n_active;
+        const size_t e0 = (size_t)ip.elem0 + (size_t)(ring - ip.ring0) * ip.n_phi;
+        __syncthreads();
+        for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x)
+            sm[lay.tmpl + i] = tmpl[(size_t)ring * 4 * (n_fp + 1) + i];
+        const int c_lo = EMIS == 1 ? rp->iT : 0, c_n = EMIS == 1 ? rp->tT : 1;
+        for (int cell = c_lo; cell < c_lo + c_n; ++cell) {
+            __syncthreads();  // previous cell (or ring) done with the staged data
+            if (EMIS == 1) {
+                // the cell's two logT planes, interpolated linearly in logg
+                const int plane = A.nmu * A.nE;
+                const float wg0 = rp->wg[0], wg1 = rp->wg[1];
+                const float *Ia = A.I + ((size_t)cell * A.ng + rp->ig) * plane;
+                const float *Ib = Ia + (size_t)A.ng * plane;
+                for (int idx = tid; idx < plane; idx += blockDim.x) {
+                    const int m = idx / A.nE, n = idx - m * A.nE;
+                    sm[lay.slab + n * Pm + m] = wg0 * __ldg(Ia + idx) + wg1 * __ldg(Ia + plane + idx);
+                    sm[lay.slab2 + n * Pm + m] = wg0 * __ldg(Ib + idx) + wg1 * __ldg(Ib + plane + idx);
+                }
+            }
+            // the ring's elements in this cell, in ring order (stable compaction)
+            if (tid == 0) s_cnt = 0;
+            __syncthreads();
+            for (int m0 = 0; m0 < n_act; m0 += blockDim.x) {
+                const int m = m0 + tid;
+                bool in = false;
+                float2 x = make_float2(0.0f, 0.0f);
+                if (m < n_act) {
+                    x = elemx[e0 + m];
+                    in = EMIS == 1 ? __float_as_int(x.y) == cell : true;
+                }
+                const unsigned bal = __ballot_sync(kFull, in);
+                if (lane == 0) s_wsum[warp] = __popc(bal);
+                __syncthreads();
+                int off = s_cnt;
+                for (int w = 0; w < warp; ++w) off += s_wsum[w];
+                if (in) {
+                    const int slot = off + __popc(bal & ((1u << lane) - 1u));
+                    cs[slot] = elems[e0 + m];
+                    cw[slot] = x.x;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int tot = 0;
+                    for (int w = 0; w < kSABlock / 32; ++w) tot += s_wsum[w];
+                    s_cnt += tot;
+                }
+                __syncthreads();
+            }
+            const int cnt = s_cnt;
+            for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
+                const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
+                float *frow = Fblk + jl * nEpad;
+                for (int g0 = 0; g0 < cnt; g0 += 32) {
+                    const int m = g0 + lane;
+                    const bool on = m < cnt;
+                    if (EMIS == 1) {
+                        const PairW P = pair_weights<false>(on, on ? cs[m] : 0.0f, phi_out, ph,
+                                                            mun, n_fp, top, A, inv_dlnE);
+                        const float wT = on ? cw[m] : 0.0f;
+                        PairW Pa = P, Pb = P;
+                        Pa.w0 *= 1.0f - wT; Pa.w1 *= 1.0f - wT; Pa.w2 *= 1.0f - wT; Pa.w3 *= 1.0f - wT;
+                        Pb.w0 *= wT; Pb.w1 *= wT; Pb.w2 *= wT; Pb.w3 *= wT;
+                        const bool fast = P.on && sliding && (pk0 + P.lz >= 1.0f) &&
+                                          (pkl + P.lz < (float)(A.nE - 2));
+                        const bool slow = P.on && !fast;
+                        const float lz = fast ? P.lz : lz_safe;
+                        const float a0 = fast ? Pa.w0 : 0.f, a1 = fast ? Pa.w1 : 0.f;
+                        const float a2 = fast ? Pa.w2 : 0.f, a3 = fast ? Pa.w3 : 0.f;
+                        const float b0 = fast ? Pb.w0 : 0.f, b1 = fast ? Pb.w1 : 0.f;
+                        const float b2 = fast ? Pb.w2 : 0.f, b3 = fast ? Pb.w3 : 0.f;
+                        const float q = floorf(pk0 + lz);
+                        float off = lz - q;
+                        int n = (int)q + 2;  // last node of the window
+                        auto node = [&](int nn) {
+                            const int o = nn * Pm + P.s0;
+                            return dot4(S0 + o, a0, a1, a2, a3) + dot4(S1 + o, b0, b1, b2, b3);
+                        };
+                        float y0 = node(n - 3), y1 = node(n - 2), y2 = node(n - 1), y3 = node(n);
+                        float c0 = y1, c2 = fmaf(0.5f, y0 + y2, -y1);
+                        float c3 = fmaf(y3 - y0, 1.0f / 6.0f, 0.5f * (y1 - y2));
+                        float c1 = fmaf(y2 - y0, 0.5f, -c3);
+                        float W2 = y2, W3 = y3;
+                        for (int c = 0; c < nch; ++c) {
+                            float acc[kEC];
+#pragma unroll
+                            for (int k = 0; k < kEC; ++k) acc[k] = 0.0f;
+                            if (sliding) {
+#pragma unroll
+                                for (int k = 0; k < kEC; ++k) {
+                                    float t = spk[c * kEC + k] + off;
+                                    if (t >= 1.0f) {
+                                        ++n;
+                                        const float d = node(n), a = c0, bb = W2, cc = W3;
+                                        c0 = bb;
+                                        c2 = fmaf(0.5f, a + cc, -bb);
+                                        c3 = fmaf(d - a, 1.0f / 6.0f, 0.5f * (bb - cc));
+                                        c1 = fmaf(cc - a, 0.5f, -c3);
+                                        W2 = cc;
+                                        W3 = d;
+                                        off -= 1.0f;
+                                        t -= 1.0f;
+                                    }
+                                    acc[k] = fmaf(t, fmaf(t, fmaf(t, c3, c2), c1), c0);
+                                }
+                            }
+                            if (__any_sync(kFull, slow) && slow) {
+                                for (int k = 0; k < kEC; ++k) {
+                                    const float pp = spk[c * kEC + k] + P.lz;
+                                    acc[k] += eval_general(Pa, S0, Pm, A.nE, pp, false) +
+                                              eval_general(Pb, S1, Pm, A.nE, pp, false);
+                                }
+                            }
+                            const float tot = transpose_reduce16(acc, lane);
+                            if (lane < kEC) frow[c * kEC + lane] += tot;
+                        }
+                    } else {
+                        // analytic blackbody with the element's own kT
+                        const float K = (float)(2.0 / (kH_KEVS * kH_KEVS * kH_KEVS * kC_CM * kC_CM));
+                        float az = 1.0f, bz = 0.0f;
+                        if (on) {
+                            const float x = phi_out + cs[m] + 1.0f - ph[0];
+                            const float phip = x - floorf(x) + ph[0];
+                            float Fp, zp, mp;
+                            template_at(ph, n_fp, top, phip, Fp, zp, mp);
+                            if (Fp != 0.0f && zp > 0.0f && zp < 1e30f) {
+                                az = zp / cw[m];
+                                bz = Fp * K * zp * zp * zp;
+                            }
+                        }
+                        for (int c = 0; c < nch; ++c) {
+                            float acc[kEC];
+#pragma unroll
+                            for (int k = 0; k < kEC; ++k) {
+                                const int kk = c * kEC + k;
+                                acc[k] = bz != 0.0f ? bz * sE3[kk] / expm1f(az * sE[kk]) : 0.0f;
+                            }
+                            const float tot = transpose_reduce16(acc, lane);
+                            if (lane < kEC) frow[c * kEC + lane] += tot;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float *dst = partials + (size_t)item_id * pt * nEpad;
+    for (int i = tid; i < it.nj * nEpad; i += blockDim.x) dst[i] = Fblk[i];
+}
+
+MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
+                     int n_phi_max)
+{
+    MapLayout lay;
+    int off = 0;
+    auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
+    const int slab = p.emission == 1 ? A.nE * A.nmu_pad : 0;
+    lay.tmpl = take(4 * (plan.n_fp + 1));
+    lay.elems = 0;
+    lay.cs = take(n_phi_max);
+    lay.cw = take(n_phi_max);
+    lay.munodes = take(p.emission == 1 ? A.nmu : 0);
+    lay.slab = take(slab);
+    lay.slab2 = take(slab);
+    lay.pk = take(en.nEpad);
+    lay.E = take(en.nEpad);
+    lay.E3 = take(en.nEpad);
+    lay.fblk = take(plan.pt * en.nEpad);
+    lay.total = off;
+    return lay;
+}
+
 // F_t[row][k] = (sum over the work items of (instance, phase tile)) / E_k.
 // One block per (row, 128-energy chunk): warp w sums items w, w+8, ... with
 // float4 loads, then the 8 warp sums are added in warp order (fixed order, so
@@ -531,10 +760,10 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
     const int tile = q0 / pt, jl0 = q0 - tile * pt;
     const int2 rng = plan.tile_items[ip.tile0 + tile];
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int sub = 0; sub < ip.n_sub && 4 * k4 < nEpad; ++sub) {
-        const float4 *base =
-            reinterpret_cast<const float4 *>(partials + (size_t)(jl0 + sub) * nEpad) + k4;
-        const size_t stride4 = (size_t)pt * nEpad / 4;
+    const size_t stride4 = (size_t)pt * nEpad / 4;
+    const int n_sub = ip.n_sub;
+    if (4 * k4 < nEpad) {
+        const float4 *base = reinterpret_cast<const float4 *>(partials + (size_t)jl0 * nEpad) + k4;
         int i = rng.x + warp;
         for (; i + 8 < rng.y; i += 16) {
             const float4 a = base[(size_t)i * stride4], c = base[(size_t)(i + 8) * stride4];
@@ -544,6 +773,14 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
         if (i < rng.y) {
             const float4 a = base[(size_t)i * stride4];
             acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+        }
+        // further point samples of the same output phase (phase_sub > 1)
+        for (int sub = 1; sub < n_sub; ++sub) {
+            const float4 *bs = base + (size_t)sub * nEpad / 4;
+            for (int q = rng.x + warp; q < rng.y; q += 8) {
+                const float4 a = bs[(size_t)q * stride4];
+                acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+            }
         }
     }
     red[warp][threadIdx.x & 31] = acc;
@@ -570,6 +807,7 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max)
 {
+    if (p.logT_map) return (size_t)map_layout(p, plan, A, en, n_phi_max).total * sizeof(float);
     int off = 0;
     auto take = [&](int n) { off += (n + 3) & ~3; };
     take(4 * (plan.n_fp + 1));
@@ -586,9 +824,24 @@ size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
-                             int n_phi_max, cudaStream_t st, int grid_blocks)
+                             int n_phi_max, cudaStream_t st, int grid_blocks,
+                             const float2 *elemx)
 {
     if (plan.n_items <= 0) return cudaSuccess;
+    if (p.logT_map) {
+        // temperature maps: one block per item (the static schedule)
+        const MapLayout lay = map_layout(p, plan, A, en, n_phi_max);
+        const size_t bytes = (size_t)lay.total * sizeof(float);
+        auto go = [&](auto kern) -> cudaError_t {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)bytes);
+            if (r != cudaSuccess) return r;
+            kern<<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems,
+                                                        elemx, status, partials);
+            return cudaGetLastError();
+        };
+        return p.emission == 1 ? go(k_shift_add_map<1>) : go(k_shift_add_map<0>);
+    }
     // persistent schedule: the queue counter must start at zero on the stream
     if (plan.queue) {
         cudaError_t e0 = cudaMemsetAsync(plan.queue, 0, sizeof(int), st);

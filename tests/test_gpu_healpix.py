@@ -58,3 +58,48 @@ def test_mesh_noalloc_matches_profile(synth, atm, small_lens):
     assert st == 0
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+# ---- full-surface temperature maps ----------------------------------------
+def _smooth_map(orc, w, north_only=True):
+    from test_oracle_healpix import pixel_centres
+    th, ph = pixel_centres(orc, w)
+    lt = 6.0 + 0.2 * np.cos(th) + 0.05 * np.sin(2 * ph)
+    if north_only:
+        lt = np.where(th < 1.2, lt, 0.0)
+    return lt[None, :]
+
+
+def test_temperature_map_atmosphere(orc, synth, atm, small_lens):
+    w = on_mesh(synth.atm_two_spot(n_phase=32, n_E=64, n_chan=8, atm=atm, lens=small_lens), 24)
+    w.inst = w.inst.select([0])
+    w.inst.n_spots = 1
+    for f in ("colat", "azim", "zeta", "logT", "mask_colat", "mask_azim", "mask_zeta"):
+        setattr(w.inst, f, np.ascontiguousarray(getattr(w.inst, f)[:, :1]))
+    w.inst.logT_map = _smooth_map(orc, w)
+    Ft, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(Ft, orc.profile(w)) < 1e-3
+
+
+def test_temperature_map_blackbody(orc, synth, small_lens):
+    w = on_mesh(synth.bb_small(n_phase=32, n_E=24, lens=small_lens), 20)
+    w.inst.logT_map = _smooth_map(orc, w, north_only=False)
+    Ft, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(Ft, orc.profile(w)) < 1e-4
+
+
+def test_map_of_a_uniform_cap_equals_the_cap_on_gpu(orc, synth, small_lens):
+    from test_oracle_healpix import pixel_centres
+    import math
+    w = on_mesh(synth.bb_small(n_phase=32, n_E=24, lens=small_lens), 24)
+    w.inst.colat[:] = 1.0
+    w.inst.zeta[:] = 0.35
+    cap, _ = gpu_profile(w)
+    th, ph = pixel_centres(orc, w)
+    cd = np.cos(th) * math.cos(1.0) + np.sin(th) * math.sin(1.0) * np.cos(ph - w.inst.azim[0, 0])
+    w.inst.logT_map = np.where(cd >= math.cos(0.35), float(w.inst.logT[0, 0]), 0.0)[None, :]
+    mp, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(mp, cap) < 1e-6
