@@ -125,7 +125,7 @@ class _CD(C.Structure):
 class InstT(C.Structure):
     """orc_inst of the tangent build: every real field is a complex pair."""
     _fields_ = [(n, (_CD * t._length_) if hasattr(t, "_length_") else _CD)
-                if t in (C.c_double,) or (hasattr(t, "_type_") and t._type_ is C.c_double)
+                if t is C.c_double or (hasattr(t, "_length_") and t._type_ is C.c_double)
                 else (n, t) for n, t in InstC._fields_]
 
 
@@ -350,7 +350,7 @@ def loglike_tangent(w, v, b: int = 0, h: float = 1e-20):
         val = getattr(base, name)
         if t is C.c_double:
             getattr(ic, name).re = val
-        elif hasattr(t, "_type_") and t._type_ is C.c_double:
+        elif hasattr(t, "_length_") and t._type_ is C.c_double:
             arr = getattr(ic, name)
             for s in range(len(arr)):
                 arr[s].re = val[s]
