@@ -176,3 +176,70 @@ def test_grad_with_phase_sub_samples(orc, synth, atm, small_lens):
     ll, g, st = gpu_grad(w)
     assert st[0] == 0
     _check(g[0, :13], orc.grad_tangent(w))
+
+
+@pytest.mark.parametrize("strategy", ["d", "a"])
+def test_grad_energies_past_the_table_edges(orc, synth, atm, small_lens, strategy):
+    """Energies from 0.06 to 9.5 keV put redshifted queries beyond both ends of
+    the table's energy axis (clamped) and on its edge intervals (linear for the
+    method's scheme, one-sided cubic for strategy a): the backward pass's
+    general path."""
+    w = visible_two_cap(synth, atm, small_lens, n_theta=8, n_phi=12, n_phase=16, n_E=40,
+                        n_chan=20)
+    w.E_keV = synth.logspace(0.06, 9.5, 40)
+    w.R = synth.response(w.E_keV, 20)
+    w.sigma_ism = synth.sigma_ism(w.E_keV)
+    w.interp = strategy
+    ll, g, st = gpu_grad(w)
+    assert st[0] == 0
+    _check(g[0, :13], orc.grad_tangent(w))
+
+
+def test_grad_background_and_shared_counts(orc, synth, atm, small_lens):
+    """lambda = tau C + bkg and one block of counts shared by two instances."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = visible_two_cap(synth, atm, small_lens, n_theta=8, n_phi=12, n_phase=16, n_E=40,
+                        n_chan=20)
+    inst = w.inst.select([0, 0])
+    inst.incl_rad[1] = 0.7
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=w.counts, tau=w.tau)
+    bkg = np.full(w.counts.shape, 3.0, np.float32)
+    ctx = context(w2)
+    dp = ppm.DeviceParams(w2.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    ll, g = ctx.loglike_grad(dp, cnt, w.tau, bkg=torch.from_numpy(bkg).cuda(), counts_shared=True)
+    g = g.cpu().numpy()
+    for b in range(2):
+        # reference: central differences of the oracle with the background
+        from grad_helpers import NAMES, SCALE, get_param, set_param
+        single = synth.Workload("s", inst.select([b]), small_lens, w.E_keV, atm=atm, R=w.R,
+                                sigma_ism=w.sigma_ism, counts=w.counts, tau=w.tau)
+
+        def f(x, j):
+            i2 = single.inst.copy()
+            set_param(i2, j, x)
+            s2 = synth.Workload("s", i2, small_lens, w.E_keV, atm=atm, R=w.R,
+                                sigma_ism=w.sigma_ism, counts=w.counts, tau=w.tau)
+            C = orc.counts_model(orc.profile(s2), w.R, w.sigma_ism, float(i2.nh_1e20[0]))
+            return orc.loglike(C, w.counts, w.tau, bkg)
+        ref = np.zeros(13)
+        for j in range(13):
+            th = get_param(single.inst, j)
+            h = 1e-5 * max(abs(th), SCALE[j] / 10.0)
+            ref[j] = (f(th + h, j) - f(th - h, j)) / (2 * h)
+        _check(g[b], ref)
+
+
+def test_grad_of_an_invisible_instance_is_nan(synth, atm, small_lens):
+    """A star whose spots never face the observer has lambda = 0 with counts
+    > 0: logL = -inf and the gradient is not defined (NaN)."""
+    w = visible_two_cap(synth, atm, small_lens, n_theta=8, n_phi=12, n_phase=16, n_E=40,
+                        n_chan=20)
+    w.inst.incl_rad[0] = 0.0
+    w.inst.colat[0] = [np.pi - 0.05, np.pi - 0.08]
+    w.inst.zeta[0] = [0.03, 0.02]
+    ll, g, st = gpu_grad(w)
+    assert ll[0] == -np.inf and np.all(np.isnan(g[0]))
