@@ -10,7 +10,8 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libppm.so")
+# the bounds-checked build (libppm_check.so) is selected with PPM_LIB_PATH
+LIB_PATH = os.environ.get("PPM_LIB_PATH") or os.path.join(HERE, "libppm.so")
 
 PPM_OK, PPM_EINVAL, PPM_ERANGE, PPM_ENOMEM, PPM_ECUDA, PPM_ETIMEOUT, PPM_ENOTREADY = range(7)
 STATUS_NAMES = ["PPM_OK", "PPM_EINVAL", "PPM_ERANGE", "PPM_ENOMEM", "PPM_ECUDA", "PPM_ETIMEOUT",

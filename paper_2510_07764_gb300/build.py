@@ -1,4 +1,8 @@
-"""Build libppm.so (the CUDA kernels and the C ABI) for sm_103a, in-tree."""
+"""Build libppm.so (the CUDA kernels and the C ABI) for sm_103a, in-tree.
+
+build(check=True) builds the bounds-checked variant libppm_check.so
+(-DPPM_BOUNDS_CHECK: index checks at the table, slab and template gathers,
+reported through ppm_sync); select it with PPM_LIB_PATH."""
 from __future__ import annotations
 
 import concurrent.futures
@@ -10,6 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libppm.so")
+BUILD_CHECK = os.path.join(ROOT, "_build_check")
+LIB_CHECK = os.path.join(HERE, "libppm_check.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 SOURCES = ["api.cu", "lens.cu", "ring.cu", "shift_add.cu", "loglike.cu", "resp_tc.cu",
            "shift_add_bwd.cu", "ring_bwd.cu", "grad.cu", "peak.cu"]
@@ -25,17 +31,19 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, ptxas_info: bool = False, check: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECK, LIB_CHECK) if check else (BUILD, LIB)
+    flags = FLAGS + (["-DPPM_BOUNDS_CHECK"] if check else [])
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, "ppm_internal.cuh"), os.path.join(ROOT, "include", "ppm.h")]
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if _stale(o, [s] + headers) or ptxas_info:
-            cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
+            cmd = [NVCC] + flags + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", s, "-o", o]
             jobs.append(cmd)
 
     def run(cmd):
@@ -48,11 +56,11 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         for out in ex.map(run, jobs):
             if verbose and out.strip():
                 print(out)
-    if _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         run([NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -10,6 +10,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ppm_internal.cuh"
 
 using namespace ppm;
@@ -116,14 +118,28 @@ struct ppm_ctx {
 };
 
 namespace {
+// NVTX names of the timed stages (ranges around their launches, visible to
+// Nsight tools; no-ops without a tool attached)
+const char *const kStageName[] = {"ppm ring template", "ppm shift-and-add", "ppm reduce",
+                                  "ppm response + logL", "ppm response adjoint",
+                                  "ppm backward shift-and-add", "ppm template tangents"};
+
+// an NVTX range for the lifetime of one API call
+struct NvtxCall {
+    explicit NvtxCall(const char *name) { nvtxRangePushA(name); }
+    ~NvtxCall() { nvtxRangePop(); }
+};
+
 // records an event pair around one stage when timing is enabled
 struct StageTimer {
     ppm_ctx *c;
     int stage;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
+    bool open = true;
     StageTimer(ppm_ctx *c_, int stage_, cudaStream_t st_) : c(c_), stage(stage_), st(st_)
     {
+        nvtxRangePushA(kStageName[stage]);
         if (!c->timing) return;
         a = take();
         if (a) cudaEventRecord(a, st);
@@ -139,8 +155,14 @@ struct StageTimer {
         if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
         return e;
     }
+    ~StageTimer()
+    {
+        if (open) nvtxRangePop();
+    }
     void done(int kernels)
     {
+        if (open) nvtxRangePop();
+        open = false;
         if (!c->timing) return;
         c->acc.launches += kernels;
         if (!a) return;
@@ -733,6 +755,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     plan->order = reinterpret_cast<const int *>(
         d + b_inst + b_items + align256(hp.tiles.size() * sizeof(int2)));
     plan->queue = ctx->tile_persistent ? ctx->d_queue : nullptr;
+    plan->err = ctx->d_err;
     const ppm_lens_spec &s = ctx->lens;
     L->u_min = s.u_min; L->u_max = s.u_max; L->n_u = s.n_u;
     L->cpsi_min = s.cpsi_min; L->cpsi_max = s.cpsi_max; L->n_cpsi = s.n_cpsi;
@@ -799,6 +822,7 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
 ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
                        int *inst_status, void *stream)
 {
+    NvtxCall nvtx_("ppm_profile");
     if (!ctx) return PPM_EINVAL;
     if (!Ft) return fail(ctx, PPM_EINVAL, "null Ft");
     DeviceGuard g(ctx->device);
@@ -867,6 +891,7 @@ ppm_status ppm_loglike(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, co
                        int counts_shared, const float *bkg, double tau, double *logL,
                        float *model_counts, int *inst_status, void *stream)
 {
+    NvtxCall nvtx_("ppm_loglike");
     if (!ctx) return PPM_EINVAL;
     ppm_status s = check_loglike_args(ctx, p, res, counts, counts_shared, tau, logL);
     if (s != PPM_OK) return s;
@@ -889,6 +914,7 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
                             const int *counts, int counts_shared, const float *bkg, double tau,
                             double *logL, double *grad, int *inst_status, void *stream)
 {
+    NvtxCall nvtx_("ppm_loglike_grad");
     if (!ctx) return PPM_EINVAL;
     ppm_status s = check_loglike_args(ctx, p, res, counts, counts_shared, tau, logL);
     if (s != PPM_OK) return s;
@@ -1105,9 +1131,10 @@ ppm_status ppm_sync(ppm_ctx *ctx, void *stream, double timeout_s)
     PPM_CUDA(cudaMemcpy(&bits, ctx->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost), "read error word");
     if (bits) {
         PPM_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)), "clear error word");
-        return fail(ctx, PPM_ENOTREADY, "device invariant failed (bits 0x%x%s%s)", bits,
+        return fail(ctx, PPM_ENOTREADY, "device invariant failed (bits 0x%x%s%s%s)", bits,
                     (bits & kErrPhaseOrder) ? ": template observed phases not increasing" : "",
-                    (bits & kErrTimeout) ? ": a bounded in-kernel wait timed out" : "");
+                    (bits & kErrTimeout) ? ": a bounded in-kernel wait timed out" : "",
+                    (bits & kErrBounds) ? ": an index check failed" : "");
     }
     return PPM_OK;
 }
@@ -1304,6 +1331,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     plan.tile_items = reinterpret_cast<const int2 *>(dev + L.o_tiles);
     plan.order = nullptr;
     plan.queue = nullptr;
+    plan.err = ctx->d_err;
     const ppm_lens_spec &ls = ctx->lens;
     LensDev Ld;
     Ld.u_min = ls.u_min; Ld.u_max = ls.u_max; Ld.n_u = ls.n_u;

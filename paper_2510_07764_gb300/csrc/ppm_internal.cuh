@@ -33,7 +33,21 @@ enum : unsigned {
     kErrPhaseOrder = 1u,  // template observed phases not increasing
     kErrPlan = 2u,        // inconsistent plan (should not happen)
     kErrTimeout = 4u,     // a bounded wait inside a kernel gave up
+    kErrBounds = 8u,      // an index check of the bounds-checked build failed
 };
+
+// Bounds-checked build (-DPPM_BOUNDS_CHECK, build(check=True)): table, slab
+// and template gathers verify their indices and set kErrBounds in the
+// context's error word (reported by ppm_sync); the ordinary build compiles
+// the checks away.
+#ifdef PPM_BOUNDS_CHECK
+#define PPM_CHECK(cond, errp)                                   \
+    do {                                                        \
+        if (!(cond) && (errp)) atomicOr((errp), ppm::kErrBounds); \
+    } while (0)
+#else
+#define PPM_CHECK(cond, errp) ((void)0)
+#endif
 
 struct LensDev {
     double u_min, u_max;
@@ -109,6 +123,7 @@ struct PlanDev {
     const int2 *tile_items;  // [sum tiles] item range of (instance, tile)
     const int *order;        // launch order of the items (largest first); null = identity
     int *queue;              // persistent schedule: next-entry counter (null = one block per item)
+    unsigned *err;           // device error word (kErr* bits)
 };
 
 // Energy-side arrays (device).

@@ -360,6 +360,7 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             for (int w = 0; w < wid; ++w) off += s_wsum[w];
             if (act) {
                 const int slot = off + __popc(bal & ((1u << lane) - 1u));
+                PPM_CHECK(slot < ip.n_phi, plan.err);
                 ep[slot] = (float)(phia / (2.0 * kPI));
                 if (use_map) xp[slot] = xv;
             }

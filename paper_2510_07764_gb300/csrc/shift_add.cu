@@ -220,7 +220,7 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
                                           const float *slab, int Pm, int n_fp, int top,
                                           const AtmDev &A, float inv_dlnE, const float *spk,
                                           int nch, bool sliding, float pk0, float pkl,
-                                          float lz_safe, float *frow)
+                                          float lz_safe, float *frow, unsigned *errp)
 {
     constexpr int NS = 2 * NP;
     constexpr bool ONESIDED = MODE != 0, CLIP = MODE == 2;
@@ -243,6 +243,8 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
         PPM_C(w0, e) = a0; PPM_C(w1, e) = a1; PPM_C(w2, e) = a2; PPM_C(w3, e) = a3;
         PPM_C(off, e) = lz - q;
         sp[e] = slab + ((int)q + 2) * Pm + P.s0;
+        PPM_CHECK(sp[e] - 3 * Pm >= slab && sp[e] + 3 < slab + A.nE * Pm && P.s0 + 3 < A.nmu,
+                  errp);
         const float na = dot4(sp[e] - 3 * Pm, a0, a1, a2, a3);
         const float nb = dot4(sp[e] - 2 * Pm, a0, a1, a2, a3);
         const float nc = dot4(sp[e] - Pm, a0, a1, a2, a3);
@@ -276,6 +278,7 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
             for (int e = 0; e < NS; ++e) {
                 if (PPM_C(t, e) >= 1.0f) {
                     sp[e] += Pm;
+                    PPM_CHECK(sp[e] + 3 < slab + A.nE * Pm, errp);
                     const float d = dot4(sp[e], PPM_C(w0, e), PPM_C(w1, e), PPM_C(w2, e),
                                          PPM_C(w3, e));
                     const float a = PPM_C(c0, e), b = PPM_C(W2, e), cc = PPM_C(W3, e);
@@ -389,10 +392,14 @@ __global__ void __launch_bounds__(kSABlock, 2)
             const float *tsrc = tmpl + (size_t)ring * 4 * (n_fp + 1);
             for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) sm[lay.tmpl + i] = tsrc[i];
             const float *esrc = elems + (size_t)ip.elem0 + (size_t)(ring - ip.ring0) * ip.n_phi;
+            PPM_CHECK(rec.n_active <= ip.n_phi && ring < plan.total_rings, plan.err);
             for (int i = tid; i < rec.n_active; i += blockDim.x) sm[lay.elems + i] = esrc[i];
             if (EMIS == 1) {
                 const int plane = A.nmu * A.nE;
                 const float *I0 = A.I + ((size_t)rec.iT * A.ng + rec.ig) * plane;
+                PPM_CHECK(rec.iT >= 0 && rec.iT + rec.tT <= A.nT && rec.ig >= 0 &&
+                              rec.ig + rec.tg <= A.ng,
+                          plan.err);
                 const bool lin2 = rec.tT == 2 && rec.tg == 2;
                 const float w00 = rp->wT[0] * rp->wg[0], w01 = rp->wT[0] * rp->wg[1];
                 const float w10 = rp->wT[1] * rp->wg[0], w11 = rp->wT[1] * rp->wg[1];
@@ -445,12 +452,12 @@ __global__ void __launch_bounds__(kSABlock, 2)
                     if (n_act - g0 > 64) {
                         atm_group<2, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
                                      A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
-                                     Fblk + jl * nEpad);
+                                     Fblk + jl * nEpad, plan.err);
                         g0 += 128;
                     } else {
                         atm_group<1, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
                                      A, inv_dlnE, spk, nch, sliding, pk0, pkl, lz_safe,
-                                     Fblk + jl * nEpad);
+                                     Fblk + jl * nEpad, plan.err);
                         g0 += 64;
                     }
                 }
@@ -759,6 +766,8 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
     const int q0 = (row - ip.row0) * ip.n_sub;
     const int tile = q0 / pt, jl0 = q0 - tile * pt;
     const int2 rng = plan.tile_items[ip.tile0 + tile];
+    PPM_CHECK(tile < ip.tiles && rng.x >= 0 && rng.y <= plan.n_items && jl0 + ip.n_sub <= pt,
+              plan.err);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const size_t stride4 = (size_t)pt * nEpad / 4;
     const int n_sub = ip.n_sub;

@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                     const float q = floorf(pk0 + lz);
                     float off = lz - q;
                     const float *sp = S + ((int)q + 2) * Pm + P.s0;
+                    PPM_CHECK(sp - 3 * Pm >= S && sp + 3 < S + A.nE * Pm, plan.err);
                     // (I, I_mu) and (I_T, I_g) as packed pairs: one FFMA2 chain each
                     auto nodeIM = [&](const float *r) {
                         return make_float2(dot4(r, a0, a1, a2, a3), dot4(r, b0, b1, b2, b3));
@@ -413,6 +414,7 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                         float t = pka.x + off;
                         if (t >= 1.0f) {
                             sp += Pm;
+                            PPM_CHECK(sp + 3 < S + A.nE * Pm, plan.err);
                             cubic2_shift(cIM, nodeIM(sp));
                             cubic2_shift(cTG, nodeTG(sp));
                             d1 = 2.0f * cIM.c2.x;
@@ -474,6 +476,7 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                 }
             }
             if (P.on) {
+                PPM_CHECK(P.i >= 0 && P.i + 1 <= n_fp, plan.err);
                 const float w = P.w, u = 1.0f - w;
                 atomicAdd(&gF[P.i], gFp * u);
                 atomicAdd(&gF[P.i + 1], gFp * w);
