@@ -69,4 +69,4 @@ def test_bounds_checked_build_reports_no_violation(tmp_path):
     b = _run(tmp_path, build.build())
     import numpy as np
     for k in a:
-        assert np.array_equal(a[k], b[k]) or np.allclose(a[k], b[k], rtol=1e-6, atol=0), k
+        assert np.allclose(a[k], b[k], rtol=1e-6, atol=0, equal_nan=True), k
