@@ -110,3 +110,33 @@ def test_fp32_fma_microbenchmark():
         assert st == 0
         # a GB300 sustains tens of TFLOP/s of FP32 FMA; the derived peak is 80.5
         assert 10.0 < tf < 200.0, (paired, tf)
+
+
+def test_full_batch_sampled_instances_match_oracle(orc, synth, atm):
+    """The 4096-instance mixed batch at full size (default lens grid, 256
+    energies): 64 seeded instances, 4 phases x 16 energies of each, against
+    the oracle, 1e-3 relative where the flux is above 1e-6 of the instance's
+    maximum."""
+    from gpu_helpers import gpu_profile
+    from grad_helpers import single
+    w = synth.batch(atm=atm)
+    Ft, st = gpu_profile(w)
+    rng = np.random.default_rng(11)
+    picks = rng.choice(w.inst.B, 64, replace=False)
+    row0 = np.concatenate([[0], np.cumsum(w.inst.n_phase)])
+    worst, checked = 0.0, 0
+    for b in picks:
+        if st[b] != 0:
+            continue
+        n = int(w.inst.n_phase[b])
+        js = np.sort(rng.choice(n, 4, replace=False)).astype(np.int32)
+        ks = np.sort(rng.choice(len(w.E_keV), 16, replace=False)).astype(np.int32)
+        ref = orc.profile(single(w, b), jsel=js, ksel=ks)
+        got = Ft[row0[b] + js][:, ks]
+        floor = 1e-6 * np.abs(Ft[row0[b]:row0[b] + n]).max()
+        m = np.abs(ref) > floor
+        if m.any():
+            worst = max(worst, float(np.max(np.abs(got[m] / ref[m] - 1.0))))
+            checked += 1
+    assert checked >= 40
+    assert worst < 1e-3, worst
