@@ -408,7 +408,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     timing = ctx.get_timing()
     ctx.set_timing(False)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    dev_ms = sum(step_ms)
     n_bad = 0 if profile_mode else int((~np.isfinite(logL.cpu().numpy())).sum())
     fwd_ms = None
     if grad_mode:
@@ -500,6 +501,7 @@ def run_ours(args, rank, world, local_rank):
     unit = "grad-evals/s" if grad_mode else ("profile evals/s" if profile_mode else "evals/s")
     line = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dev_ms / args.steps,
+            "ms_per_step_median": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": cfg,
             "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(h2d),
