@@ -970,7 +970,7 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     {
         StageTimer t(ctx, 5, st);
         PPM_CUDA(launch_shift_add_bwd(P, plan, A, en, w.recs, w.tmpl, w.elems, w.status, w.Aadj,
-                                      w.ringadj, hp.n_phi_max, st),
+                                      w.ringadj, hp.n_phi_max, st, ctx->smem_optin),
                  "backward shift-and-add kernel");
         t.done(1);
     }

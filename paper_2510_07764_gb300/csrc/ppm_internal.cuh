@@ -193,7 +193,8 @@ size_t shift_add_bwd_smem_bytes(int emission, const PlanDev &plan, const AtmDev 
 cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const AtmDev &A,
                                  const EnergyDev &en, const RingRec *recs, const float *tmpl,
                                  const float *elems, const int *status, const float *Aadj,
-                                 float *ringadj, int n_phi_max, cudaStream_t st);
+                                 float *ringadj, int n_phi_max, cudaStream_t st,
+                                 size_t smem_limit);
 cudaError_t launch_template_bwd(const Params &p, const PlanDev &plan, const LensDev &L,
                                 const AtmDev &A, const RingRec *recs, const float *tmpl,
                                 const int *status, const float *ringadj, double *ring_grad,

@@ -31,6 +31,7 @@ constexpr int kBwdBlock = 512;
 
 struct BLayout {
     int tmpl, elems, munodes, pk, E3, arow, adj, red, slab, slabT, slabG, total;
+    int det;  // 1: one adjoint copy per warp, added in a fixed order (bitwise reproducible)
 };
 
 __device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, float w1, float w2,
@@ -294,10 +295,14 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
         for (int i = tid; i < rec_len; i += blockDim.x) out[i] = 0.0f;
         return;
     }
-    float *adj = sm + lay.adj;  // gF | gZ | gMu | gPh
-    float *red = sm + lay.red;  // 4 ring sums
-    for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) adj[i] = 0.0f;
-    if (tid < 4) red[tid] = 0.0f;
+    // template adjoints gF | gZ | gMu | gPh: one copy per warp in the
+    // reproducible mode (lanes add in a fixed order, copies are summed in warp
+    // order at the end), else one copy updated with shared-memory atomics
+    const int alen = 4 * (n_fp + 1);
+    const int ncopy = lay.det ? kBwdBlock / 32 : 1;
+    float *adj = sm + lay.adj;
+    float *red = sm + lay.red;  // 4 ring sums per warp
+    for (int i = tid; i < ncopy * alen; i += blockDim.x) adj[i] = 0.0f;
     {
         const float *tsrc = tmpl + (size_t)ring * 4 * (n_fp + 1);
         for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) sm[lay.tmpl + i] = tsrc[i];
@@ -361,7 +366,8 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
     const float s_ref = sel[0];
     const float inv_kT = 1.0f / rec.kT;
     const float Kbb = (float)(2.0 / (kH_KEVS * kH_KEVS * kH_KEVS * kC_CM * kC_CM));
-    float *gF = adj, *gZ = adj + (n_fp + 1), *gM = adj + 2 * (n_fp + 1), *gP = adj + 3 * (n_fp + 1);
+    float *adjw = adj + (lay.det ? warp * alen : 0);
+    float *gF = adjw, *gZ = adjw + (n_fp + 1), *gM = adjw + 2 * (n_fp + 1), *gP = adjw + 3 * (n_fp + 1);
     float lane_gs = 0.0f, lane_gss = 0.0f, lane_T = 0.0f, lane_G = 0.0f;
 
     for (int j = warp; j < n_q; j += kBwdBlock / 32) {
@@ -475,25 +481,51 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                     lane_T = fmaf(P.Fp, sR * inv_kT, lane_T);
                 }
             }
+            // the pair's contributions to the template adjoints at points i, i + 1
+            float vF0 = 0.f, vF1 = 0.f, vZ0 = 0.f, vZ1 = 0.f, vM0 = 0.f, vM1 = 0.f;
+            float vP0 = 0.f, vP1 = 0.f;
             if (P.on) {
                 PPM_CHECK(P.i >= 0 && P.i + 1 <= n_fp, plan.err);
                 const float w = P.w, u = 1.0f - w;
-                atomicAdd(&gF[P.i], gFp * u);
-                atomicAdd(&gF[P.i + 1], gFp * w);
-                atomicAdd(&gZ[P.i], gzp * u);
-                atomicAdd(&gZ[P.i + 1], gzp * w);
-                if (EMIS == 1) {
-                    atomicAdd(&gM[P.i], gmp * u);
-                    atomicAdd(&gM[P.i + 1], gmp * w);
-                }
+                vF0 = gFp * u; vF1 = gFp * w;
+                vZ0 = gzp * u; vZ1 = gzp * w;
+                vM0 = gmp * u; vM1 = gmp * w;
                 if (P.dphi > 0.0f) {
                     // phi_p = phi_out + s (mod 1); w = (phi_p - phi_o[i]) / (phi_o[i+1] - phi_o[i])
                     const float gw = gFp * P.dF + gzp * P.dZ + gmp * P.dM;
                     const float gwd = gw / P.dphi;
-                    atomicAdd(&gP[P.i], gwd * (w - 1.0f));
-                    atomicAdd(&gP[P.i + 1], -gwd * w);
+                    vP0 = gwd * (w - 1.0f);
+                    vP1 = -gwd * w;
                     lane_gs += gwd;
                     lane_gss = fmaf(gwd, s - s_ref, lane_gss);
+                }
+            }
+            if (lay.det) {
+                // lanes in increasing order into the warp's own copy
+                unsigned todo = __ballot_sync(kFull, P.on);
+                while (todo) {
+                    const int l = __ffs(todo) - 1;
+                    todo &= todo - 1;
+                    if (lane == l) {
+                        gF[P.i] += vF0; gF[P.i + 1] += vF1;
+                        gZ[P.i] += vZ0; gZ[P.i + 1] += vZ1;
+                        gM[P.i] += vM0; gM[P.i + 1] += vM1;
+                        gP[P.i] += vP0; gP[P.i + 1] += vP1;
+                    }
+                    __syncwarp();
+                }
+            } else if (P.on) {
+                atomicAdd(&gF[P.i], vF0);
+                atomicAdd(&gF[P.i + 1], vF1);
+                atomicAdd(&gZ[P.i], vZ0);
+                atomicAdd(&gZ[P.i + 1], vZ1);
+                if (EMIS == 1) {
+                    atomicAdd(&gM[P.i], vM0);
+                    atomicAdd(&gM[P.i + 1], vM1);
+                }
+                if (P.dphi > 0.0f) {
+                    atomicAdd(&gP[P.i], vP0);
+                    atomicAdd(&gP[P.i + 1], vP1);
                 }
             }
         }
@@ -508,15 +540,25 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
         lane_G += __shfl_xor_sync(kFull, lane_G, o);
     }
     if (lane == 0) {
-        atomicAdd(&red[0], lane_gs);
-        atomicAdd(&red[1], lane_gss);
-        atomicAdd(&red[2], lane_T);
-        atomicAdd(&red[3], lane_G);
+        red[4 * warp + 0] = lane_gs;
+        red[4 * warp + 1] = lane_gss;
+        red[4 * warp + 2] = lane_T;
+        red[4 * warp + 3] = lane_G;
     }
     __syncthreads();
-    for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x) out[i] = adj[i];
-    if (tid < kRingAdjTail)
-        out[4 * (n_fp + 1) + tid] = tid < 4 ? red[tid] : (tid == 4 ? s_ref : 0.0f);
+    for (int i = tid; i < alen; i += blockDim.x) {
+        float v = adj[i];
+        for (int c = 1; c < ncopy; ++c) v += adj[c * alen + i];
+        out[i] = v;
+    }
+    if (tid < kRingAdjTail) {
+        float v = tid == 4 ? s_ref : 0.0f;
+        if (tid < 4) {
+            v = 0.0f;
+            for (int w = 0; w < kBwdBlock / 32; ++w) v += red[4 * w + tid];
+        }
+        out[alen + tid] = v;
+    }
 }
 
 struct BwdSizes {
@@ -525,7 +567,7 @@ struct BwdSizes {
 };
 
 BwdSizes bwd_layout(int emission, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
-                    int n_phi_max)
+                    int n_phi_max, bool det = false)
 {
     BwdSizes z;
     BLayout &lay = z.lay;
@@ -538,12 +580,13 @@ BwdSizes bwd_layout(int emission, const PlanDev &plan, const AtmDev &A, const En
     lay.pk = take(en.nEpad);
     lay.E3 = take(emission == 1 ? 0 : en.nEpad);
     lay.arow = take((kBwdBlock / 32) * 2 * en.nEpad);
-    lay.adj = take(4 * (plan.n_fp + 1));
-    lay.red = take(4);
+    lay.adj = take((det ? kBwdBlock / 32 : 1) * 4 * (plan.n_fp + 1));
+    lay.red = take(4 * (kBwdBlock / 32));
     lay.slab = take(slab);
     lay.slabT = take(slab);
     lay.slabG = take(slab);
     lay.total = off;
+    lay.det = det ? 1 : 0;
     z.bytes = (size_t)off * sizeof(float);
     return z;
 }
@@ -559,10 +602,13 @@ size_t shift_add_bwd_smem_bytes(int emission, const PlanDev &plan, const AtmDev 
 cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const AtmDev &A,
                                  const EnergyDev &en, const RingRec *recs, const float *tmpl,
                                  const float *elems, const int *status, const float *Aadj,
-                                 float *ringadj, int n_phi_max, cudaStream_t st)
+                                 float *ringadj, int n_phi_max, cudaStream_t st,
+                                 size_t smem_limit)
 {
     if (plan.total_rings <= 0) return cudaSuccess;
-    const BwdSizes z = bwd_layout(p.emission, plan, A, en, n_phi_max);
+    // the reproducible mode when its per-warp adjoint copies fit in shared memory
+    BwdSizes z = bwd_layout(p.emission, plan, A, en, n_phi_max, true);
+    if (z.bytes > smem_limit) z = bwd_layout(p.emission, plan, A, en, n_phi_max, false);
     cudaError_t e;
     if (p.emission == 1 && A.strategy == kInterpB) {
         e = cudaFuncSetAttribute(k_shift_add_bwd<1, true>,
