@@ -257,3 +257,43 @@ def test_gradient_is_bitwise_reproducible(synth, atm):
     for _ in range(3):
         ll2, g2 = ctx.loglike_grad(dp, cnt, w.tau)
         assert torch.equal(g1, g2) and torch.equal(ll1, ll2)
+
+
+def test_gradient_ascent_recovers_parameters(synth, atm, small_lens):
+    """The autograd wrapper inside an optimiser: counts drawn from a known
+    parameter vector, ascent from a perturbed start raises logL and moves the
+    inclination and the spot colatitude back toward the truth."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    w = visible_two_cap(synth, atm, small_lens, n_theta=10, n_phi=14, n_phase=32, n_E=48,
+                        n_chan=30)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    truth = dp.theta().clone()
+    tau = w.tau * 1e3   # a long exposure: ~1e4 counts per bin
+    mc = torch.empty((dp.rows, w.nc), dtype=torch.float32, device="cuda")
+    ctx.loglike(dp, torch.zeros((dp.rows, w.nc), dtype=torch.int32, device="cuda"), tau,
+                model_counts=mc)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    counts = torch.poisson(mc.double(), generator=g).to(torch.int32)
+    start = truth.clone()
+    start[0, 2] += 0.06     # inclination
+    start[0, 5] -= 0.05     # colatitude of spot 1
+    theta = start.clone().requires_grad_(True)
+    free = torch.zeros_like(theta)
+    free[0, 2] = free[0, 5] = 1.0
+    opt = torch.optim.Adam([theta], lr=4e-3)
+    ll0 = None
+    for _ in range(60):
+        opt.zero_grad()
+        ll = ppm.LogLikelihood(theta, ctx, dp, counts, tau)
+        if ll0 is None:
+            ll0 = float(ll.detach())
+        (-ll.sum()).backward()
+        theta.grad *= free
+        opt.step()
+    ll1 = float(ppm.LogLikelihood(theta.detach(), ctx, dp, counts, tau))
+    assert ll1 > ll0 + 10.0
+    err0 = torch.abs(start - truth)[0, [2, 5]]
+    err1 = torch.abs(theta.detach() - truth)[0, [2, 5]]
+    assert torch.all(err1 < 0.3 * err0), (err0, err1)
