@@ -31,6 +31,12 @@
  * - A context is not thread-safe: calls on one context must be serialised
  *   (they may use different streams; the context's workspace is reused, so
  *   two compute calls on one context must not overlap on the GPU).
+ * - CUDA graphs: once a context has run a problem of the same resolution
+ *   (its plan, workspace and kernel attributes are then settled),
+ *   ppm_profile, ppm_loglike and ppm_loglike_grad enqueue only kernels and
+ *   asynchronous copies and can be captured; a replay reads the parameters,
+ *   counts and background again from the same device arrays.  A later call
+ *   that grows the workspace invalidates earlier captures.
  */
 #ifndef PPM_H
 #define PPM_H
