@@ -140,3 +140,36 @@ def test_full_batch_sampled_instances_match_oracle(orc, synth, atm):
             checked += 1
     assert checked >= 40
     assert worst < 1e-3, worst
+
+
+def test_cuda_graph_replay_of_the_gradient(synth, atm, small_lens):
+    """ppm_loglike_grad captured once and replayed after in-place parameter
+    updates equals the direct call bit for bit."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    w = _batch(synth, atm, small_lens, B=4)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    out = torch.empty(dp.B, dtype=torch.float64, device="cuda")
+    grad = torch.empty((dp.B, ppm.N_GRAD), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            ctx.loglike_grad(dp, cnt, w.tau, out=out, grad=grad, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.loglike_grad(dp, cnt, w.tau, out=out, grad=grad, stream=s)
+    th0 = dp.theta()
+    for k in range(2):
+        th = th0.clone()
+        th[:, 2] += 0.03 * (k + 1)
+        dp.set_theta(th)
+        g.replay()
+        torch.cuda.synchronize()
+        got_ll, got_g = out.clone(), grad.clone()
+        ref_ll, ref_g = ctx.loglike_grad(dp, cnt, w.tau)
+        torch.cuda.synchronize()
+        assert torch.equal(got_ll, ref_ll)
+        assert torch.equal(torch.nan_to_num(got_g), torch.nan_to_num(ref_g))
