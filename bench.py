@@ -62,6 +62,9 @@ def parse():
                     help="capture one step in a CUDA graph and time its replays")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the shift-and-add tiles with ppm_autotune before timing")
+    ap.add_argument("--walk", type=int, choices=[0, 1], default=0,
+                    help="energy walk of the atmosphere shift-and-add: 0 node-major where "
+                         "the energy grid allows it, 1 energy walk (ppm_tiles.walk)")
     return ap.parse_args()
 
 
@@ -356,6 +359,8 @@ def run_ours(args, rank, world, local_rank):
             ctx.loglike(dp, counts, w.tau, out=logL, stream=stream)
 
     tuned = None
+    if args.walk:
+        ctx.set_tiles(walk=args.walk)
     if args.autotune:
         tuned = ctx.autotune(dp)
     for _ in range(args.warmup):

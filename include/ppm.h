@@ -313,18 +313,27 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
  * `waves` waves of two blocks per SM; items run largest first, either one
  * block per item (persistent = 0) or as a queue drained by two resident
  * blocks per SM (persistent = 1).  phase_tile = 0 picks 16 or 32 from the
- * problem size.  The setting applies to later calls of the context.
+ * problem size.  walk selects how a warp steps through the energies with
+ * the atmosphere table: 0 (default) takes the node-major walk wherever the
+ * observed energy grid is uniform in ln E with a step of 0.34 to 0.498
+ * table nodes (every table interval then holds two or three observed
+ * energies; one interval per iteration for all elements of a warp), and the
+ * energy walk elsewhere; 1 always takes the energy walk (one observed
+ * energy per iteration, interval changes per element).  The two sum the
+ * same terms in a different order.  The setting applies to later calls of
+ * the context.
  *
  * ppm_autotune runs the forward profile of (p, res) once per candidate
  * (phase_tile 16/32 x waves 8/16/32 x persistent 0/1, one untimed and one
  * timed pass each, synchronising `stream`), keeps the fastest, and returns
- * it in *best (ms = its time).  Results do not depend on the choice
- * (the partial sums are added in a fixed order).
+ * it in *best (ms = its time; walk is left as set).  Results do not depend
+ * on the choice (the partial sums are added in a fixed order).
  * ------------------------------------------------------------------------ */
 typedef struct {
     int phase_tile;   /* 0 (automatic), 16 or 32 */
     int waves;        /* 1 .. 256, default 16 */
     int persistent;   /* 0 or 1 */
+    int walk;         /* 0 (node-major where it applies) or 1 (energy walk) */
     double ms;        /* ppm_autotune: time of the chosen candidate */
 } ppm_tiles;
 

@@ -257,22 +257,24 @@ class Context:
         self.last_status = status
         return out, grad
 
-    def set_tiles(self, phase_tile: int = 0, waves: int = 16, persistent: bool = False):
+    def set_tiles(self, phase_tile: int = 0, waves: int = 16, persistent: bool = False,
+                  walk: int = 0):
         """Work decomposition of the shift-and-add (see ppm_set_tiles)."""
         self._check(_abi.ppm_set_tiles(self.h, _abi.ppm_tiles(phase_tile, waves,
-                                                               int(persistent), 0.0)))
+                                                               int(persistent), int(walk), 0.0)))
 
     def get_tiles(self) -> dict:
         t = _abi.ppm_tiles()
         self._check(_abi.ppm_get_tiles(self.h, t))
-        return {"phase_tile": t.phase_tile, "waves": t.waves, "persistent": bool(t.persistent)}
+        return {"phase_tile": t.phase_tile, "waves": t.waves, "persistent": bool(t.persistent),
+                "walk": t.walk}
 
     def autotune(self, dp: DeviceParams, stream=None) -> dict:
         """Time the tile candidates on dp's problem, keep the fastest, return it."""
         t = _abi.ppm_tiles()
         self._check(_abi.ppm_autotune(self.h, dp.struct(), dp.res, _stream_handle(stream), t))
         return {"phase_tile": t.phase_tile, "waves": t.waves, "persistent": bool(t.persistent),
-                "ms": t.ms}
+                "walk": t.walk, "ms": t.ms}
 
     def set_timing(self, enable: bool = True):
         self._check(_abi.ppm_set_timing(self.h, int(enable)))

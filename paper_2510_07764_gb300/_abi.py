@@ -49,7 +49,7 @@ class ppm_params(C.Structure):
 
 class ppm_tiles(C.Structure):
     _fields_ = [("phase_tile", C.c_int), ("waves", C.c_int), ("persistent", C.c_int),
-                ("ms", C.c_double)]
+                ("walk", C.c_int), ("ms", C.c_double)]
 
 
 class ppm_timing(C.Structure):

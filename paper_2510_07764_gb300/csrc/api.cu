@@ -88,6 +88,7 @@ struct ppm_ctx {
     DevBuf d_E, d_E3, d_pk, d_invE;
     bool energy_dirty = true;
     int nEpad = 0, sliding = 0;
+    float walk_step = 0.0f;  // uniform pk step (node-major walk) or 0
     // response
     int nc = 0;
     DevBuf d_R, d_sigma, d_Rtc;  // d_Rtc: R split into bf16 hi/lo tiles for the tensor cores
@@ -95,6 +96,7 @@ struct ppm_ctx {
     int tile_pt = 0;          // output phases per item: 0 = automatic, 16 or 32
     int tile_waves = 16;      // target waves of 2 blocks per SM (sets the ring-group size)
     int tile_persistent = 0;  // 1: persistent blocks take items from a queue
+    int tile_walk = 0;        // 0: node-major walk where it applies, 1: energy walk
     int *d_queue = nullptr;
     // plan
     std::vector<int> plan_key;
@@ -462,6 +464,44 @@ ppm_status ppm_set_response_fine(ppm_ctx *ctx, const double *E_lo, const double 
 // ---------------------------------------------------------------------------
 // planning and launch
 // ---------------------------------------------------------------------------
+// Position of observed energy k on the table's ln E axis, in nodes.
+static float pk_of(const ppm_ctx *ctx, int k)
+{
+    return ctx->atm_ready ? (float)((std::log(ctx->E[k]) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
+}
+
+// The energy walk may slide along the table (consecutive pk differ by less
+// than one node and the grid spans less than the table's interior).
+static int sliding_of(const ppm_ctx *ctx)
+{
+    const int nE = (int)ctx->E.size();
+    if (!ctx->atm_ready || nE < 1) return 0;
+    for (int k = 0; k + 1 < nE; ++k)
+        if (!((double)pk_of(ctx, k + 1) - pk_of(ctx, k) < 0.999)) return 0;
+    return ((double)pk_of(ctx, nE - 1) - pk_of(ctx, 0) < ctx->nEt - 3.5) ? 1 : 0;
+}
+
+// Step of pk when the walk slides, pk is uniform to 1e-4 node and the step
+// lies in [0.34, 0.498], so that every table interval holds two or three
+// observed energies (the node-major walk of the shift-and-add); 0 otherwise.
+static float walk_step_of(const ppm_ctx *ctx)
+{
+    const int nE = (int)ctx->E.size();
+    if (nE < 2 || !sliding_of(ctx)) return 0.0f;
+    const double p0 = pk_of(ctx, 0);
+    const double d = ((double)pk_of(ctx, nE - 1) - p0) / (nE - 1);
+    if (!(d >= 0.34 && d <= 0.498)) return 0.0f;
+    for (int k = 0; k < nE; ++k)
+        if (!(std::fabs((double)pk_of(ctx, k) - (p0 + k * d)) <= 1e-4)) return 0.0f;
+    return (float)d;
+}
+
+// the atmosphere shift-and-add of this call takes the node-major walk
+static bool node_walk_on(const ppm_ctx *ctx, const ppm_params *p, float step)
+{
+    return p->emission == 1 && !p->logT_map && ctx->tile_walk == 0 && step > 0.0f;
+}
+
 static ppm_status refresh_energies(ppm_ctx *ctx)
 {
     if (!ctx->energy_dirty) return PPM_OK;
@@ -473,14 +513,9 @@ static ppm_status refresh_energies(ppm_ctx *ctx)
         E[k] = (float)e;
         E3[k] = (float)(e * e * e);
         invE[k] = (float)(1.0 / e);
-        pk[k] = ctx->atm_ready ? (float)((std::log(e) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
+        pk[k] = pk_of(ctx, std::min(k, nE - 1));
     }
-    int sliding = ctx->atm_ready ? 1 : 0;
-    if (sliding) {
-        for (int k = 0; k + 1 < nE; ++k)
-            if (!((double)pk[k + 1] - pk[k] < 0.999)) sliding = 0;
-        if (!((double)pk[nE - 1] - pk[0] < ctx->nEt - 3.5)) sliding = 0;
-    }
+    const int sliding = sliding_of(ctx);
     DeviceGuard g(ctx->device);
     PPM_CUDA(cudaDeviceSynchronize(), "sync");
     for (DevBuf *b : {&ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE})
@@ -491,6 +526,7 @@ static ppm_status refresh_energies(ppm_ctx *ctx)
     PPM_CUDA(cudaMemcpy(ctx->d_invE.p, invE.data(), nEpad * 4, cudaMemcpyHostToDevice), "copy");
     ctx->nEpad = nEpad;
     ctx->sliding = sliding;
+    ctx->walk_step = walk_step_of(ctx);
     ctx->energy_dirty = false;
     return PPM_OK;
 }
@@ -566,6 +602,8 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(res->grid);
     key.push_back(res->phase_sub);
     key.push_back(p->logT_map ? 1 : 0);
+    const bool node = node_walk_on(ctx, p, ctx->walk_step);
+    key.push_back(node ? 1 : 0);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
         key.push_back(res->n_phi[b]);
@@ -583,7 +621,9 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
                  ((res->n_phase[b] * res->phase_sub + pt - 1) / pt);
         return T;
     };
-    int pt = ring_tiles(kPT) < (long long)ctx->sm_count * 16 ? 16 : kPT;
+    // (16 with the node-major walk, whose ring buffers leave room for two
+    // blocks per SM only with 16-phase tiles)
+    int pt = (node || ring_tiles(kPT) < (long long)ctx->sm_count * 16) ? 16 : kPT;
     if (ctx->tile_pt == 16 || ctx->tile_pt == 32) pt = ctx->tile_pt;
     if (const char *env = getenv("PPM_PHASE_TILE")) {
         const int v = atoi(env);
@@ -770,6 +810,8 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     en->E = ctx->d_E.as<float>(); en->E3 = ctx->d_E3.as<float>();
     en->pk = ctx->d_pk.as<float>(); en->invE = ctx->d_invE.as<float>();
     en->sliding = ctx->sliding;
+    en->step = node_walk_on(ctx, p, ctx->walk_step) ? ctx->walk_step : 0.0f;
+    en->inv_step = en->step > 0.0f ? 1.0f / en->step : 0.0f;
 }
 
 static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
@@ -1000,9 +1042,11 @@ ppm_status ppm_set_tiles(ppm_ctx *ctx, const ppm_tiles *t)
     if (t->waves < 1 || t->waves > 256) return fail(ctx, PPM_EINVAL, "waves must be in [1, 256]");
     if (t->persistent != 0 && t->persistent != 1)
         return fail(ctx, PPM_EINVAL, "persistent must be 0 or 1");
+    if (t->walk != 0 && t->walk != 1) return fail(ctx, PPM_EINVAL, "walk must be 0 or 1");
     ctx->tile_pt = t->phase_tile;
     ctx->tile_waves = t->waves;
     ctx->tile_persistent = t->persistent;
+    ctx->tile_walk = t->walk;
     return PPM_OK;
 }
 
@@ -1012,6 +1056,7 @@ ppm_status ppm_get_tiles(ppm_ctx *ctx, ppm_tiles *t)
     t->phase_tile = ctx->tile_pt;
     t->waves = ctx->tile_waves;
     t->persistent = ctx->tile_persistent;
+    t->walk = ctx->tile_walk;
     t->ms = 0.0;
     return PPM_OK;
 }
@@ -1027,7 +1072,7 @@ ppm_status ppm_autotune(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, v
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PPM_CUDA(cudaEventCreate(&e0), "event");
     PPM_CUDA(cudaEventCreate(&e1), "event");
-    ppm_tiles cur{ctx->tile_pt, ctx->tile_waves, ctx->tile_persistent, 0.0};
+    ppm_tiles cur{ctx->tile_pt, ctx->tile_waves, ctx->tile_persistent, ctx->tile_walk, 0.0};
     ppm_tiles top = cur;
     top.ms = INFINITY;
     ppm_status s = PPM_OK;
@@ -1054,7 +1099,7 @@ ppm_status ppm_autotune(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, v
                     s = fail(ctx, PPM_ECUDA, "autotune timing failed");
                     break;
                 }
-                if (ms < top.ms) top = ppm_tiles{a, wv, q, (double)ms};
+                if (ms < top.ms) top = ppm_tiles{a, wv, q, ctx->tile_walk, (double)ms};
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1242,7 +1287,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
                ((res->n_phase[b] * res->phase_sub + kPT - 1) / kPT);
         max_theta = std::max(max_theta, rings_per_spot(res, b));
     }
-    const int pt = T32 < (long long)ctx->sm_count * 16 ? 16 : kPT;
+    const float step = walk_step_of(ctx);
+    const int pt = (node_walk_on(ctx, p, step) || T32 < (long long)ctx->sm_count * 16) ? 16 : kPT;
     long long T = 0;
     for (int b = 0; b < p->B; ++b)
         T += (long long)p->n_spots * rings_per_spot(res, b) *
@@ -1307,14 +1353,9 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
         hE[k] = (float)e;
         hE3[k] = (float)(e * e * e);
         hinv[k] = (float)(1.0 / e);
-        hpk[k] = ctx->atm_ready ? (float)((std::log(e) - ctx->lnE0_t) / ctx->dlnE_t) : 0.0f;
+        hpk[k] = pk_of(ctx, std::min(k, nE - 1));
     }
-    int sliding = ctx->atm_ready ? 1 : 0;
-    if (sliding) {
-        for (int k = 0; k + 1 < nE; ++k)
-            if (!((double)hpk[k + 1] - hpk[k] < 0.999)) sliding = 0;
-        if (!((double)hpk[nE - 1] - hpk[0] < ctx->nEt - 3.5)) sliding = 0;
-    }
+    const int sliding = sliding_of(ctx);
 
     Params P;
     P.B = p->B; P.n_spots = p->n_spots; P.oblate = p->oblate; P.emission = p->emission;
@@ -1346,6 +1387,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     A.lnE0 = ctx->lnE0_t; A.dlnE = ctx->dlnE_t;
     EnergyDev en;
     en.nE = nE; en.nEpad = L.nEpad; en.sliding = sliding;
+    en.step = node_walk_on(ctx, p, step) ? step : 0.0f;
+    en.inv_step = en.step > 0.0f ? 1.0f / en.step : 0.0f;
     en.E = reinterpret_cast<const float *>(dev + L.o_E);
     en.E3 = reinterpret_cast<const float *>(dev + L.o_E3);
     en.pk = reinterpret_cast<const float *>(dev + L.o_pk);

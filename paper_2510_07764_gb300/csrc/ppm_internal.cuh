@@ -134,6 +134,8 @@ struct EnergyDev {
     const float *pk;     // [nEpad] (ln E - lnE0_table) / dlnE_table
     const float *invE;   // [nEpad] 1/E
     int sliding;         // consecutive pk differ by < 1 (one node shift per step)
+    float step;          // > 0: pk is uniform with this step (1/3 .. 1/2), node-major walk
+    float inv_step;      // 1 / step
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------

@@ -31,7 +31,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 struct Layout {
-    int tmpl, elems, slab, munodes, pk, E, E3, fblk, total;  // offsets in floats
+    int tmpl, elems, slab, munodes, pk, E, E3, fblk, ring, total;  // offsets in floats
 };
 
 __device__ __forceinline__ float contract4(const float *__restrict__ s, int off, float w0,
@@ -330,7 +330,262 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
 }
 #undef PPM_C
 
-template <int EMIS, int MODE>
+// ---------------------------------------------------------------------------
+// Node-major walk (energy grids uniform in ln E with a step d of 1/3 to 1/2
+// table node; en.step > 0).  Two elements per lane, packed in float2 (slot
+// 0: element g0 + lane, slot 1: g0 + lane + 32).  Each iteration moves every
+// slot one table interval up in ln E: it evaluates the interval's cubic at
+// the observed energies inside it (positions t and t + d always, t + 2d when
+// it is below 1), then contracts the next node and rebuilds the power-basis
+// coefficients.  Every slot does the same work in every iteration, so the
+// interval change is no longer a divergent branch.
+//
+// After i iterations a slot has passed ceil((i - f) / d) energies (f its
+// fractional start), so two slots differ by at most three energies.  Each
+// slot stores its values in its own column of a ring of 16 energy rows
+// (row = energy mod 16); once every slot of the warp has passed a block of
+// 8 energies the warp sums the block's rows (fixed order) into the phase
+// row.  A slot starts with up to two virtual energies below energy 0 in its
+// first interval and may run up to five past the last one: their rows are
+// rewritten by real energies before they are summed, or have been summed
+// already, or lie beyond nE.
+// ---------------------------------------------------------------------------
+constexpr int kRingRows = 16;
+constexpr int kRingBlock = 8;
+constexpr int kRingWarpBytes = kRingRows * 64 * 4;  // 64 columns of FP32 per row
+constexpr int kSlabMargin = 3;  // rows past the table read by slots past their last interval
+
+__device__ __forceinline__ void ring_put(unsigned kk, unsigned colbase, float v)
+{
+    // row (kk >> 8) & 15 of the ring; colbase has no bits in 0xF00
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"((kk & 0xF00u) | colbase), "f"(v));
+}
+
+// Power basis of the 4-point cubic on the interval between nodes n and n + 1
+// from half-scaled node values u_i = y_i / 2 of nodes n - 1 .. n + 2:
+// p(t) = c0 + t (k1 + t (k2 + t k3)), c0 = y_n = 2 u1, k2 = u0 + u2 - 2 u1,
+// k3 = (u3 - u0) / 3 + u1 - u2, k1 = u2 - u0 - k3 (the centred cubic
+// Lagrange interpolant on a uniform grid; no negated operands).
+__device__ __forceinline__ void cubic_half2(float2 u0, float2 u1, float2 u2, float2 u3,
+                                            float2 &c0, float2 &k1, float2 &k2, float2 &k3)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), m2 = make_float2(-2.0f, -2.0f);
+    const float2 p3 = make_float2(1.0f / 3.0f, 1.0f / 3.0f);
+    const float2 m3 = make_float2(-1.0f / 3.0f, -1.0f / 3.0f);
+    k2 = __ffma2_rn(u1, m2, __fadd2_rn(u0, u2));
+    k3 = __ffma2_rn(u3, p3, __ffma2_rn(u0, m3, __ffma2_rn(u2, m1, u1)));
+    k1 = __ffma2_rn(k3, m1, __ffma2_rn(u0, m1, u2));
+    c0 = __fadd2_rn(u1, u1);
+}
+
+template <bool CLIP>
+__device__ __forceinline__ float2 horner2(float2 t, float2 k0, float2 k1, float2 k2, float2 k3)
+{
+    float2 v = __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, k3, k2), k1), k0);
+    // strategy B: F_p >= 0, so clipping F_p I clips I
+    if (CLIP) v = make_float2(fmaxf(v.x, 0.0f), fmaxf(v.y, 0.0f));
+    return v;
+}
+
+// 16 bytes of the ring at a + OFF (OFF 0 or 2048: rows 0-7 or 8-15)
+template <unsigned OFF>
+__device__ __forceinline__ float4 ring_get4(unsigned a)
+{
+    float4 v;
+    if (OFF == 0)
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(a)
+                     : "memory");
+    else
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+2048];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "r"(a)
+                     : "memory");
+    return v;
+}
+
+template <int MODE>
+__device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, float phi_out,
+                                                const float *sel, const float *ph,
+                                                const float *mun, const float *slab, int Pm,
+                                                int n_fp, int top, const AtmDev &A,
+                                                float inv_dlnE, const float *spk, int nE,
+                                                int nch, float d, float inv_d, float pk0,
+                                                float pkl, float lz_safe, unsigned ring,
+                                                float *frow, unsigned *errp)
+{
+    constexpr bool ONESIDED = MODE != 0, CLIP = MODE == 2;
+    const float nEm2 = (float)(A.nE - 2);
+    float tv[2], wv[2][4], uv[2][4];
+    unsigned kkv[2];
+    int ofv[2], nit = 0;
+    bool slow[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = g0 + lane + 32 * e;
+        const PairW P = pair_weights<ONESIDED>(m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, ph,
+                                               mun, n_fp, top, A, inv_dlnE);
+        const bool fast = P.on && (pk0 + P.lz >= 1.0f) && (pkl + P.lz < nEm2);
+        slow[e] = P.on && !fast;
+        // slots outside the window run the walk with zero weights
+        const float lz = fast ? P.lz : lz_safe;
+        const float x0 = pk0 + lz;
+        const float n0 = floorf(x0);
+        const float f = x0 - n0;
+        // virtual energies -mv .. -1 put the walk's start t in [0, d)
+        int mv = (int)(f * inv_d);
+        float t = fmaf(-(float)mv, d, f);
+        if (t >= d) { t -= d; ++mv; }
+        if (t < 0.0f) { t += d; --mv; }
+        tv[e] = t;
+        kkv[e] = (unsigned)(-mv) << 8;
+        const int i0 = (int)n0;
+        nit = max(nit, (int)floorf(pkl + lz) - i0 + 1);
+        const int s0 = fast ? P.s0 : 0;
+        ofv[e] = (i0 + 2) * Pm + s0;
+        // half weights: the walk carries u = y / 2 (see cubic_half2)
+        wv[e][0] = fast ? 0.5f * P.w0 : 0.0f;
+        wv[e][1] = fast ? 0.5f * P.w1 : 0.0f;
+        wv[e][2] = fast ? 0.5f * P.w2 : 0.0f;
+        wv[e][3] = fast ? 0.5f * P.w3 : 0.0f;
+        PPM_CHECK(i0 >= 1 && i0 + 2 <= A.nE - 1 && s0 + 3 < A.nmu, errp);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            uv[e][q] = dot4(slab + (i0 - 1 + q) * Pm + s0, wv[e][0], wv[e][1], wv[e][2], wv[e][3]);
+    }
+    // one iteration more than the intervals of the last energy: the walk's
+    // positions are accumulated and may cross the last node slightly late
+    nit = __reduce_max_sync(kFull, nit) + 1;
+    const float2 W0 = make_float2(wv[0][0], wv[1][0]), W1 = make_float2(wv[0][1], wv[1][1]);
+    const float2 W2 = make_float2(wv[0][2], wv[1][2]), W3 = make_float2(wv[0][3], wv[1][3]);
+    float2 a = make_float2(uv[0][1], uv[1][1]);
+    float2 b = make_float2(uv[0][2], uv[1][2]);
+    float2 c = make_float2(uv[0][3], uv[1][3]);
+    float2 K0, K1, K2, K3;
+    cubic_half2(make_float2(uv[0][0], uv[1][0]), a, b, c, K0, K1, K2, K3);
+    float2 t = make_float2(tv[0], tv[1]);
+    const float2 d2 = make_float2(d, d), m1 = make_float2(-1.0f, -1.0f);
+    unsigned kk0 = kkv[0], kk1 = kkv[1];
+    int of0 = ofv[0], of1 = ofv[1];
+    const unsigned cb0 = ring + 4u * lane, cb1 = ring + 128u + 4u * lane;
+    // lane (row rr = lane >> 2, quarter q = lane & 3) of a block sum adds the
+    // float4 columns q + 4 ((i + rr) & 3), i = 0 .. 3 (no bank conflicts)
+    const int rr = lane >> 2, qq = lane & 3;
+    unsigned fa[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) fa[i] = ring + 256u * rr + 16u * (qq + 4 * ((i + rr) & 3));
+    int r0 = 0;                       // first energy of the ring block not yet summed
+    int lim = kRingBlock << 8;        // (r0 + 8) << 8
+
+    // sum energies r0 .. r0 + 7 (rows r0 & 15 ..) into the phase row
+    auto flush = [&]() {
+        __syncwarp();
+        float4 v[4];
+        if (r0 & 8) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = ring_get4<2048>(fa[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = ring_get4<0>(fa[i]);
+        }
+        float2 s01 = __fadd2_rn(__fadd2_rn(make_float2(v[0].x, v[0].y), make_float2(v[0].z, v[0].w)),
+                                __fadd2_rn(make_float2(v[1].x, v[1].y), make_float2(v[1].z, v[1].w)));
+        float2 s23 = __fadd2_rn(__fadd2_rn(make_float2(v[2].x, v[2].y), make_float2(v[2].z, v[2].w)),
+                                __fadd2_rn(make_float2(v[3].x, v[3].y), make_float2(v[3].z, v[3].w)));
+        s01 = __fadd2_rn(s01, s23);
+        float tot = s01.x + s01.y;
+        tot += __shfl_xor_sync(kFull, tot, 1);
+        tot += __shfl_xor_sync(kFull, tot, 2);
+        const int k = r0 + rr;
+        if (qq == 0 && k < nE) frow[k] += tot;
+        __syncwarp();
+        r0 += kRingBlock;
+        lim += kRingBlock << 8;
+    };
+
+    // one interval: A0, A1, A2 = half values of nodes n, n + 1, n + 2 and
+    // K0..K3 the interval's coefficients.  Leaves A0 = node n + 3 and K0..K3
+    // of interval n + 1, so the next call takes (A1, A2, A0).
+    auto interval = [&](float2 &A0, float2 &A1, float2 &A2) {
+        const float2 t2 = __fadd2_rn(t, d2);
+        const float2 t3 = __fadd2_rn(t2, d2);
+        const float2 v1 = horner2<CLIP>(t, K0, K1, K2, K3);
+        const float2 v2 = horner2<CLIP>(t2, K0, K1, K2, K3);
+        const float2 v3 = horner2<CLIP>(t3, K0, K1, K2, K3);
+        const bool th0 = t3.x < 1.0f, th1 = t3.y < 1.0f;
+        const unsigned k3a = kk0 + 512u, k3b = kk1 + 512u;
+        ring_put(kk0, cb0, v1.x);
+        ring_put(kk1, cb1, v1.y);
+        ring_put(kk0 + 256u, cb0, v2.x);
+        ring_put(kk1 + 256u, cb1, v2.y);
+        if (th0) ring_put(k3a, cb0, v3.x);
+        if (th1) ring_put(k3b, cb1, v3.y);
+        kk0 = th0 ? k3a + 256u : k3a;
+        kk1 = th1 ? k3b + 256u : k3b;
+        t = __fadd2_rn(t3, m1);
+        if (th0) t.x += d;
+        if (th1) t.y += d;
+        // node n + 3 (slots past their last interval read the margin rows;
+        // those values only reach virtual energies)
+        of0 += Pm;
+        of1 += Pm;
+        PPM_CHECK(of0 + 3 < (A.nE + kSlabMargin) * Pm && of1 + 3 < (A.nE + kSlabMargin) * Pm,
+                  errp);
+        const float *q0 = slab + of0, *q1 = slab + of1;
+        float2 y = __fmul2_rn(W0, make_float2(q0[0], q1[0]));
+        y = __ffma2_rn(W1, make_float2(q0[1], q1[1]), y);
+        y = __ffma2_rn(W2, make_float2(q0[2], q1[2]), y);
+        y = __ffma2_rn(W3, make_float2(q0[3], q1[3]), y);
+        cubic_half2(A0, A1, A2, y, K0, K1, K2, K3);
+        A0 = y;
+    };
+    auto passed = [&]() {
+        // kk may start "negative" (virtual energies): compare as signed
+        if (__all_sync(kFull, min((int)kk0, (int)kk1) >= lim)) flush();
+    };
+    for (int it = 0;;) {
+        interval(a, b, c);
+        passed();
+        if (++it >= nit) break;
+        interval(b, c, a);
+        passed();
+        if (++it >= nit) break;
+        interval(c, a, b);
+        passed();
+        if (++it >= nit) break;
+    }
+    while (r0 < nE) flush();
+
+    // elements whose window leaves the table interior: general evaluation
+    // per chunk of 16 energies, summed across the warp like the energy walk
+    if (__any_sync(kFull, slow[0] || slow[1])) {
+        for (int cc = 0; cc < nch; ++cc) {
+            float acc[kEC];
+#pragma unroll
+            for (int s = 0; s < kEC; ++s) acc[s] = 0.0f;
+            const float *pkc = spk + cc * kEC;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (slow[e]) {
+                    const int m = g0 + lane + 32 * e;
+                    const PairW P = pair_weights_slow<ONESIDED>(sel[m], phi_out, ph, mun, n_fp,
+                                                                top, A, inv_dlnE);
+#pragma unroll
+                    for (int k = 0; k < kEC; ++k) {
+                        const float v = eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz, ONESIDED);
+                        acc[k] += CLIP ? fmaxf(v, 0.0f) : v;
+                    }
+                }
+            }
+            const float tot = transpose_reduce16(acc, lane);
+            if (lane < kEC) frow[cc * kEC + lane] += tot;
+        }
+        __syncwarp();
+    }
+}
+
+template <int EMIS, int MODE, bool NODES>
 __global__ void __launch_bounds__(kSABlock, 2)
     k_shift_add(Params p, PlanDev plan, AtmDev A, EnergyDev en, Layout lay,
                 const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
@@ -339,6 +594,9 @@ __global__ void __launch_bounds__(kSABlock, 2)
 {
     extern __shared__ float sm[];
     __shared__ int s_next;
+    if (NODES)  // rows past the table that the node-major walk may read
+        for (int i = threadIdx.x; i < kSlabMargin * A.nmu_pad; i += blockDim.x)
+            sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
     // static schedule: block b runs item order[b]; persistent schedule
     // (plan.queue): blocks take the next entry of the order from a counter
     for (int slot = blockIdx.x;;) {
@@ -379,6 +637,11 @@ __global__ void __launch_bounds__(kSABlock, 2)
     const float inv_dlnE = (EMIS == 1) ? (float)(1.0 / A.dlnE) : 0.0f;
     const int Pm = A.nmu_pad;
     const bool inst_ok = status[it.b] == 0;
+    // this warp's ring (node-major walk): 4096-byte aligned shared address
+    unsigned ring_w = 0;
+    if (NODES)
+        ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
+                 (unsigned)(warp * kRingWarpBytes);
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;
@@ -447,7 +710,14 @@ __global__ void __launch_bounds__(kSABlock, 2)
 
         for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
             const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
-            if constexpr (EMIS == 1) {
+            if constexpr (EMIS == 1 && NODES) {
+                for (int g0 = 0; g0 < n_act; g0 += 64)
+                    atm_group_nodes<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp,
+                                          top, A, inv_dlnE, spk, en.nE, nch, en.step,
+                                          en.inv_step, pk0, pkl, lz_safe, ring_w,
+                                          Fblk + jl * nEpad, plan.err);
+                continue;
+            } else if constexpr (EMIS == 1) {
                 for (int g0 = 0; g0 < n_act;) {
                     if (n_act - g0 > 64) {
                         atm_group<2, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top,
@@ -813,6 +1083,15 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
 
 }  // namespace
 
+// the node-major walk applies (atmosphere emission, uniform energy step)
+static bool node_walk(const Params &p, const EnergyDev &en)
+{
+    return p.emission == 1 && en.sliding && en.step > 0.0f;
+}
+
+// rings of the block's warps plus the slack that aligns them to 4096 bytes
+static int ring_floats() { return (kSABlock / 32 * kRingWarpBytes + 4096) / 4; }
+
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max)
 {
@@ -822,11 +1101,12 @@ size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &
     take(4 * (plan.n_fp + 1));
     take(n_phi_max);
     take(p.emission == 1 ? A.nmu : 0);
-    take(p.emission == 1 ? A.nE * A.nmu_pad : 0);
+    take(p.emission == 1 ? (A.nE + (node_walk(p, en) ? kSlabMargin : 0)) * A.nmu_pad : 0);
     take(en.nEpad);
     take(en.nEpad);
     take(en.nEpad);
     take(plan.pt * en.nEpad);
+    take(node_walk(p, en) ? ring_floats() : 0);
     return (size_t)off * sizeof(float);
 }
 
@@ -865,11 +1145,13 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
     lay.tmpl = take(4 * (plan.n_fp + 1));
     lay.elems = take(n_phi_max);
     lay.munodes = take(p.emission == 1 ? A.nmu : 0);
-    lay.slab = take(p.emission == 1 ? A.nE * A.nmu_pad : 0);
+    const bool nodes = node_walk(p, en);
+    lay.slab = take(p.emission == 1 ? (A.nE + (nodes ? kSlabMargin : 0)) * A.nmu_pad : 0);
     lay.pk = take(en.nEpad);
     lay.E = take(en.nEpad);
     lay.E3 = take(en.nEpad);
     lay.fblk = take(plan.pt * en.nEpad);
+    lay.ring = take(nodes ? ring_floats() : 0);
     lay.total = off;
     const size_t bytes = (size_t)off * sizeof(float);
     cudaError_t e;
@@ -882,10 +1164,13 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
         return cudaSuccess;
     };
     (void)grid_blocks;
-    if (p.emission == 0) e = go(k_shift_add<0, 0>);
-    else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1>);
-    else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2>);
-    else e = go(k_shift_add<1, 0>);
+    if (p.emission == 0) e = go(k_shift_add<0, 0, false>);
+    else if (nodes && A.strategy == kInterpA) e = go(k_shift_add<1, 1, true>);
+    else if (nodes && A.strategy == kInterpB) e = go(k_shift_add<1, 2, true>);
+    else if (nodes) e = go(k_shift_add<1, 0, true>);
+    else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1, false>);
+    else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2, false>);
+    else e = go(k_shift_add<1, 0, false>);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

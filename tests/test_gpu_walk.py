@@ -1,0 +1,116 @@
+"""The node-major walk of the atmosphere shift-and-add (observed energies
+uniform in ln E with a step of 0.34-0.498 table nodes: every table interval
+holds two or three of them) against the FP64 oracle, and against the energy
+walk (ppm_tiles.walk = 1) on the same inputs: the two walks evaluate the
+same interpolants and sum them in a different order."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import context, max_rel
+
+pytestmark = pytest.mark.gpu
+
+TOL_ATM = 1e-3
+TOL_WALKS = 1e-4   # FP32 sums in another order, positions accumulated by the walk
+
+
+def _workload(synth, atm, small_lens, n_E, lo, hi, interp="d", **kw):
+    w = synth.atm_two_spot(n_theta=kw.get("n_theta", 14), n_phi=kw.get("n_phi", 40),
+                           n_phase=kw.get("n_phase", 24), n_E=n_E, n_chan=8, atm=atm,
+                           lens=small_lens)
+    w.E_keV = synth.logspace(lo, hi, n_E)
+    w.interp = interp
+    return w
+
+
+def _step(w, atm):
+    """Observed-energy step in table nodes."""
+    dln = (atm.lnE[-1] - atm.lnE[0]) / (len(atm.lnE) - 1)
+    return math.log(w.E_keV[-1] / w.E_keV[0]) / (len(w.E_keV) - 1) / dln
+
+
+def _both_walks(w):
+    import paper_2510_07764_gb300 as ppm
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    out = []
+    try:
+        for walk in (0, 1):
+            ctx.set_tiles(walk=walk)
+            Ft = ctx.profile(dp)
+            ctx.sync()
+            out.append(Ft.cpu().numpy().astype(np.float64))
+    finally:
+        ctx.set_tiles()
+    return out
+
+
+@pytest.mark.parametrize("interp", ["d", "a", "b", "c"])
+def test_node_walk_matches_oracle_and_energy_walk(orc, synth, atm, small_lens, interp):
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, interp)
+    assert 0.34 <= _step(w, atm) <= 0.498
+    node, energy = _both_walks(w)
+    assert not np.array_equal(node, energy)       # the node-major walk ran
+    assert max_rel(node, energy) < TOL_WALKS
+    assert max_rel(node, orc.profile(w)) < TOL_ATM
+
+
+@pytest.mark.parametrize("n_E,lo,hi", [
+    (159, 0.5, 6.0),     # step 0.49, near the upper bound
+    (230, 0.5, 6.6),     # step 0.349, near the lower bound: three energies per interval
+    (300, 0.1, 5.215),   # the crescent workload's grid, step 0.41
+])
+def test_node_walk_steps(orc, synth, atm, small_lens, n_E, lo, hi):
+    w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=16)
+    assert 0.34 <= _step(w, atm) <= 0.498
+    node, energy = _both_walks(w)
+    assert not np.array_equal(node, energy)
+    assert max_rel(node, energy) < TOL_WALKS
+    assert max_rel(node, orc.profile(w)) < TOL_ATM
+
+
+@pytest.mark.parametrize("lo,hi", [(0.052, 0.32), (3.5, 7.8)])
+def test_node_walk_with_table_edges(orc, synth, atm, small_lens, lo, hi):
+    """Redshifted energies leave the table interior at its low or high end:
+    elements of the same warp split between the walk and the general path."""
+    n_E = int(round(math.log(hi / lo) / (0.45 * 0.0321))) + 1
+    w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=20)
+    assert 0.34 <= _step(w, atm) <= 0.498
+    node, energy = _both_walks(w)
+    assert max_rel(node, energy) < TOL_WALKS
+    assert max_rel(node, orc.profile(w)) < TOL_ATM
+
+
+def test_walk_setting_is_inert_off_its_grids(synth, atm, small_lens):
+    """A step above 1/2 node (and a grid not uniform in ln E) keeps the energy
+    walk whatever the setting: both runs are bit-identical."""
+    w = _workload(synth, atm, small_lens, 64, 0.6, 2.6)
+    assert 0.5 < _step(w, atm) < 0.999
+    node, energy = _both_walks(w)
+    assert np.array_equal(node, energy)
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6)
+    w.E_keV = w.E_keV * (1.0 + 0.01 * np.sin(np.arange(96)))
+    node, energy = _both_walks(w)
+    assert np.array_equal(node, energy)
+
+
+def test_node_walk_persistent_schedule_is_bitwise_identical(synth, atm, small_lens):
+    import paper_2510_07764_gb300 as ppm
+    w = _workload(synth, atm, small_lens, 120, 0.4, 2.6, n_theta=20, n_phi=72, n_phase=40)
+    inst = w.inst.select(np.zeros(5, dtype=int))
+    inst.incl_rad[:] = np.linspace(0.3, 1.4, 5)
+    w.inst = inst
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    res = []
+    try:
+        for pers in (False, True):
+            ctx.set_tiles(16, 16, pers)
+            Ft = ctx.profile(dp)
+            ctx.sync()
+            res.append(Ft.cpu().numpy())
+    finally:
+        ctx.set_tiles()
+    assert np.array_equal(res[0], res[1])
