@@ -387,7 +387,9 @@ __device__ __forceinline__ float2 horner2(float2 t, float2 k0, float2 k1, float2
     return v;
 }
 
-// 16 bytes of the ring at a + OFF (OFF 0 or 2048: rows 0-7 or 8-15)
+// 16 bytes of the ring at a + OFF (OFF 0 or 2048: rows 0-7 or 8-15).  The
+// ring is only touched by these volatile loads and ring_put's volatile
+// stores, which keep their program order; __syncwarp orders the lanes.
 template <unsigned OFF>
 __device__ __forceinline__ float4 ring_get4(unsigned a)
 {
@@ -395,13 +397,11 @@ __device__ __forceinline__ float4 ring_get4(unsigned a)
     if (OFF == 0)
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "r"(a)
-                     : "memory");
+                     : "r"(a));
     else
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+2048];"
                      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "r"(a)
-                     : "memory");
+                     : "r"(a));
     return v;
 }
 
@@ -540,20 +540,42 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         cubic_half2(A0, A1, A2, y, K0, K1, K2, K3);
         A0 = y;
     };
+    // Checked every second interval: when a check finds the slowest slot
+    // below r0 + 8, the next two intervals write at most energy r0 + 15
+    // (slots differ by three, an interval adds three), inside the ring, and
+    // leave the slowest slot below r0 + 16, so one block sum per check keeps
+    // up.  kk may start "negative" (virtual energies): compare as signed.
     auto passed = [&]() {
-        // kk may start "negative" (virtual energies): compare as signed
         if (__all_sync(kFull, min((int)kk0, (int)kk1) >= lim)) flush();
     };
-    for (int it = 0;;) {
+    // six intervals per trip (the node roles rotate with period three), then
+    // the remainder
+    for (int n6 = nit / 6; n6 > 0; --n6) {
         interval(a, b, c);
-        passed();
-        if (++it >= nit) break;
         interval(b, c, a);
         passed();
-        if (++it >= nit) break;
+        interval(c, a, b);
+        interval(a, b, c);
+        passed();
+        interval(b, c, a);
         interval(c, a, b);
         passed();
-        if (++it >= nit) break;
+    }
+    const int rem = nit % 6;
+    if (rem > 0) {
+        interval(a, b, c);
+        if (rem > 1) {
+            interval(b, c, a);
+            passed();
+            if (rem > 2) {
+                interval(c, a, b);
+                if (rem > 3) {
+                    interval(a, b, c);
+                    passed();
+                    if (rem > 4) interval(b, c, a);
+                }
+            }
+        }
     }
     while (r0 < nE) flush();
 
