@@ -211,6 +211,23 @@ cudaError_t launch_grad_final(const Params &p, const PlanDev &plan, const double
                               const double *row_sums, int ktiles, const int *status,
                               const double *logL, double *grad, cudaStream_t st);
 
+// Power basis of the 4-point cubic on the interval between nodes n and n + 1
+// from half-scaled node values u_i = y_i / 2 of nodes n - 1 .. n + 2:
+// p(t) = c0 + t (k1 + t (k2 + t k3)), c0 = y_n = 2 u1, k2 = u0 + u2 - 2 u1,
+// k3 = (u3 - u0) / 3 + u1 - u2, k1 = u2 - u0 - k3 (the centred cubic
+// Lagrange interpolant on a uniform grid; no negated operands).
+__device__ __forceinline__ void cubic_half2(float2 u0, float2 u1, float2 u2, float2 u3,
+                                            float2 &c0, float2 &k1, float2 &k2, float2 &k3)
+{
+    const float2 m1 = make_float2(-1.0f, -1.0f), m2 = make_float2(-2.0f, -2.0f);
+    const float2 p3 = make_float2(1.0f / 3.0f, 1.0f / 3.0f);
+    const float2 m3 = make_float2(-1.0f / 3.0f, -1.0f / 3.0f);
+    k2 = __ffma2_rn(u1, m2, __fadd2_rn(u0, u2));
+    k3 = __ffma2_rn(u3, p3, __ffma2_rn(u0, m3, __ffma2_rn(u2, m1, u1)));
+    k1 = __ffma2_rn(k3, m1, __ffma2_rn(u0, m1, u2));
+    c0 = __fadd2_rn(u1, u1);
+}
+
 // row -> instance lookup (binary search over InstPlan.row0)
 __device__ __forceinline__ int find_instance_by_row(const InstPlan *ip, int B, int row)
 {

@@ -28,6 +28,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBwdBlock = 512;
+// node-major walk: zero adjoints before energy 0 and past the last energy,
+// and table rows past the slab that slots beyond their last interval read
+constexpr int kApadLead = 2, kApadTail = 16, kBwdMargin = 3;
+
+// floats of a warp's adjoint row: (position, adjoint) pairs, or the padded
+// adjoints of the node-major walk
+__host__ __device__ constexpr int arow_len(int nEpad) { return 2 * nEpad + kApadLead + kApadTail; }
 
 struct BLayout {
     int tmpl, elems, munodes, pk, E3, arow, adj, red, slab, slabT, slabG, total;
@@ -84,6 +91,11 @@ __device__ __forceinline__ void cubic2_shift(Cubic2 &C, float2 d)
 __device__ __forceinline__ float2 horner2(const Cubic2 &C, float2 t)
 {
     return __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, C.c3, C.c2), C.c1), C.c0);
+}
+
+__device__ __forceinline__ float2 horner2(float2 k0, float2 k1, float2 k2, float2 k3, float2 t)
+{
+    return __ffma2_rn(t, __ffma2_rn(t, __ffma2_rn(t, k3, k2), k1), k0);
 }
 
 // state of one (element, phase) pair in the backward pass
@@ -274,7 +286,7 @@ __device__ __noinline__ Quint bwd_general(const PairB &P, const float *S, const 
     return Q;
 }
 
-template <int EMIS, bool CLIP>
+template <int EMIS, bool CLIP, bool NODES>
 __global__ void __launch_bounds__(kBwdBlock, 1)
     k_shift_add_bwd(Params p, PlanDev plan, AtmDev A, EnergyDev en, BLayout lay,
                     const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
@@ -335,6 +347,12 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                 sm[lay.slabT + o] = vT;
                 sm[lay.slabG + o] = vG;
             }
+            if (NODES)
+                for (int i = tid; i < kBwdMargin * Pm; i += blockDim.x) {
+                    sm[lay.slab + A.nE * Pm + i] = 0.0f;
+                    sm[lay.slabT + A.nE * Pm + i] = 0.0f;
+                    sm[lay.slabG + A.nE * Pm + i] = 0.0f;
+                }
         }
     }
     __syncthreads();
@@ -356,8 +374,12 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
     const float *S = sm + lay.slab;
     const float *spk = sm + lay.pk;  // table positions (atmosphere) or energies (blackbody)
     const float *sE3 = sm + lay.E3;
-    float *arow = sm + lay.arow + warp * 2 * nEpad;  // (table position or energy, adjoint) pairs
+    // (table position or energy, adjoint) pairs; the node-major walk keeps the
+    // padded adjoints apad instead
+    float *arow = sm + lay.arow + warp * arow_len(nEpad);
+    float *apad = arow;
     const float2 *parow = reinterpret_cast<const float2 *>(arow);
+    const float d = en.step;
     const float pk0 = spk[0], pkl = spk[nE - 1];
     const float lz_safe = 1.25f - pk0;
     const bool sliding = en.sliding != 0;
@@ -372,9 +394,17 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
 
     for (int j = warp; j < n_q; j += kBwdBlock / 32) {
         const float *asrc = Aadj + (size_t)(ip.row0 + j / ip.n_sub) * nEpad;
-        for (int k = lane; k < nEpad; k += 32) {
-            arow[2 * k] = spk[k];
-            arow[2 * k + 1] = asrc[k] * inv_sub;
+        if (NODES) {
+            // apad[kApadLead + k] = A_k, zero outside 0 <= k < nE
+            for (int i = lane; i < nE + kApadLead + kApadTail; i += 32) {
+                const int k = i - kApadLead;
+                apad[i] = (k >= 0 && k < nE) ? asrc[k] * inv_sub : 0.0f;
+            }
+        } else {
+            for (int k = lane; k < nEpad; k += 32) {
+                arow[2 * k] = spk[k];
+                arow[2 * k + 1] = asrc[k] * inv_sub;
+            }
         }
         __syncwarp();
         const float phi_out = ((float)j - q_half) * inv_nphase;
@@ -389,7 +419,118 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                                   (pkl + P.lz < (float)(A.nE - 2));
                 const bool anyslow = __any_sync(kFull, P.on && !fast);
                 float sF = 0.f, sZ = 0.f, sMu = 0.f, sT = 0.f, sG = 0.f;
-                if (sliding && !anyslow) {
+                if (sliding && !anyslow && NODES) {
+                    // node-major walk (energy grid uniform in ln E, step d of
+                    // 0.34-0.498 node): every lane moves one table interval per
+                    // iteration and evaluates the two or three energies in it;
+                    // the adjoints of virtual energies (before 0, past nE - 1)
+                    // are the zeros padding apad.  Nodes are half-scaled (see
+                    // cubic_half2): (I, I_mu) and (I_T, I_g) as packed pairs.
+                    const float lz = fast ? P.lz : lz_safe;
+                    const float hw0 = fast ? 0.5f * P.w0 : 0.f, hw1 = fast ? 0.5f * P.w1 : 0.f;
+                    const float hw2 = fast ? 0.5f * P.w2 : 0.f, hw3 = fast ? 0.5f * P.w3 : 0.f;
+                    const float hv0 = fast ? 0.5f * P.v0 : 0.f, hv1 = fast ? 0.5f * P.v1 : 0.f;
+                    const float hv2 = fast ? 0.5f * P.v2 : 0.f, hv3 = fast ? 0.5f * P.v3 : 0.f;
+                    const float2 WI0 = make_float2(hw0, hv0), WI1 = make_float2(hw1, hv1);
+                    const float2 WI2 = make_float2(hw2, hv2), WI3 = make_float2(hw3, hv3);
+                    const float2 WT0 = make_float2(hw0, hw0), WT1 = make_float2(hw1, hw1);
+                    const float2 WT2 = make_float2(hw2, hw2), WT3 = make_float2(hw3, hw3);
+                    const float x0 = pk0 + lz;
+                    const float n0 = floorf(x0);
+                    const float f = x0 - n0;
+                    int mv = (int)(f * en.inv_step);
+                    float t = fmaf(-(float)mv, d, f);
+                    if (t >= d) { t -= d; ++mv; }
+                    if (t < 0.0f) { t += d; --mv; }
+                    int kidx = kApadLead - mv;  // apad index of the energy at t
+                    const int i0 = (int)n0;
+                    const int s0 = fast ? P.s0 : 0;
+                    const float *sp = S + (i0 + 2) * Pm + s0;
+                    PPM_CHECK(i0 >= 1 && i0 + 2 <= A.nE - 1 && s0 + 3 < A.nmu, plan.err);
+                    auto nodeIM = [&](const float *r) {
+                        float2 y = __fmul2_rn(WI0, make_float2(r[0], r[0]));
+                        y = __ffma2_rn(WI1, make_float2(r[1], r[1]), y);
+                        y = __ffma2_rn(WI2, make_float2(r[2], r[2]), y);
+                        return __ffma2_rn(WI3, make_float2(r[3], r[3]), y);
+                    };
+                    auto nodeTG = [&](const float *r) {
+                        const float *rt = r + offT, *rg = r + offG;
+                        float2 y = __fmul2_rn(WT0, make_float2(rt[0], rg[0]));
+                        y = __ffma2_rn(WT1, make_float2(rt[1], rg[1]), y);
+                        y = __ffma2_rn(WT2, make_float2(rt[2], rg[2]), y);
+                        return __ffma2_rn(WT3, make_float2(rt[3], rg[3]), y);
+                    };
+                    float2 ia = nodeIM(sp - 2 * Pm), ib = nodeIM(sp - Pm), ic = nodeIM(sp);
+                    float2 ga = nodeTG(sp - 2 * Pm), gb = nodeTG(sp - Pm), gc = nodeTG(sp);
+                    float2 I0, I1, I2, I3, G0, G1, G2, G3;
+                    cubic_half2(nodeIM(sp - 3 * Pm), ia, ib, ic, I0, I1, I2, I3);
+                    cubic_half2(nodeTG(sp - 3 * Pm), ga, gb, gc, G0, G1, G2, G3);
+                    int nit = __reduce_max_sync(kFull, (int)floorf(pkl + lz) - i0 + 1) + 1;
+                    float2 sFM = make_float2(0.f, 0.f), sTG = make_float2(0.f, 0.f);
+                    float sZa = 0.f;
+                    // one energy at position te with adjoint ae
+                    auto eval = [&](float te, float ae) {
+                        const float2 tt = make_float2(te, te);
+                        const float2 vIM = horner2(I0, I1, I2, I3, tt);
+                        const float2 vTG = horner2(G0, G1, G2, G3, tt);
+                        // strategy B: max(I, 0) passes no derivative where I <= 0
+                        const float a1 = CLIP ? (vIM.x > 0.0f ? ae : 0.0f) : ae;
+                        const float2 ak = make_float2(a1, a1);
+                        sFM = __ffma2_rn(ak, vIM, sFM);
+                        sTG = __ffma2_rn(ak, vTG, sTG);
+                        const float dIdt =
+                            fmaf(te, fmaf(te, 3.0f * I3.x, 2.0f * I2.x), I1.x);
+                        sZa = fmaf(a1, dIdt, sZa);
+                    };
+                    // one interval with half nodes (xa, xb, xc) = n, n+1, n+2 of
+                    // both pairs; leaves xa = node n + 3 and the next coefficients
+                    auto interval = [&](float2 &ja, float2 &jb, float2 &jc, float2 &ka,
+                                        float2 &kb, float2 &kc) {
+                        const float t2 = t + d, t3 = t2 + d;
+                        const float a1 = apad[kidx], a2 = apad[kidx + 1], a3r = apad[kidx + 2];
+                        const bool th = t3 < 1.0f;
+                        eval(t, a1);
+                        eval(t2, a2);
+                        eval(t3, th ? a3r : 0.0f);
+                        kidx += th ? 3 : 2;
+                        t = (th ? t3 + d : t3) - 1.0f;
+                        // node n + 3 (past the last interval: margin rows, zero adjoints)
+                        sp += Pm;
+                        PPM_CHECK(sp + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
+                        const float2 yI = nodeIM(sp), yG = nodeTG(sp);
+                        cubic_half2(ja, jb, jc, yI, I0, I1, I2, I3);
+                        cubic_half2(ka, kb, kc, yG, G0, G1, G2, G3);
+                        ja = yI;
+                        ka = yG;
+                    };
+                    for (int n6 = nit / 6; n6 > 0; --n6) {
+                        interval(ia, ib, ic, ga, gb, gc);
+                        interval(ib, ic, ia, gb, gc, ga);
+                        interval(ic, ia, ib, gc, ga, gb);
+                        interval(ia, ib, ic, ga, gb, gc);
+                        interval(ib, ic, ia, gb, gc, ga);
+                        interval(ic, ia, ib, gc, ga, gb);
+                    }
+                    const int rem = nit % 6;
+                    if (rem > 0) {
+                        interval(ia, ib, ic, ga, gb, gc);
+                        if (rem > 1) {
+                            interval(ib, ic, ia, gb, gc, ga);
+                            if (rem > 2) {
+                                interval(ic, ia, ib, gc, ga, gb);
+                                if (rem > 3) {
+                                    interval(ia, ib, ic, ga, gb, gc);
+                                    if (rem > 4) interval(ib, ic, ia, gb, gc, ga);
+                                }
+                            }
+                        }
+                    }
+                    sF = sFM.x;
+                    sMu = sFM.y;
+                    sT = sTG.x;
+                    sG = sTG.y;
+                    sZ = sZa;
+                } else if (sliding && !anyslow) {
                     // lanes without a pair run the window with zero weights
                     const float lz = fast ? P.lz : lz_safe;
                     const float a0 = fast ? P.w0 : 0.f, a1 = fast ? P.w1 : 0.f;
@@ -446,7 +587,9 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                     for (int k = 0; k < nE; ++k) {
                         const Quint Q = bwd_general(P, S, S + offT, S + offG, Pm, A.nE,
                                                     spk[k] + P.lz, onesided);
-                        const float ak = CLIP ? (Q.I > 0.0f ? parow[k].y : 0.0f) : parow[k].y;
+                        // the adjoint row holds padded adjoints in the node-major kernel
+                        const float ar = NODES ? apad[kApadLead + k] : parow[k].y;
+                        const float ak = CLIP ? (Q.I > 0.0f ? ar : 0.0f) : ar;
                         sF = fmaf(ak, Q.I, sF);
                         sZ = fmaf(ak, Q.dI, sZ);
                         sMu = fmaf(ak, Q.Im, sMu);
@@ -573,13 +716,13 @@ BwdSizes bwd_layout(int emission, const PlanDev &plan, const AtmDev &A, const En
     BLayout &lay = z.lay;
     int off = 0;
     auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
-    const int slab = emission == 1 ? A.nE * A.nmu_pad : 0;
+    const int slab = emission == 1 ? (A.nE + (en.step > 0.0f ? kBwdMargin : 0)) * A.nmu_pad : 0;
     lay.tmpl = take(4 * (plan.n_fp + 1));
     lay.elems = take(n_phi_max);
     lay.munodes = take(emission == 1 ? A.nmu : 0);
     lay.pk = take(en.nEpad);
     lay.E3 = take(emission == 1 ? 0 : en.nEpad);
-    lay.arow = take((kBwdBlock / 32) * 2 * en.nEpad);
+    lay.arow = take((kBwdBlock / 32) * arow_len(en.nEpad));
     lay.adj = take((det ? kBwdBlock / 32 : 1) * 4 * (plan.n_fp + 1));
     lay.red = take(4 * (kBwdBlock / 32));
     lay.slab = take(slab);
@@ -610,25 +753,23 @@ cudaError_t launch_shift_add_bwd(const Params &p, const PlanDev &plan, const Atm
     BwdSizes z = bwd_layout(p.emission, plan, A, en, n_phi_max, true);
     if (z.bytes > smem_limit) z = bwd_layout(p.emission, plan, A, en, n_phi_max, false);
     cudaError_t e;
-    if (p.emission == 1 && A.strategy == kInterpB) {
-        e = cudaFuncSetAttribute(k_shift_add_bwd<1, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
-        if (e != cudaSuccess) return e;
-        k_shift_add_bwd<1, true><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
-            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
-    } else if (p.emission == 1) {
-        e = cudaFuncSetAttribute(k_shift_add_bwd<1, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
-        if (e != cudaSuccess) return e;
-        k_shift_add_bwd<1, false><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
-            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
-    } else {
-        e = cudaFuncSetAttribute(k_shift_add_bwd<0, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)z.bytes);
-        if (e != cudaSuccess) return e;
-        k_shift_add_bwd<0, false><<<plan.total_rings, kBwdBlock, z.bytes, st>>>(
-            p, plan, A, en, z.lay, recs, tmpl, elems, status, Aadj, ringadj);
-    }
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)z.bytes);
+        if (r != cudaSuccess) return r;
+        kern<<<plan.total_rings, kBwdBlock, z.bytes, st>>>(p, plan, A, en, z.lay, recs, tmpl,
+                                                           elems, status, Aadj, ringadj);
+        return cudaSuccess;
+    };
+    // node-major walk on uniform energy grids (as the forward)
+    const bool nodes = p.emission == 1 && en.sliding && en.step > 0.0f;
+    const bool clip = A.strategy == kInterpB;
+    if (p.emission == 0) e = go(k_shift_add_bwd<0, false, false>);
+    else if (nodes && clip) e = go(k_shift_add_bwd<1, true, true>);
+    else if (nodes) e = go(k_shift_add_bwd<1, false, true>);
+    else if (clip) e = go(k_shift_add_bwd<1, true, false>);
+    else e = go(k_shift_add_bwd<1, false, false>);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
