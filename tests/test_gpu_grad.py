@@ -47,6 +47,16 @@ def visible_two_cap(synth, atm, lens, **kw):
     return w
 
 
+def counts_from_model(orc, w, seed=7):
+    """Poisson counts drawn from the oracle's model of w on its own energy
+    grid and response (bins without model flux get no counts, so logL stays
+    finite where a generic count map would meet a zero or underflowing
+    model)."""
+    C = orc.counts_model(orc.profile(w), w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
+    rng = np.random.default_rng(seed)
+    return rng.poisson(np.maximum(w.tau * C, 0.0)).astype(np.int32)
+
+
 def _check(g, ref, mask=None):
     assert np.isfinite(g).all() and np.isfinite(ref).all(), (g, ref)
     tol = grad_tol(ref)
@@ -190,12 +200,10 @@ def test_grad_energies_past_the_table_edges(orc, synth, atm, small_lens, strateg
     w.R = synth.response(w.E_keV, 20)
     w.sigma_ism = synth.sigma_ism(w.E_keV)
     w.interp = strategy
-    # counts drawn from this grid's own model: the workload's generic count
-    # map puts counts near 9.5 keV, where the model flux (~e^-80) underflows
-    # FP32 and logL would be -inf on the GPU (finite only in FP64)
-    C = orc.counts_model(orc.profile(w), w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
-    rng = np.random.default_rng(7)
-    w.counts = rng.poisson(np.maximum(w.tau * C, 0.0)).astype(np.int32)
+    # the workload's generic count map puts counts near 9.5 keV, where the
+    # model flux (~e^-80) underflows FP32 (logL -inf on the GPU, finite only
+    # in FP64)
+    w.counts = counts_from_model(orc, w)
     ll, g, st = gpu_grad(w)
     assert st[0] == 0
     _check(g[0, :13], orc.grad_tangent(w))
