@@ -460,70 +460,127 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                         y = __ffma2_rn(WT2, make_float2(rt[2], rg[2]), y);
                         return __ffma2_rn(WT3, make_float2(rt[3], rg[3]), y);
                     };
-                    float2 ia = nodeIM(sp - 2 * Pm), ib = nodeIM(sp - Pm), ic = nodeIM(sp);
-                    float2 ga = nodeTG(sp - 2 * Pm), gb = nodeTG(sp - Pm), gc = nodeTG(sp);
-                    float2 I0, I1, I2, I3, G0, G1, G2, G3;
-                    cubic_half2(nodeIM(sp - 3 * Pm), ia, ib, ic, I0, I1, I2, I3);
-                    cubic_half2(nodeTG(sp - 3 * Pm), ga, gb, gc, G0, G1, G2, G3);
                     int nit = __reduce_max_sync(kFull, (int)floorf(pkl + lz) - i0 + 1) + 1;
                     float2 sFM = make_float2(0.f, 0.f), sTG = make_float2(0.f, 0.f);
                     float sZa = 0.f;
-                    // one energy at position te with adjoint ae
-                    auto eval = [&](float te, float ae) {
-                        const float2 tt = make_float2(te, te);
-                        const float2 vIM = horner2(I0, I1, I2, I3, tt);
-                        const float2 vTG = horner2(G0, G1, G2, G3, tt);
-                        // strategy B: max(I, 0) passes no derivative where I <= 0
-                        const float a1 = CLIP ? (vIM.x > 0.0f ? ae : 0.0f) : ae;
-                        const float2 ak = make_float2(a1, a1);
-                        sFM = __ffma2_rn(ak, vIM, sFM);
-                        sTG = __ffma2_rn(ak, vTG, sTG);
-                        const float dIdt =
-                            fmaf(te, fmaf(te, 3.0f * I3.x, 2.0f * I2.x), I1.x);
-                        sZa = fmaf(a1, dIdt, sZa);
-                    };
-                    // one interval with half nodes (xa, xb, xc) = n, n+1, n+2 of
-                    // both pairs; leaves xa = node n + 3 and the next coefficients
-                    auto interval = [&](float2 &ja, float2 &jb, float2 &jc, float2 &ka,
-                                        float2 &kb, float2 &kc) {
-                        const float t2 = t + d, t3 = t2 + d;
-                        const float a1 = apad[kidx], a2 = apad[kidx + 1], a3r = apad[kidx + 2];
-                        const bool th = t3 < 1.0f;
-                        eval(t, a1);
-                        eval(t2, a2);
-                        eval(t3, th ? a3r : 0.0f);
-                        kidx += th ? 3 : 2;
-                        t = (th ? t3 + d : t3) - 1.0f;
-                        // node n + 3 (past the last interval: margin rows, zero adjoints)
-                        sp += Pm;
-                        PPM_CHECK(sp + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
-                        const float2 yI = nodeIM(sp), yG = nodeTG(sp);
-                        cubic_half2(ja, jb, jc, yI, I0, I1, I2, I3);
-                        cubic_half2(ka, kb, kc, yG, G0, G1, G2, G3);
-                        ja = yI;
-                        ka = yG;
-                    };
-                    for (int n6 = nit / 6; n6 > 0; --n6) {
-                        interval(ia, ib, ic, ga, gb, gc);
-                        interval(ib, ic, ia, gb, gc, ga);
-                        interval(ic, ia, ib, gc, ga, gb);
-                        interval(ia, ib, ic, ga, gb, gc);
-                        interval(ib, ic, ia, gb, gc, ga);
-                        interval(ic, ia, ib, gc, ga, gb);
-                    }
-                    const int rem = nit % 6;
-                    if (rem > 0) {
-                        interval(ia, ib, ic, ga, gb, gc);
-                        if (rem > 1) {
+                    if constexpr (CLIP) {
+                        // strategy B: the clip decision needs each energy's
+                        // intensity, so the interval cubics are evaluated
+                        float2 ia = nodeIM(sp - 2 * Pm), ib = nodeIM(sp - Pm), ic = nodeIM(sp);
+                        float2 ga = nodeTG(sp - 2 * Pm), gb = nodeTG(sp - Pm), gc = nodeTG(sp);
+                        float2 I0, I1, I2, I3, G0, G1, G2, G3;
+                        cubic_half2(nodeIM(sp - 3 * Pm), ia, ib, ic, I0, I1, I2, I3);
+                        cubic_half2(nodeTG(sp - 3 * Pm), ga, gb, gc, G0, G1, G2, G3);
+                        // one energy at position te with adjoint ae
+                        auto eval = [&](float te, float ae) {
+                            const float2 tt = make_float2(te, te);
+                            const float2 vIM = horner2(I0, I1, I2, I3, tt);
+                            const float2 vTG = horner2(G0, G1, G2, G3, tt);
+                            // max(I, 0) passes no derivative where I <= 0
+                            const float a1 = vIM.x > 0.0f ? ae : 0.0f;
+                            const float2 ak = make_float2(a1, a1);
+                            sFM = __ffma2_rn(ak, vIM, sFM);
+                            sTG = __ffma2_rn(ak, vTG, sTG);
+                            const float dIdt =
+                                fmaf(te, fmaf(te, 3.0f * I3.x, 2.0f * I2.x), I1.x);
+                            sZa = fmaf(a1, dIdt, sZa);
+                        };
+                        // one interval with half nodes (xa, xb, xc) = n, n+1, n+2 of
+                        // both pairs; leaves xa = node n + 3 and the next coefficients
+                        auto interval = [&](float2 &ja, float2 &jb, float2 &jc, float2 &ka,
+                                            float2 &kb, float2 &kc) {
+                            const float t2 = t + d, t3 = t2 + d;
+                            const float a1 = apad[kidx], a2 = apad[kidx + 1],
+                                        a3r = apad[kidx + 2];
+                            const bool th = t3 < 1.0f;
+                            eval(t, a1);
+                            eval(t2, a2);
+                            eval(t3, th ? a3r : 0.0f);
+                            kidx += th ? 3 : 2;
+                            t = (th ? t3 + d : t3) - 1.0f;
+                            // node n + 3 (past the last interval: margin rows, zero adjoints)
+                            sp += Pm;
+                            PPM_CHECK(sp + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
+                            const float2 yI = nodeIM(sp), yG = nodeTG(sp);
+                            cubic_half2(ja, jb, jc, yI, I0, I1, I2, I3);
+                            cubic_half2(ka, kb, kc, yG, G0, G1, G2, G3);
+                            ja = yI;
+                            ka = yG;
+                        };
+                        for (int n3 = nit / 3; n3 > 0; --n3) {
+                            interval(ia, ib, ic, ga, gb, gc);
                             interval(ib, ic, ia, gb, gc, ga);
-                            if (rem > 2) {
-                                interval(ic, ia, ib, gc, ga, gb);
-                                if (rem > 3) {
-                                    interval(ia, ib, ic, ga, gb, gc);
-                                    if (rem > 4) interval(ib, ic, ia, gb, gc, ga);
-                                }
-                            }
+                            interval(ic, ia, ib, gc, ga, gb);
                         }
+                        const int rem = nit % 3;
+                        if (rem > 0) interval(ia, ib, ic, ga, gb, gc);
+                        if (rem > 1) interval(ib, ic, ia, gb, gc, ga);
+                    } else {
+                        // No cubic is formed: the sums over an interval's energies,
+                        //   sum_k a_k p(t_k) and sum_k a_k p'(t_k),
+                        // are linear in the interval's four node values, with
+                        // weights from the adjoint-weighted moments
+                        // m_j = sum_k a_k t_k^j (j = 0..3) through the constant
+                        // map from the 4-point cubic's nodes to its power basis
+                        // (c0 = y1, c1 = -y0/3 - y1/2 + y2 - y3/6,
+                        // c2 = y0/2 - y1 + y2/2, c3 = (y3 - y0)/6 + (y1 - y2)/2).
+                        // The weights below act on half-scaled nodes u = y / 2 and
+                        // serve all four cubics of the two packed pairs.
+                        float2 qa = nodeIM(sp - 3 * Pm), qb = nodeIM(sp - 2 * Pm);
+                        float2 qc = nodeIM(sp - Pm), qd = nodeIM(sp);
+                        float2 ra = nodeTG(sp - 3 * Pm), rb = nodeTG(sp - 2 * Pm);
+                        float2 rc = nodeTG(sp - Pm), rd = nodeTG(sp);
+                        // interval with half nodes (Q0..Q3, R0..R3) = n - 1 .. n + 2;
+                        // leaves Q0, R0 = node n + 3
+                        auto interval = [&](float2 &Q0, float2 &Q1, float2 &Q2, float2 &Q3,
+                                            float2 &R0, float2 &R1, float2 &R2, float2 &R3) {
+                            const float t2 = t + d, t3 = t2 + d;
+                            const float a1 = apad[kidx], a2 = apad[kidx + 1],
+                                        a3r = apad[kidx + 2];
+                            const bool th = t3 < 1.0f;
+                            const float a3 = th ? a3r : 0.0f;
+                            const float b1 = a1 * (t * t), b2 = a2 * (t2 * t2), b3 = a3 * (t3 * t3);
+                            const float m0 = a1 + a2 + a3;
+                            const float m1 = fmaf(a1, t, fmaf(a2, t2, a3 * t3));
+                            const float m2 = b1 + b2 + b3;
+                            const float m3 = fmaf(b1, t, fmaf(b2, t2, b3 * t3));
+                            // sum_k a_k p(t_k) = sum_i W_i u_i
+                            const float W0 = fmaf(m1, -2.0f / 3.0f, fmaf(m3, -1.0f / 3.0f, m2));
+                            const float W1 = fmaf(m0 - m2, 2.0f, m3 - m1);
+                            const float W2 = fmaf(m1, 2.0f, m2 - m3);
+                            const float W3 = (m3 - m1) * (1.0f / 3.0f);
+                            // sum_k a_k p'(t_k) = sum_i D_i u_i (the intensity only)
+                            const float D0 = fmaf(m0, -2.0f / 3.0f, fmaf(m1, 2.0f, -m2));
+                            const float D1 = fmaf(m2, 3.0f, fmaf(m1, -4.0f, -m0));
+                            const float D2 = fmaf(m0 + m1, 2.0f, -3.0f * m2);
+                            const float D3 = fmaf(m0, -1.0f / 3.0f, m2);
+                            sFM = __ffma2_rn(Q0, make_float2(W0, W0), sFM);
+                            sFM = __ffma2_rn(Q1, make_float2(W1, W1), sFM);
+                            sFM = __ffma2_rn(Q2, make_float2(W2, W2), sFM);
+                            sFM = __ffma2_rn(Q3, make_float2(W3, W3), sFM);
+                            sTG = __ffma2_rn(R0, make_float2(W0, W0), sTG);
+                            sTG = __ffma2_rn(R1, make_float2(W1, W1), sTG);
+                            sTG = __ffma2_rn(R2, make_float2(W2, W2), sTG);
+                            sTG = __ffma2_rn(R3, make_float2(W3, W3), sTG);
+                            sZa = fmaf(D0, Q0.x, fmaf(D1, Q1.x, fmaf(D2, Q2.x, fmaf(D3, Q3.x, sZa))));
+                            kidx += th ? 3 : 2;
+                            t = (th ? t3 + d : t3) - 1.0f;
+                            // node n + 3 (past the last interval: margin rows, zero adjoints)
+                            sp += Pm;
+                            PPM_CHECK(sp + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
+                            Q0 = nodeIM(sp);
+                            R0 = nodeTG(sp);
+                        };
+                        for (int n4 = nit / 4; n4 > 0; --n4) {
+                            interval(qa, qb, qc, qd, ra, rb, rc, rd);
+                            interval(qb, qc, qd, qa, rb, rc, rd, ra);
+                            interval(qc, qd, qa, qb, rc, rd, ra, rb);
+                            interval(qd, qa, qb, qc, rd, ra, rb, rc);
+                        }
+                        const int rem = nit % 4;
+                        if (rem > 0) interval(qa, qb, qc, qd, ra, rb, rc, rd);
+                        if (rem > 1) interval(qb, qc, qd, qa, rb, rc, rd, ra);
+                        if (rem > 2) interval(qc, qd, qa, qb, rc, rd, ra, rb);
                     }
                     sF = sFM.x;
                     sMu = sFM.y;
