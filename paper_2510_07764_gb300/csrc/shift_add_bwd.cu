@@ -516,24 +516,41 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                         if (rem > 0) interval(ia, ib, ic, ga, gb, gc);
                         if (rem > 1) interval(ib, ic, ia, gb, gc, ga);
                     } else {
-                        // No cubic is formed: the sums over an interval's energies,
+                        // No cubic is formed.  The sums over an interval's energies,
                         //   sum_k a_k p(t_k) and sum_k a_k p'(t_k),
-                        // are linear in the interval's four node values, with
-                        // weights from the adjoint-weighted moments
-                        // m_j = sum_k a_k t_k^j (j = 0..3) through the constant
-                        // map from the 4-point cubic's nodes to its power basis
+                        // are linear in the interval's four node values y_{n-1..n+2},
+                        // with weights from the adjoint-weighted moments
+                        // m_j = sum_k a_k t_k^j (j = 0..3) through the constant map
+                        // from the 4-point cubic's nodes to its power basis
                         // (c0 = y1, c1 = -y0/3 - y1/2 + y2 - y3/6,
-                        // c2 = y0/2 - y1 + y2/2, c3 = (y3 - y0)/6 + (y1 - y2)/2).
-                        // The weights below act on half-scaled nodes u = y / 2 and
-                        // serve all four cubics of the two packed pairs.
-                        float2 qa = nodeIM(sp - 3 * Pm), qb = nodeIM(sp - 2 * Pm);
-                        float2 qc = nodeIM(sp - Pm), qd = nodeIM(sp);
-                        float2 ra = nodeTG(sp - 3 * Pm), rb = nodeTG(sp - 2 * Pm);
-                        float2 rc = nodeTG(sp - Pm), rd = nodeTG(sp);
-                        // interval with half nodes (Q0..Q3, R0..R3) = n - 1 .. n + 2;
-                        // leaves Q0, R0 = node n + 3
-                        auto interval = [&](float2 &Q0, float2 &Q1, float2 &Q2, float2 &Q3,
-                                            float2 &R0, float2 &R1, float2 &R2, float2 &R3) {
+                        // c2 = y0/2 - y1 + y2/2, c3 = (y3 - y0)/6 + (y1 - y2)/2);
+                        // W and D below are twice those weights.  A node's weights
+                        // are summed over the four intervals that use it; when it
+                        // leaves the window its total weights multiply its raw
+                        // slab rows (all four mu rows of the stencil), and the
+                        // element's mu weights contract the accumulated rows once
+                        // at the end: the intensity and its mu derivative share
+                        // the accumulation.
+                        float2 P0 = make_float2(0.f, 0.f), P1 = P0, P2 = P0, P3 = P0;
+                        float2 V0 = P0, V1 = P0, V2 = P0, V3 = P0;  // (sum W S, sum D S) per mu row
+                        float2 U0 = P0, U1 = P0, U2 = P0, U3 = P0;  // (sum W S_T, sum W S_G)
+                        const float *sq = sp - 3 * Pm;              // row of node n - 1
+                        // node with total weights X = (W, D) at row r leaves the window
+                        auto retire = [&](const float *r, float2 X) {
+                            const float *rt = r + offT, *rg = r + offG;
+                            const float2 XW = make_float2(X.x, X.x);
+                            V0 = __ffma2_rn(X, make_float2(r[0], r[0]), V0);
+                            V1 = __ffma2_rn(X, make_float2(r[1], r[1]), V1);
+                            V2 = __ffma2_rn(X, make_float2(r[2], r[2]), V2);
+                            V3 = __ffma2_rn(X, make_float2(r[3], r[3]), V3);
+                            U0 = __ffma2_rn(XW, make_float2(rt[0], rg[0]), U0);
+                            U1 = __ffma2_rn(XW, make_float2(rt[1], rg[1]), U1);
+                            U2 = __ffma2_rn(XW, make_float2(rt[2], rg[2]), U2);
+                            U3 = __ffma2_rn(XW, make_float2(rt[3], rg[3]), U3);
+                        };
+                        // interval n: partial weights (X0..X3) of nodes n - 1 .. n + 2;
+                        // node n - 1 retires and X0 restarts as node n + 3
+                        auto interval = [&](float2 &X0, float2 &X1, float2 &X2, float2 &X3) {
                             const float t2 = t + d, t3 = t2 + d;
                             const float a1 = apad[kidx], a2 = apad[kidx + 1],
                                         a3r = apad[kidx + 2];
@@ -544,43 +561,55 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                             const float m1 = fmaf(a1, t, fmaf(a2, t2, a3 * t3));
                             const float m2 = b1 + b2 + b3;
                             const float m3 = fmaf(b1, t, fmaf(b2, t2, b3 * t3));
-                            // sum_k a_k p(t_k) = sum_i W_i u_i
-                            const float W0 = fmaf(m1, -2.0f / 3.0f, fmaf(m3, -1.0f / 3.0f, m2));
-                            const float W1 = fmaf(m0 - m2, 2.0f, m3 - m1);
-                            const float W2 = fmaf(m1, 2.0f, m2 - m3);
-                            const float W3 = (m3 - m1) * (1.0f / 3.0f);
-                            // sum_k a_k p'(t_k) = sum_i D_i u_i (the intensity only)
-                            const float D0 = fmaf(m0, -2.0f / 3.0f, fmaf(m1, 2.0f, -m2));
-                            const float D1 = fmaf(m2, 3.0f, fmaf(m1, -4.0f, -m0));
-                            const float D2 = fmaf(m0 + m1, 2.0f, -3.0f * m2);
-                            const float D3 = fmaf(m0, -1.0f / 3.0f, m2);
-                            sFM = __ffma2_rn(Q0, make_float2(W0, W0), sFM);
-                            sFM = __ffma2_rn(Q1, make_float2(W1, W1), sFM);
-                            sFM = __ffma2_rn(Q2, make_float2(W2, W2), sFM);
-                            sFM = __ffma2_rn(Q3, make_float2(W3, W3), sFM);
-                            sTG = __ffma2_rn(R0, make_float2(W0, W0), sTG);
-                            sTG = __ffma2_rn(R1, make_float2(W1, W1), sTG);
-                            sTG = __ffma2_rn(R2, make_float2(W2, W2), sTG);
-                            sTG = __ffma2_rn(R3, make_float2(W3, W3), sTG);
-                            sZa = fmaf(D0, Q0.x, fmaf(D1, Q1.x, fmaf(D2, Q2.x, fmaf(D3, Q3.x, sZa))));
+                            X0 = __fadd2_rn(X0, make_float2(fmaf(m1, -2.0f / 3.0f, fmaf(m3, -1.0f / 3.0f, m2)),
+                                                            fmaf(m0, -2.0f / 3.0f, fmaf(m1, 2.0f, -m2))));
+                            X1 = __fadd2_rn(X1, make_float2(fmaf(m0 - m2, 2.0f, m3 - m1),
+                                                            fmaf(m2, 3.0f, fmaf(m1, -4.0f, -m0))));
+                            X2 = __fadd2_rn(X2, make_float2(fmaf(m1, 2.0f, m2 - m3),
+                                                            fmaf(m0 + m1, 2.0f, -3.0f * m2)));
+                            X3 = __fadd2_rn(X3, make_float2((m3 - m1) * (1.0f / 3.0f),
+                                                            fmaf(m0, -1.0f / 3.0f, m2)));
                             kidx += th ? 3 : 2;
                             t = (th ? t3 + d : t3) - 1.0f;
-                            // node n + 3 (past the last interval: margin rows, zero adjoints)
-                            sp += Pm;
-                            PPM_CHECK(sp + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
-                            Q0 = nodeIM(sp);
-                            R0 = nodeTG(sp);
+                            PPM_CHECK(sq >= S && sq + 3 < S + (A.nE + kBwdMargin) * Pm, plan.err);
+                            retire(sq, X0);
+                            sq += Pm;
+                            X0 = make_float2(0.f, 0.f);
                         };
                         for (int n4 = nit / 4; n4 > 0; --n4) {
-                            interval(qa, qb, qc, qd, ra, rb, rc, rd);
-                            interval(qb, qc, qd, qa, rb, rc, rd, ra);
-                            interval(qc, qd, qa, qb, rc, rd, ra, rb);
-                            interval(qd, qa, qb, qc, rd, ra, rb, rc);
+                            interval(P0, P1, P2, P3);
+                            interval(P1, P2, P3, P0);
+                            interval(P2, P3, P0, P1);
+                            interval(P3, P0, P1, P2);
                         }
                         const int rem = nit % 4;
-                        if (rem > 0) interval(qa, qb, qc, qd, ra, rb, rc, rd);
-                        if (rem > 1) interval(qb, qc, qd, qa, rb, rc, rd, ra);
-                        if (rem > 2) interval(qc, qd, qa, qb, rc, rd, ra, rb);
+                        // the last three nodes of the window retire after the walk
+                        if (rem == 0) {
+                            retire(sq, P0); retire(sq + Pm, P1); retire(sq + 2 * Pm, P2);
+                        } else if (rem == 1) {
+                            interval(P0, P1, P2, P3);
+                            retire(sq, P1); retire(sq + Pm, P2); retire(sq + 2 * Pm, P3);
+                        } else if (rem == 2) {
+                            interval(P0, P1, P2, P3);
+                            interval(P1, P2, P3, P0);
+                            retire(sq, P2); retire(sq + Pm, P3); retire(sq + 2 * Pm, P0);
+                        } else {
+                            interval(P0, P1, P2, P3);
+                            interval(P1, P2, P3, P0);
+                            interval(P2, P3, P0, P1);
+                            retire(sq, P3); retire(sq + Pm, P0); retire(sq + 2 * Pm, P1);
+                        }
+                        // contract the accumulated mu rows with the element's mu
+                        // weights (halved: W and D are twice the weights)
+                        const float hw0 = fast ? 0.5f * P.w0 : 0.f, hw1 = fast ? 0.5f * P.w1 : 0.f;
+                        const float hw2 = fast ? 0.5f * P.w2 : 0.f, hw3 = fast ? 0.5f * P.w3 : 0.f;
+                        const float hv0 = fast ? 0.5f * P.v0 : 0.f, hv1 = fast ? 0.5f * P.v1 : 0.f;
+                        const float hv2 = fast ? 0.5f * P.v2 : 0.f, hv3 = fast ? 0.5f * P.v3 : 0.f;
+                        sFM = make_float2(fmaf(hw0, V0.x, fmaf(hw1, V1.x, fmaf(hw2, V2.x, hw3 * V3.x))),
+                                          fmaf(hv0, V0.x, fmaf(hv1, V1.x, fmaf(hv2, V2.x, hv3 * V3.x))));
+                        sTG = make_float2(fmaf(hw0, U0.x, fmaf(hw1, U1.x, fmaf(hw2, U2.x, hw3 * U3.x))),
+                                          fmaf(hw0, U0.y, fmaf(hw1, U1.y, fmaf(hw2, U2.y, hw3 * U3.y))));
+                        sZa = fmaf(hw0, V0.y, fmaf(hw1, V1.y, fmaf(hw2, V2.y, hw3 * V3.y)));
                     }
                     sF = sFM.x;
                     sMu = sFM.y;
