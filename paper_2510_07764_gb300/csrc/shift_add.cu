@@ -370,21 +370,15 @@ __device__ __forceinline__ float2 horner2(float2 t, float2 k0, float2 k1, float2
     return v;
 }
 
-// 16 bytes of the ring at a + OFF (OFF 0 or 2048: rows 0-7 or 8-15).  The
-// ring is only touched by these volatile loads and ring_put's volatile
-// stores, which keep their program order; __syncwarp orders the lanes.
-template <unsigned OFF>
+// 16 bytes of the ring at shared address a.  The ring is only touched by
+// these volatile loads and ring_put's volatile stores, which keep their
+// program order; __syncwarp orders the lanes.
 __device__ __forceinline__ float4 ring_get4(unsigned a)
 {
     float4 v;
-    if (OFF == 0)
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "r"(a));
-    else
-        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4+2048];"
-                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                     : "r"(a));
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(a));
     return v;
 }
 
@@ -465,13 +459,10 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     auto flush = [&]() {
         __syncwarp();
         float4 v[4];
-        if (r0 & 8) {
+        // rows 8-15 for odd blocks (fa[i] < ring + 2048, so the OR adds)
+        const unsigned hi = ((unsigned)r0 & 8u) << 8;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = ring_get4<2048>(fa[i]);
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) v[i] = ring_get4<0>(fa[i]);
-        }
+        for (int i = 0; i < 4; ++i) v[i] = ring_get4(fa[i] | hi);
         float2 s01 = __fadd2_rn(__fadd2_rn(make_float2(v[0].x, v[0].y), make_float2(v[0].z, v[0].w)),
                                 __fadd2_rn(make_float2(v[1].x, v[1].y), make_float2(v[1].z, v[1].w)));
         float2 s23 = __fadd2_rn(__fadd2_rn(make_float2(v[2].x, v[2].y), make_float2(v[2].z, v[2].w)),
@@ -491,6 +482,16 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     // K0..K3 the interval's coefficients.  Leaves A0 = node n + 3 and K0..K3
     // of interval n + 1, so the next call takes (A1, A2, A0).
     auto interval = [&](float2 &A0, float2 &A1, float2 &A2) {
+        // node n + 3, loaded first so the loads overlap the evaluations (slots
+        // past their last interval read the margin rows; those values only
+        // reach virtual energies)
+        of0 += Pm;
+        of1 += Pm;
+        PPM_CHECK(of0 + 3 < (A.nE + kSlabMargin) * Pm && of1 + 3 < (A.nE + kSlabMargin) * Pm,
+                  errp);
+        const float *q0 = slab + of0, *q1 = slab + of1;
+        const float2 r0v = make_float2(q0[0], q1[0]), r1v = make_float2(q0[1], q1[1]);
+        const float2 r2v = make_float2(q0[2], q1[2]), r3v = make_float2(q0[3], q1[3]);
         const float2 t2 = __fadd2_rn(t, d2);
         const float2 t3 = __fadd2_rn(t2, d2);
         const float2 v1 = horner2<CLIP>(t, K0, K1, K2, K3);
@@ -509,17 +510,10 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         t = __fadd2_rn(t3, m1);
         if (th0) t.x += d;
         if (th1) t.y += d;
-        // node n + 3 (slots past their last interval read the margin rows;
-        // those values only reach virtual energies)
-        of0 += Pm;
-        of1 += Pm;
-        PPM_CHECK(of0 + 3 < (A.nE + kSlabMargin) * Pm && of1 + 3 < (A.nE + kSlabMargin) * Pm,
-                  errp);
-        const float *q0 = slab + of0, *q1 = slab + of1;
-        float2 y = __fmul2_rn(W0, make_float2(q0[0], q1[0]));
-        y = __ffma2_rn(W1, make_float2(q0[1], q1[1]), y);
-        y = __ffma2_rn(W2, make_float2(q0[2], q1[2]), y);
-        y = __ffma2_rn(W3, make_float2(q0[3], q1[3]), y);
+        float2 y = __fmul2_rn(W0, r0v);
+        y = __ffma2_rn(W1, r1v, y);
+        y = __ffma2_rn(W2, r2v, y);
+        y = __ffma2_rn(W3, r3v, y);
         cubic_half2(A0, A1, A2, y, K0, K1, K2, K3);
         A0 = y;
     };
