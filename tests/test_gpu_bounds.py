@@ -1,7 +1,8 @@
 """The bounds-checked build (libppm_check.so, -DPPM_BOUNDS_CHECK) runs the
 forward, likelihood and gradient paths on workloads that reach the table
-edges, the HEALPix mesh and a temperature map, and reports no failed index
-check through ppm_sync; its results equal the ordinary build's."""
+edges, the node-major walks (with and without elements leaving the table),
+the HEALPix mesh and a temperature map, and reports no failed index check
+through ppm_sync; its results equal the ordinary build's."""
 import os
 import subprocess
 import sys
@@ -35,6 +36,23 @@ for s in "dab":
     out["grad_" + s] = g.cpu().numpy()
     out["Ft_" + s] = ctx.profile(dp).cpu().numpy()
     ctx.sync()
+# uniform ln E grids of 0.49 and 0.45 table node per step: the node-major walks
+# of the forward and backward, the second with elements leaving the table top
+for name, (lo, hi, n) in {"nw": (0.5, 6.0, 159), "nwedge": (3.5, 7.8, 56)}.items():
+    v = synth.atm_two_spot(n_theta=12, n_phi=40, n_phase=24, n_E=n, n_chan=20, atm=atm, lens=lens)
+    v.E_keV = synth.logspace(lo, hi, n)
+    v.R = synth.response(v.E_keV, 20)
+    v.sigma_ism = synth.sigma_ism(v.E_keV)
+    for s in "db":
+        v.interp = s
+        ctx = context(v)
+        dp = ppm.DeviceParams(v.inst)
+        cnt = torch.from_numpy(v.counts).cuda()
+        ll, g = ctx.loglike_grad(dp, cnt, v.tau)
+        ctx.sync()
+        out[name + "_grad_" + s] = g.cpu().numpy()
+        out[name + "_Ft_" + s] = ctx.profile(dp).cpu().numpy()
+        ctx.sync()
 c = synth.crescent_extreme(n_theta=24, n_phi=24, n_phase=32, n_E=48, n_chan=8, atm=atm)
 ctx = context(c)
 out["crescent"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
