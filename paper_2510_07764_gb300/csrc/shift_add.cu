@@ -10,17 +10,23 @@
 //     of a stencil are four consecutive words).
 // Each warp owns one output phase at a time; its lanes are 32 elements of
 // the ring (neighbouring elements see nearly the same redshift and emission
-// angle, so their table reads are broadcast-friendly and their stencil
-// shifts coincide).  A lane holds four elements and 16 energy accumulators.
-// For each element the mu stencil is contracted once per table energy node
-// (4 FMA) and the cubic in ln E of the current node interval is kept as
-// power-basis coefficients in registers, so an observed energy costs one add
-// (position), one compare (interval change) and three FMA (Horner); an
-// interval change contracts one new node and rebuilds the four coefficients.
-// After each chunk of 16 energies the accumulators are transposed across the
-// warp with 16 shuffles so lane l owns energy l, and added to the block's
-// phase x energy tile.  No atomics: each item writes its tile to a partial
-// buffer that a second kernel sums in a fixed order.
+// angle, so their table reads are broadcast-friendly).  For each element the
+// mu stencil is contracted once per table energy node (4 FMA) and the cubic
+// in ln E of the current node interval is kept as power-basis coefficients
+// in registers (packed FP32 pairs of elements).  Two walks through the
+// observed energies:
+//   - node-major (energy grids uniform in ln E with 0.34-0.498 table node
+//     per step): every element of the warp moves one table interval per
+//     iteration and evaluates the two or three energies inside it; the
+//     values go through a per-warp shared-memory ring and are summed into
+//     the phase row in blocks of eight energies (atm_group_nodes);
+//   - energy walk (other grids): one observed energy per step for all
+//     elements, an interval change per element where its position crosses
+//     a node; after each chunk of 16 energies the accumulators are
+//     transposed across the warp with 16 shuffles so lane l owns energy l
+//     (atm_group).
+// No atomics: each item writes its tile to a partial buffer that a second
+// kernel sums in a fixed order.
 #include <algorithm>
 
 #include "ppm_internal.cuh"
