@@ -5,16 +5,18 @@
 //   lambda    = tau C + bkg
 //   logL[b]   = sum_{rows of b, c} d ln(lambda) - lambda - ln Gamma(d + 1)
 //
-// k_resp_ll: 16 x 32 output tile per block (128 threads, 2 x 2 outputs each),
-// K staged through shared memory in steps of 32; the epilogue evaluates the
-// likelihood terms (ln lambda in FP32, sums in FP64) and writes one partial sum per (row, column tile).
+// k_resp_ll: 16 x 32 output tile per block; four groups of 128 threads (2 x 2
+// outputs each) take every fourth K step of 32 energies (staged through
+// shared memory), their partial tiles are added in group order, and the
+// first group evaluates the likelihood terms (ln lambda in FP32, sums in
+// FP64) and writes one partial sum per (row, column tile).
 // k_ll_final adds the partials of each instance in a fixed order.
 #include "ppm_internal.cuh"
 
 namespace ppm {
 namespace {
 
-constexpr int kTM = 16, kTN = 32, kTK = 32, kThreads = 128;
+constexpr int kTM = 16, kTN = 32, kTK = 32, kGroup = 128, kSplitK = 4, kThreads = kGroup * kSplitK;
 
 // ln Gamma(d + 1) = ln d!: table below kLogFactN (built on the host in FP64),
 // Stirling series above it (relative error < 1e-16 for d >= 4096).
@@ -37,12 +39,14 @@ __global__ void __launch_bounds__(kThreads) k_resp_ll(Params p, PlanDev plan,
                                                 double *__restrict__ row_ll,
                                                 float *__restrict__ model_counts)
 {
-    __shared__ float As[kTK][kTM + 1];
-    __shared__ float Bs[kTK][kTN + 1];
+    __shared__ float As[kSplitK][kTK][kTM + 1];
+    __shared__ float Bs[kSplitK][kTK][kTN + 1];
+    __shared__ float part[kSplitK - 1][kTM][kTN];  // partial tiles of groups 1..3
     __shared__ double red[kTM][17];  // [row][column-pair]
     __shared__ float att_nh[kTM];
     const int row0 = blockIdx.y * kTM, col0 = blockIdx.x * kTN;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 2 x 2 outputs per thread (8 x 16 threads)
+    const int grp = threadIdx.x / kGroup, lt = threadIdx.x % kGroup;
+    const int tx = lt & 15, ty = lt >> 4;   // 2 x 2 outputs per thread (8 x 16 threads)
     if (threadIdx.x < kTM) {
         const int row = row0 + threadIdx.x;
         att_nh[threadIdx.x] =
@@ -51,24 +55,28 @@ __global__ void __launch_bounds__(kThreads) k_resp_ll(Params p, PlanDev plan,
     }
     __syncthreads();
     float acc[2][2] = {};
-    for (int k0 = 0; k0 < nE; k0 += kTK) {
-        for (int i = threadIdx.x; i < kTM * kTK; i += kThreads) {
+    // every group runs the same number of steps (the barriers); steps past
+    // nE stage zeros
+    const int steps = (nE + kSplitK * kTK - 1) / (kSplitK * kTK);
+    for (int st = 0; st < steps; ++st) {
+        const int k0 = (st * kSplitK + grp) * kTK;
+        for (int i = lt; i < kTM * kTK; i += kGroup) {
             const int rr = i / kTK, kk = i - rr * kTK;
             const int row = row0 + rr, k = k0 + kk;
-            As[kk][rr] = (row < total_rows && k < nE)
-                             ? Ft[(size_t)row * nE + k] * expf(-att_nh[rr] * sigma[k])
-                             : 0.0f;
+            As[grp][kk][rr] = (row < total_rows && k < nE)
+                                  ? Ft[(size_t)row * nE + k] * expf(-att_nh[rr] * sigma[k])
+                                  : 0.0f;
         }
-        for (int i = threadIdx.x; i < kTK * kTN; i += kThreads) {
+        for (int i = lt; i < kTK * kTN; i += kGroup) {
             const int kk = i / kTN, cc = i - kk * kTN;
             const int k = k0 + kk, c = col0 + cc;
-            Bs[kk][cc] = (k < nE && c < nc) ? R[(size_t)k * nc + c] : 0.0f;
+            Bs[grp][kk][cc] = (k < nE && c < nc) ? R[(size_t)k * nc + c] : 0.0f;
         }
         __syncthreads();
 #pragma unroll 8
         for (int kk = 0; kk < kTK; ++kk) {
-            const float a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-            const float b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+            const float a0 = As[grp][kk][ty * 2], a1 = As[grp][kk][ty * 2 + 1];
+            const float b0 = Bs[grp][kk][tx * 2], b1 = Bs[grp][kk][tx * 2 + 1];
             acc[0][0] = fmaf(a0, b0, acc[0][0]);
             acc[0][1] = fmaf(a0, b1, acc[0][1]);
             acc[1][0] = fmaf(a1, b0, acc[1][0]);
@@ -76,7 +84,22 @@ __global__ void __launch_bounds__(kThreads) k_resp_ll(Params p, PlanDev plan,
         }
         __syncthreads();
     }
-    // epilogue: likelihood terms in FP64
+    // partial tiles of groups 1..3 added to group 0's in group order
+    if (grp > 0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) part[grp - 1][ty * 2 + i][tx * 2 + j] = acc[i][j];
+    }
+    __syncthreads();
+    if (grp > 0) return;
+#pragma unroll
+    for (int q = 0; q < kSplitK - 1; ++q)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) acc[i][j] += part[q][ty * 2 + i][tx * 2 + j];
+    // epilogue (first group): likelihood terms in FP64
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         const int rr = ty * 2 + i, row = row0 + rr;
@@ -105,7 +128,8 @@ __global__ void __launch_bounds__(kThreads) k_resp_ll(Params p, PlanDev plan,
         }
         red[rr][tx] = s;
     }
-    __syncthreads();
+    // barrier over the first group only (the others have returned)
+    asm volatile("bar.sync 1, %0;" ::"r"(kGroup));
     if (threadIdx.x < kTM) {
         const int row = row0 + threadIdx.x;
         double s = 0.0;
