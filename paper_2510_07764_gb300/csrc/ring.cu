@@ -17,6 +17,8 @@
 namespace ppm {
 namespace {
 
+constexpr unsigned kFullMask = 0xffffffffu;
+
 struct RingGeo {
     double theta, st, ct, half, dphi, R, u, sq1u, cos_eta, sin_eta, logg, beta, gamma;
     double area, dt_obl, nu, sini, cosi, phic, mask_c, mask_ct, mask_st, mask_phi;
@@ -127,7 +129,13 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
     __shared__ int s_inv_min, s_inv_max, s_vis0, s_base, s_wsum[8], s_cmin, s_cmax;
     const bool use_map = p.logT_map != nullptr;  // (HEALPix mesh only)
 
-    if (threadIdx.x == 0) {
+    // Ring set-up by warp 0.  Every lane computes the same scalars; the
+    // independent sines and cosines are evaluated in one lane-parallel
+    // sincos (lane k takes argument k) and the two logarithms in one
+    // lane-parallel log10, since an FP64 warp instruction costs the same with
+    // one active lane as with 32.  Lane 0 writes the shared record.
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         const double GM = p.mass_msun[b] * kGM_SUN;
         const double Rs = 2.0 * GM / (kC * kC);
         const double Re = p.radius_km[b] * 1e3;
@@ -138,57 +146,74 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         const double o2 = p.oblate ? Obar * Obar * (-0.788 + 1.030 * x) : 0.0;
         const double g0 = GM / (Re * Re) / sqrt(1.0 - Rs / Re);
         const double tc = p.colat[sidx], zt = p.zeta[sidx];
-        double th, dcos, half;
+        const double mz = p.mask_zeta[sidx];
+        double th, dth = 0.0, lo = 0.0, z = 0.0;
+        int n_el = ip.n_phi;
+        double phi0 = 0.0, dphi_hp = 0.0;
         if (plan.grid == 1) {
             // HEALPix ring r + 1 of N_side = (rings + 1) / 4 (Gorski et al. 2005):
             // z, pixel count and first azimuth; every pixel has solid angle pi/(3 N^2)
             const int N = (ip.n_theta + 1) / 4, i = r + 1;
             const double NN = (double)N;
-            double z;
             if (i < N || i > 3 * N) {
                 const int ipl = i < N ? i : 4 * N - i;
                 const double zz = 1.0 - (double)ipl * ipl / (3.0 * NN * NN);
                 z = i < N ? zz : -zz;
-                G.n_el = 4 * ipl;
-                G.phi0 = 0.25 * kPI / ipl;
+                n_el = 4 * ipl;
+                phi0 = 0.25 * kPI / ipl;
             } else {
                 z = 4.0 / 3.0 - 2.0 * i / (3.0 * NN);
-                G.n_el = 4 * N;
-                G.phi0 = 0.5 * kPI / NN * (1.0 - 0.5 * ((i - N + 1) % 2));
+                n_el = 4 * N;
+                phi0 = 0.5 * kPI / NN * (1.0 - 0.5 * ((i - N + 1) % 2));
             }
             th = acos(z);
-            G.dphi = 2.0 * kPI / G.n_el;
-            dcos = (kPI / (3.0 * NN * NN)) / G.dphi;
+            dphi_hp = 2.0 * kPI / n_el;
+        } else {
+            // ring of the spot's bounding grid
+            lo = fmax(tc - zt, 0.0);
+            const double hi = fmin(tc + zt, kPI);
+            dth = (hi - lo) / ip.n_theta;
+            th = lo + (r + 0.5) * dth;
+        }
+        // lane-parallel sines and cosines
+        double arg = 0.0;
+        arg = lane == 0 ? th : arg;
+        arg = lane == 1 ? lo + r * dth : arg;
+        arg = lane == 2 ? lo + (r + 1) * dth : arg;
+        arg = lane == 3 ? tc : arg;
+        arg = lane == 4 ? zt : arg;
+        arg = lane == 5 ? p.incl_rad[b] : arg;
+        arg = lane == 6 ? p.mask_colat[sidx] : arg;
+        arg = lane == 7 ? mz : arg;
+        double sv, cv;
+        sincos(arg, &sv, &cv);
+        const double st = __shfl_sync(kFullMask, sv, 0), ct = __shfl_sync(kFullMask, cv, 0);
+        const double c_lo = __shfl_sync(kFullMask, cv, 1), c_hi = __shfl_sync(kFullMask, cv, 2);
+        const double s_tc = __shfl_sync(kFullMask, sv, 3), c_tc = __shfl_sync(kFullMask, cv, 3);
+        const double c_zt = __shfl_sync(kFullMask, cv, 4);
+        const double sini = __shfl_sync(kFullMask, sv, 5), cosi = __shfl_sync(kFullMask, cv, 5);
+        const double s_mc = __shfl_sync(kFullMask, sv, 6), c_mc = __shfl_sync(kFullMask, cv, 6);
+        const double c_mz = __shfl_sync(kFullMask, cv, 7);
+        double dcos, half, dphi;
+        if (plan.grid == 1) {
+            dphi = dphi_hp;
+            dcos = (kPI / (3.0 * ((ip.n_theta + 1) / 4) * ((ip.n_theta + 1) / 4))) / dphi;
             // rings that cannot reach the emitter cap hold no pixel of the spot;
             // with a temperature map every ring is a candidate
             half = (use_map || fabs(th - tc) <= zt + 1e-12) ? kPI : 0.0;
-            G.cap_c = cos(zt);
-            G.cap_ct = cos(tc);
-            G.cap_st = sin(tc);
         } else {
-            // ring of the spot's bounding grid
-            const double lo = fmax(tc - zt, 0.0), hi = fmin(tc + zt, kPI);
-            const double dth = (hi - lo) / ip.n_theta;
-            th = lo + (r + 0.5) * dth;
-            dcos = cos(lo + r * dth) - cos(lo + (r + 1) * dth);
-            const double num = cos(zt) - cos(th) * cos(tc), den = sin(th) * sin(tc);
+            dcos = c_lo - c_hi;
+            const double num = c_zt - ct * c_tc, den = st * s_tc;
             if (den <= 0.0) half = num <= 0.0 ? kPI : 0.0;
             else half = acos(fmin(fmax(num / den, -1.0), 1.0));
-            G.n_el = ip.n_phi;
-            G.dphi = 2.0 * half / ip.n_phi;
-            G.phi0 = 0.0;
+            dphi = 2.0 * half / ip.n_phi;
         }
-        double st, ct;
-        sincos(th, &st, &ct);
-        G.theta = th; G.st = st; G.ct = ct; G.half = half;
         // shape, slope, gravity, speed
         const double R = Re * (1.0 + o2 * ct * ct);
         const double u = Rs / R;
         const double sq = sqrt(1.0 - u);
         const double f = -2.0 * o2 * Re * ct * st / (R * sq);
-        G.R = R; G.u = u; G.sq1u = sq;
-        G.cos_eta = 1.0 / sqrt(1.0 + f * f);
-        G.sin_eta = f / sqrt(1.0 + f * f);
+        const double sf = sqrt(1.0 + f * f);
         double gg = g0;
         if (p.oblate) {
             const double O2 = Obar * Obar, O4 = O2 * O2, O6 = O4 * O2;
@@ -200,39 +225,52 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
                              O6 * (0.975 * x) - O4 * (13.47 * x - 27.13 * x * x)) +
                        fabs(ct) * O4 * (13.47 * x - 27.13 * x * x));
         }
-        G.logg = log10(gg * 100.0);
-        G.beta = 2.0 * kPI * nu * R * st / (kC * sq);
-        G.gamma = 1.0 / sqrt(1.0 - G.beta * G.beta);
-        G.area = R * R * sqrt(1.0 + f * f) * dcos * G.dphi / (D * D) * kFluxScale;
-        G.dt_obl = (Re - R + Rs * log((Re - Rs) / (R - Rs))) / kC;
-        G.nu = nu;
-        sincos(p.incl_rad[b], &G.sini, &G.cosi);
-        G.phic = p.azim[sidx];
-        const double mz = p.mask_zeta[sidx];
-        G.has_mask = mz > 0.0;
-        G.mask_c = G.has_mask ? cos(mz) : 2.0;
-        G.mask_ct = cos(p.mask_colat[sidx]);
-        G.mask_st = sin(p.mask_colat[sidx]);
-        G.mask_phi = p.mask_azim[sidx];
-        // range checks (per-instance status)
-        bool in_range = u >= L.u_min && u <= L.u_max && D > 0.0 && nu >= 0.0 &&
-                        G.beta < 1.0 && Re > Rs && p.incl_rad[b] >= 0.0 &&
-                        p.incl_rad[b] <= kPI && isfinite(G.area);
-        if (!use_map) in_range = in_range && zt > 0.0 && zt <= kPI && tc >= 0.0 && tc <= kPI;
-        if (p.emission == 1) {
-            in_range = in_range && G.logg >= A.logg[0] && G.logg <= A.logg[A.ng - 1];
-            if (!use_map) {
-                const double lt = p.logT[sidx];
-                in_range = in_range && lt >= A.logT[0] && lt <= A.logT[A.nT - 1];
+        // lane-parallel log10: lane 0 the surface gravity, lane 1 the oblate delay ratio
+        const double lv = log10(lane == 1 ? (Re - Rs) / (R - Rs) : gg * 100.0);
+        const double logg = __shfl_sync(kFullMask, lv, 0);
+        const double lnr = __shfl_sync(kFullMask, lv, 1) * 2.302585092994045684;
+        const double beta = 2.0 * kPI * nu * R * st / (kC * sq);
+        const double area = R * R * sf * dcos * dphi / (D * D) * kFluxScale;
+        if (lane == 0) {
+            G.theta = th; G.st = st; G.ct = ct; G.half = half;
+            G.n_el = n_el; G.dphi = dphi; G.phi0 = phi0;
+            G.cap_c = c_zt; G.cap_ct = c_tc; G.cap_st = s_tc;
+            G.R = R; G.u = u; G.sq1u = sq;
+            G.cos_eta = 1.0 / sf;
+            G.sin_eta = f / sf;
+            G.logg = logg;
+            G.beta = beta;
+            G.gamma = 1.0 / sqrt(1.0 - beta * beta);
+            G.area = area;
+            G.dt_obl = (Re - R + Rs * lnr) / kC;
+            G.nu = nu;
+            G.sini = sini; G.cosi = cosi;
+            G.phic = p.azim[sidx];
+            G.has_mask = mz > 0.0;
+            G.mask_c = G.has_mask ? c_mz : 2.0;
+            G.mask_ct = c_mc;
+            G.mask_st = s_mc;
+            G.mask_phi = p.mask_azim[sidx];
+            // range checks (per-instance status)
+            bool in_range = u >= L.u_min && u <= L.u_max && D > 0.0 && nu >= 0.0 &&
+                            beta < 1.0 && Re > Rs && p.incl_rad[b] >= 0.0 &&
+                            p.incl_rad[b] <= kPI && isfinite(area);
+            if (!use_map) in_range = in_range && zt > 0.0 && zt <= kPI && tc >= 0.0 && tc <= kPI;
+            if (p.emission == 1) {
+                in_range = in_range && logg >= A.logg[0] && logg <= A.logg[A.ng - 1];
+                if (!use_map) {
+                    const double lt = p.logT[sidx];
+                    in_range = in_range && lt >= A.logT[0] && lt <= A.logT[A.nT - 1];
+                }
             }
+            if (!in_range) atomicMax(&status[b], (int)PPM_ERANGE);
+            G.ok = in_range && half > 0.0;
+            s_inv_min = n_fp;
+            s_inv_max = 0;
+            s_vis0 = 0;
+            s_cmin = 1 << 30;
+            s_cmax = -1;
         }
-        if (!in_range) atomicMax(&status[b], (int)PPM_ERANGE);
-        G.ok = in_range && half > 0.0;
-        s_inv_min = n_fp;
-        s_inv_max = 0;
-        s_vis0 = 0;
-        s_cmin = 1 << 30;
-        s_cmax = -1;
     }
     __syncthreads();
 
@@ -375,26 +413,48 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
         n_active = s_base;
     }
 
+    // the (logT, logg) stencils, one axis per lane of warp 0: linear for D,
+    // cubic for C, one-sided cubic for A and B; the logg stencil of a map is
+    // linear (its logT cells come from the pixels)
+    __shared__ int s_sti[2], s_stt[2];
+    __shared__ float s_stw[2][4], s_stdw[2][4];
+    const double lt = p.logT[sidx];
+    if (threadIdx.x < 2 && p.emission == 1) {
+        const bool gax = threadIdx.x == 1;
+        const int rule = (gax && use_map) ? 0
+                         : (A.strategy == kInterpD ? 0 : (A.strategy == kInterpC ? 1 : 2));
+        int taps;
+        float w[4], dw[4];
+        const int i0 = axis_stencil(gax ? A.logg : A.logT, gax ? A.ng : A.nT, gax ? G.logg : lt,
+                                    rule, &taps, w, dw);
+        s_sti[threadIdx.x] = i0;
+        s_stt[threadIdx.x] = taps;
+        for (int a = 0; a < 4; ++a) {
+            s_stw[threadIdx.x][a] = w[a];
+            s_stdw[threadIdx.x][a] = dw[a];
+        }
+    }
+    if (threadIdx.x < 32) __syncwarp();
     if (threadIdx.x == 0) {
         RingRec rec;
         rec.visible = (G.ok && s_vis0 && n_active > 0) ? 1 : 0;
         rec.n_active = n_active;
         rec.iT = 0; rec.ig = 0; rec.tT = 0; rec.tg = 0;
         for (int a = 0; a < 4; ++a) rec.wT[a] = rec.wg[a] = rec.dwT[a] = rec.dwg[a] = 0.0f;
-        const double lt = p.logT[sidx];
-        rec.kT = (float)(kKB_KEVK * pow(10.0, lt));
+        rec.kT = (float)(kKB_KEVK * exp(lt * 2.302585092994045684));
         if (p.emission == 1) {
-            // logT / logg: linear for D, cubic for C, one-sided cubic for A and B
-            const int rule = A.strategy == kInterpD ? 0 : (A.strategy == kInterpC ? 1 : 2);
-            rec.iT = axis_stencil(A.logT, A.nT, lt, rule, &rec.tT, rec.wT, rec.dwT);
-            rec.ig = axis_stencil(A.logg, A.ng, G.logg, rule, &rec.tg, rec.wg, rec.dwg);
+            rec.iT = s_sti[0]; rec.tT = s_stt[0];
+            rec.ig = s_sti[1]; rec.tg = s_stt[1];
+            for (int a = 0; a < 4; ++a) {
+                rec.wT[a] = s_stw[0][a]; rec.dwT[a] = s_stdw[0][a];
+                rec.wg[a] = s_stw[1][a]; rec.dwg[a] = s_stdw[1][a];
+            }
         }
         rec.map = use_map ? 1 : 0;
         if (use_map && p.emission == 1) {
             // the logT cells used by the ring's pixels
             rec.iT = s_cmax >= 0 ? s_cmin : 0;
             rec.tT = s_cmax >= 0 ? s_cmax - s_cmin + 1 : 0;
-            rec.ig = axis_stencil(A.logg, A.ng, G.logg, 0, &rec.tg, rec.wg, rec.dwg);
         }
         recs[g] = rec;
         if (triples && rec.visible)
