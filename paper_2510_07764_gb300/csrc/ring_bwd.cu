@@ -305,17 +305,39 @@ __global__ void __launch_bounds__(kTBlock) k_template_bwd(Params p, PlanDev plan
             atomicMax(&s_hi, i);
         }
     __syncthreads();
-    if (tid == 0) {
-        // reverse of the fill: bridged points feed z and phi_o of their ends
+    // reverse of the fill: bridged points feed z and phi_o of their ends,
+    // with weights (c - i) / (c - a) and (i - a) / (c - a); every thread sums
+    // its share and the block adds the shares in a fixed order
+    {
+        double f[4] = {0.0, 0.0, 0.0, 0.0};  // to a: z, phi_o; to c: z, phi_o
         if (s_lo <= s_hi) {
             const int a = s_lo - 1, c = s_hi + 1;
-            for (int i = s_lo; i <= s_hi; ++i) {
+            for (int i = s_lo + tid; i <= s_hi; i += blockDim.x) {
                 const double t = (double)(i - a) / (double)(c - a);
-                adj[1][a] += (1.0 - t) * adj[1][i];
-                adj[1][c] += t * adj[1][i];
-                adj[3][a] += (1.0 - t) * adj[3][i];
-                adj[3][c] += t * adj[3][i];
+                f[0] += (1.0 - t) * adj[1][i];
+                f[1] += (1.0 - t) * adj[3][i];
+                f[2] += t * adj[1][i];
+                f[3] += t * adj[3][i];
             }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double v = f[q];
+            for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((tid & 31) == 0) red[tid >> 5][q] = v;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (s_lo <= s_hi) {
+            const int a = s_lo - 1, c = s_hi + 1;
+            double t[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int w = 0; w < kTBlock / 32; ++w)
+                for (int q = 0; q < 4; ++q) t[q] += red[w][q];
+            adj[1][a] += t[0];
+            adj[3][a] += t[1];
+            adj[1][c] += t[2];
+            adj[3][c] += t[3];
         }
         // point n_fp is a copy of point 0
         for (int q = 0; q < 4; ++q) adj[q][0] += adj[q][n_fp];
