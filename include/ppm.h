@@ -320,8 +320,10 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
  * energies; one interval per iteration for all elements of a warp), and the
  * energy walk elsewhere; 1 always takes the energy walk (one observed
  * energy per iteration, interval changes per element).  The two sum the
- * same terms in a different order.  The setting applies to later calls of
- * the context.
+ * same terms in a different order.  With the node-major walk, phase_tile = 0
+ * picks 16 (its shared-memory rings leave room for two blocks per SM only
+ * with 16-phase tiles).  The backward pass of ppm_loglike_grad follows the
+ * same setting.  The setting applies to later calls of the context.
  *
  * ppm_autotune runs the forward profile of (p, res) once per candidate
  * (phase_tile 16/32 x waves 8/16/32 x persistent 0/1, one untimed and one
