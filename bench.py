@@ -53,7 +53,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="atm_two_spot",
-                    choices=["atm_two_spot", "bb_small", "crescent_extreme", "batch", "grad_batch"])
+                    choices=["atm_two_spot", "bb_small", "crescent_extreme", "batch", "grad_batch",
+                             "healpix_map"])
+    ap.add_argument("--interp", choices=["d", "a", "b", "c"], default=None,
+                    help="atmosphere interpolation strategy of Sect. 4 (default: the method's, d)")
+    ap.add_argument("--phase-sub", type=int, default=None,
+                    help="point samples per output phase bin (ppm_res.phase_sub)")
     ap.add_argument("--batch", type=int, default=None,
                     help="parameter vectors of the batch / grad_batch workloads")
     ap.add_argument("--flush-mib", type=int, default=512)
@@ -77,8 +82,14 @@ def make_workload(args, rank: int = 0):
         kw = {"seed": synth.SEED + (1 if args.workload == "grad_batch" else 0) + rank}
         if args.batch is not None:
             kw["B"] = args.batch
-        return synth.WORKLOADS[args.workload](**kw)
-    return synth.WORKLOADS[args.workload]()
+        w = synth.WORKLOADS[args.workload](**kw)
+    else:
+        w = synth.WORKLOADS[args.workload]()
+    if getattr(args, "interp", None):
+        w.interp = args.interp
+    if getattr(args, "phase_sub", None):
+        w.inst.phase_sub = int(args.phase_sub)
+    return w
 
 
 def max_over_ranks(values, device=None):
@@ -99,13 +110,18 @@ def workload_desc(w):
         "workload": w.name,
         "B": int(inst.B),
         "spots": int(inst.n_spots),
-        "elements_per_spot": "%dx%d" % (int(inst.n_theta[0]), int(inst.n_phi[0])),
+        "elements_per_spot": ("%d pixels" % (12 * int(inst.n_theta[0]) ** 2) if inst.grid == 1
+                              else "%dx%d" % (int(inst.n_theta[0]), int(inst.n_phi[0]))),
         "phases": int(inst.n_phase[0]),
         "energies": int(len(w.E_keV)),
         "channels": int(w.nc),
         "n_fp": int(inst.n_fp),
         "spacetime": "oblate Schwarzschild" if inst.oblate else "Schwarzschild+Doppler",
         "emission": "atmosphere table 35x11x67x166" if inst.emission else "analytic blackbody",
+        "interp": getattr(w, "interp", "d"),
+        "phase_sub": int(inst.phase_sub),
+        "grid": ("HEALPix N_side %d, temperature map" % int(inst.n_theta[0])
+                 if inst.grid == 1 else "spot-bounding"),
     }
 
 

@@ -209,6 +209,48 @@ __device__ __noinline__ void stage_slab_stencil(const AtmDev &A, const RingRec *
     }
 }
 
+// Slab of a 4 x 4 (logT, logg) stencil (the cubic strategies A, B, C) with
+// the 16 plane weights in registers and two words' 16 loads in flight per
+// thread; same sums as stage_slab_stencil, kept out of line (per ring).
+__device__ __noinline__ void stage_slab_4x4(const AtmDev &A, const RingRec *rp, const float *I0,
+                                            int plane, int Pm, float *slab, int tid)
+{
+    float wv[16];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) wv[4 * a + c] = rp->wT[a] * rp->wg[c];
+    const size_t ps = (size_t)plane;
+    const size_t gs = (size_t)A.ng * plane;
+    constexpr int U = 2;
+    for (int base = tid; base < plane; base += U * kSABlock) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kSABlock;
+            float acc = 0.0f;
+            if (idx < plane) {
+                float x[16];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) x[4 * a + c] = __ldg(I0 + a * gs + c * ps + idx);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) acc = fmaf(wv[q], x[q], acc);
+            }
+            v[u] = acc;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int idx = base + u * kSABlock;
+            if (idx < plane) {
+                const int m = idx / A.nE, n = idx - m * A.nE;
+                slab[n * Pm + m] = v[u];
+            }
+        }
+    }
+}
+
 // component e & 1 of a packed pair
 #define PPM_C(v, e) (((e) & 1) ? (v)[(e) >> 1].y : (v)[(e) >> 1].x)
 
@@ -697,6 +739,8 @@ __global__ void __launch_bounds__(kSABlock, 2)
                             }
                         }
                     }
+                } else if (rec.tT == 4 && rec.tg == 4) {
+                    stage_slab_4x4(A, rp, I0, plane, Pm, slab, tid);
                 } else {
                     stage_slab_stencil(A, rp, I0, plane, Pm, slab, tid);
                 }

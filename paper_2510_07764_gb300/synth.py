@@ -18,6 +18,8 @@ ranges, Sect. 2.5 / 2.8):
                         256 phases, 300 energies.
 * ``batch``             B parameter vectors with mixed resolutions.
 * ``grad_batch``        B two-cap vectors at 128x128, 128 phases.
+* ``healpix_map``       whole-surface HEALPix mesh, N_side 52, with a
+                        temperature map; the two-spot star and grids.
 
 Every function takes explicit sizes so tests can build reduced versions of
 the same workloads (several tiles plus a ragged tail).
@@ -450,10 +452,37 @@ def grad_batch(B: int = 1024, n_res: int = 128, n_phase: int = 128, n_E: int = 2
     return _with_response(w, n_chan, tau=TAU_TWO_SPOT)
 
 
+def healpix_map(n_side: int = 52, n_phase: int = 128, n_E: int = 256, n_chan: int = 300,
+                atm: Optional[AtmTable] = None, lens: Optional[LensSpec] = None,
+                seed: int = SEED) -> Workload:
+    """Whole-surface HEALPix mesh (Sect. 2.6) with a temperature map: N_side
+    = 52 gives 12 N^2 = 32,448 pixels, about the two-spot workload's 32,768
+    elements.  The map (ring order) is warm, log T 5.95-6.2 with a seeded
+    ripple, on two pixel ranges (15 % and 10 % of the surface) and dark
+    elsewhere (log T -1: no emission).  The two-spot star, atmosphere table,
+    phases, energies and response."""
+    inst = _instances(1, 1, mass_msun=1.4, radius_km=12.0, spin_hz=205.0,
+                      incl_rad=60 * DEG, dist_kpc=0.3, nh_1e20=1.0,
+                      colat=0.0, azim=0.0, zeta=math.pi, logT=6.0, mask_zeta=0.0,
+                      n_theta=n_side, n_phi=4 * n_side, n_phase=n_phase)
+    inst.grid = 1
+    npix = 12 * n_side * n_side
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = np.arange(npix)
+    lt = 6.075 + 0.125 * np.sin(2 * math.pi * 7.0 * k / npix + rng.uniform(0, 2 * math.pi))
+    warm = ((k >= int(0.20 * npix)) & (k < int(0.35 * npix))) | \
+           ((k >= int(0.60 * npix)) & (k < int(0.70 * npix)))
+    inst.logT_map = np.where(warm, lt, -1.0)[None, :]
+    w = Workload("healpix_map", inst, lens or LensSpec(), logspace(0.1, 5.215, n_E),
+                 atm=atm if atm is not None else atm_table())
+    return _with_response(w, n_chan, tau=TAU_TWO_SPOT)
+
+
 WORKLOADS = {
     "bb_small": bb_small,
     "atm_two_spot": atm_two_spot,
     "crescent_extreme": crescent_extreme,
     "batch": batch,
     "grad_batch": grad_batch,
+    "healpix_map": healpix_map,
 }

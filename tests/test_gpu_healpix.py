@@ -103,3 +103,19 @@ def test_map_of_a_uniform_cap_equals_the_cap_on_gpu(orc, synth, small_lens):
     mp, st = gpu_profile(w)
     assert st[0] == 0
     assert max_rel(mp, cap) < 1e-6
+
+
+def test_full_size_map_workload_sampled(orc, synth, atm):
+    """The HEALPix temperature-map workload at full size (N_side 52, 32,448
+    pixels, 128 phases, 256 energies): sampled bins against the oracle at
+    1e-3 relative."""
+    from gpu_helpers import gpu_profile, max_rel
+    w = synth.healpix_map(atm=atm)
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    rng = np.random.default_rng(5)
+    js = np.sort(rng.choice(128, 4, replace=False))
+    ks = np.sort(rng.choice(256, 8, replace=False))
+    ref = orc.profile(w, jsel=js, ksel=ks)
+    assert max_rel(got[np.ix_(js, ks)], ref) < 1e-3
+    assert np.isfinite(got).all() and got.sum() > 0
