@@ -422,10 +422,12 @@ __global__ void __launch_bounds__(kBwdBlock, 1)
                 if (sliding && !anyslow && NODES) {
                     // node-major walk (energy grid uniform in ln E, step d of
                     // 0.34-0.498 node): every lane moves one table interval per
-                    // iteration and evaluates the two or three energies in it;
-                    // the adjoints of virtual energies (before 0, past nE - 1)
-                    // are the zeros padding apad.  Nodes are half-scaled (see
-                    // cubic_half2): (I, I_mu) and (I_T, I_g) as packed pairs.
+                    // iteration and takes the two or three energies in it; the
+                    // adjoints of virtual energies (before 0, past nE - 1) are
+                    // the zeros padding apad.  Strategy B forms the interval
+                    // cubics from half-scaled nodes (see cubic_half2), packed as
+                    // (I, I_mu) and (I_T, I_g); the others use node weights
+                    // and a deferred mu contraction (below).
                     const float lz = fast ? P.lz : lz_safe;
                     const float hw0 = fast ? 0.5f * P.w0 : 0.f, hw1 = fast ? 0.5f * P.w1 : 0.f;
                     const float hw2 = fast ? 0.5f * P.w2 : 0.f, hw3 = fast ? 0.5f * P.w3 : 0.f;
