@@ -497,9 +497,10 @@ static float walk_step_of(const ppm_ctx *ctx)
 }
 
 // the atmosphere shift-and-add of this call takes the node-major walk
+// (spots and temperature maps alike)
 static bool node_walk_on(const ppm_ctx *ctx, const ppm_params *p, float step)
 {
-    return p->emission == 1 && !p->logT_map && ctx->tile_walk == 0 && step > 0.0f;
+    return p->emission == 1 && ctx->tile_walk == 0 && step > 0.0f;
 }
 
 static ppm_status refresh_energies(ppm_ctx *ctx)

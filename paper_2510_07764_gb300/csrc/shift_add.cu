@@ -403,6 +403,15 @@ constexpr int kRingBlock = 8;
 constexpr int kRingWarpBytes = kRingRows * 64 * 4;  // 64 columns of FP32 per row
 constexpr int kSlabMargin = 3;  // rows past the table read by slots past their last interval
 
+// the node-major walk applies (atmosphere emission, uniform energy step)
+static bool node_walk(const Params &p, const EnergyDev &en)
+{
+    return p.emission == 1 && en.sliding && en.step > 0.0f;
+}
+
+// rings of the block's warps plus the slack that aligns them to 4096 bytes
+static int ring_floats() { return (kSABlock / 32 * kRingWarpBytes + 4096) / 4; }
+
 __device__ __forceinline__ void ring_put(unsigned kk, unsigned colbase, float v)
 {
     // row (kk >> 8) & 15 of the ring; colbase has no bits in 0xF00
@@ -430,7 +439,11 @@ __device__ __forceinline__ float4 ring_get4(unsigned a)
     return v;
 }
 
-template <int MODE>
+// MAP: temperature-map elements of one logT cell; a node is contracted
+// against the cell's two slabs (slab: lower logT node, slab2: upper) with
+// the mu weights scaled by 1 - w and w, w = wcell[m] the element's own
+// weight of the upper node.
+template <int MODE, bool MAP = false>
 __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, float phi_out,
                                                 const float *sel, const float *ph,
                                                 const float *mun, const float *slab, int Pm,
@@ -438,11 +451,13 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
                                                 float inv_dlnE, const float *spk, int nE,
                                                 int nch, float d, float inv_d, float pk0,
                                                 float pkl, float lz_safe, unsigned ring,
-                                                float *frow, unsigned *errp)
+                                                float *frow, unsigned *errp,
+                                                const float *slab2 = nullptr,
+                                                const float *wcell = nullptr)
 {
     constexpr bool ONESIDED = MODE != 0, CLIP = MODE == 2;
     const float nEm2 = (float)(A.nE - 2);
-    float tv[2], wv[2][4], uv[2][4];
+    float tv[2], wv[2][4], wb[2][4], uv[2][4];
     unsigned kkv[2];
     int ofv[2], nit = 0;
     bool slow[2];
@@ -470,20 +485,32 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         const int s0 = fast ? P.s0 : 0;
         ofv[e] = (i0 + 2) * Pm + s0;
         // half weights: the walk carries u = y / 2 (see cubic_half2)
-        wv[e][0] = fast ? 0.5f * P.w0 : 0.0f;
-        wv[e][1] = fast ? 0.5f * P.w1 : 0.0f;
-        wv[e][2] = fast ? 0.5f * P.w2 : 0.0f;
-        wv[e][3] = fast ? 0.5f * P.w3 : 0.0f;
+        const float wT = MAP ? (m < n_act ? wcell[m] : 0.0f) : 0.0f;
+        const float fa = MAP ? 1.0f - wT : 1.0f;
+        wv[e][0] = fast ? 0.5f * P.w0 * fa : 0.0f;
+        wv[e][1] = fast ? 0.5f * P.w1 * fa : 0.0f;
+        wv[e][2] = fast ? 0.5f * P.w2 * fa : 0.0f;
+        wv[e][3] = fast ? 0.5f * P.w3 * fa : 0.0f;
+        wb[e][0] = (MAP && fast) ? 0.5f * P.w0 * wT : 0.0f;
+        wb[e][1] = (MAP && fast) ? 0.5f * P.w1 * wT : 0.0f;
+        wb[e][2] = (MAP && fast) ? 0.5f * P.w2 * wT : 0.0f;
+        wb[e][3] = (MAP && fast) ? 0.5f * P.w3 * wT : 0.0f;
         PPM_CHECK(i0 >= 1 && i0 + 2 <= A.nE - 1 && s0 + 3 < A.nmu, errp);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 4; ++q) {
             uv[e][q] = dot4(slab + (i0 - 1 + q) * Pm + s0, wv[e][0], wv[e][1], wv[e][2], wv[e][3]);
+            if (MAP)
+                uv[e][q] += dot4(slab2 + (i0 - 1 + q) * Pm + s0, wb[e][0], wb[e][1], wb[e][2],
+                                 wb[e][3]);
+        }
     }
     // one iteration more than the intervals of the last energy: the walk's
     // positions are accumulated and may cross the last node slightly late
     nit = __reduce_max_sync(kFull, nit) + 1;
     const float2 W0 = make_float2(wv[0][0], wv[1][0]), W1 = make_float2(wv[0][1], wv[1][1]);
     const float2 W2 = make_float2(wv[0][2], wv[1][2]), W3 = make_float2(wv[0][3], wv[1][3]);
+    const float2 B0 = make_float2(wb[0][0], wb[1][0]), B1 = make_float2(wb[0][1], wb[1][1]);
+    const float2 B2 = make_float2(wb[0][2], wb[1][2]), B3 = make_float2(wb[0][3], wb[1][3]);
     float2 a = make_float2(uv[0][1], uv[1][1]);
     float2 b = make_float2(uv[0][2], uv[1][2]);
     float2 c = make_float2(uv[0][3], uv[1][3]);
@@ -540,6 +567,14 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         const float *q0 = slab + of0, *q1 = slab + of1;
         const float2 r0v = make_float2(q0[0], q1[0]), r1v = make_float2(q0[1], q1[1]);
         const float2 r2v = make_float2(q0[2], q1[2]), r3v = make_float2(q0[3], q1[3]);
+        float2 s0v, s1v, s2v, s3v;
+        if (MAP) {
+            const float *p0 = slab2 + of0, *p1 = slab2 + of1;
+            s0v = make_float2(p0[0], p1[0]);
+            s1v = make_float2(p0[1], p1[1]);
+            s2v = make_float2(p0[2], p1[2]);
+            s3v = make_float2(p0[3], p1[3]);
+        }
         const float2 t2 = __fadd2_rn(t, d2);
         const float2 t3 = __fadd2_rn(t2, d2);
         const float2 v1 = horner2<CLIP>(t, K0, K1, K2, K3);
@@ -562,6 +597,12 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         y = __ffma2_rn(W1, r1v, y);
         y = __ffma2_rn(W2, r2v, y);
         y = __ffma2_rn(W3, r3v, y);
+        if (MAP) {
+            y = __ffma2_rn(B0, s0v, y);
+            y = __ffma2_rn(B1, s1v, y);
+            y = __ffma2_rn(B2, s2v, y);
+            y = __ffma2_rn(B3, s3v, y);
+        }
         cubic_half2(A0, A1, A2, y, K0, K1, K2, K3);
         A0 = y;
     };
@@ -618,10 +659,23 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
                     const int m = g0 + lane + 32 * e;
                     const PairW P = pair_weights_slow<ONESIDED>(sel[m], phi_out, ph, mun, n_fp,
                                                                 top, A, inv_dlnE);
+                    if (MAP) {
+                        const float wT = wcell[m];
+                        PairW Pa = P, Pb = P;
+                        Pa.w0 *= 1.0f - wT; Pa.w1 *= 1.0f - wT; Pa.w2 *= 1.0f - wT; Pa.w3 *= 1.0f - wT;
+                        Pb.w0 *= wT; Pb.w1 *= wT; Pb.w2 *= wT; Pb.w3 *= wT;
 #pragma unroll
-                    for (int k = 0; k < kEC; ++k) {
-                        const float v = eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz, ONESIDED);
-                        acc[k] += CLIP ? fmaxf(v, 0.0f) : v;
+                        for (int k = 0; k < kEC; ++k) {
+                            const float pp = pkc[k] + P.lz;
+                            acc[k] += eval_general(Pa, slab, Pm, A.nE, pp, false) +
+                                      eval_general(Pb, slab2, Pm, A.nE, pp, false);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < kEC; ++k) {
+                            const float v = eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz, ONESIDED);
+                            acc[k] += CLIP ? fmaxf(v, 0.0f) : v;
+                        }
                     }
                 }
             }
@@ -845,10 +899,10 @@ __global__ void __launch_bounds__(kSABlock, 2)
 // and reduction as k_shift_add.
 // ---------------------------------------------------------------------------
 struct MapLayout {
-    int tmpl, elems, cs, cw, munodes, slab, slab2, pk, E, E3, fblk, total;
+    int tmpl, elems, cs, cw, munodes, slab, slab2, pk, E, E3, fblk, ring, total;
 };
 
-template <int EMIS>
+template <int EMIS, bool NODES>
 __global__ void __launch_bounds__(kSABlock, 1)
     k_shift_add_map(Params p, PlanDev plan, AtmDev A, EnergyDev en, MapLayout lay,
                     const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
@@ -857,6 +911,11 @@ __global__ void __launch_bounds__(kSABlock, 1)
 {
     extern __shared__ float sm[];
     __shared__ int s_wsum[kSABlock / 32], s_cnt;
+    if (NODES)  // rows past the table that the node-major walk may read
+        for (int i = threadIdx.x; i < kSlabMargin * A.nmu_pad; i += blockDim.x) {
+            sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
+            sm[lay.slab2 + A.nE * A.nmu_pad + i] = 0.0f;
+        }
     const int item_id = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
     const Item it = plan.items[item_id];
     const InstPlan ip = plan.inst[it.b];
@@ -887,6 +946,11 @@ __global__ void __launch_bounds__(kSABlock, 1)
     const float pk0 = spk[0], pkl = spk[nE - 1];
     const float lz_safe = 1.25f - pk0;
     const bool sliding = en.sliding != 0;
+    // this warp's ring (node-major walk): 4096-byte aligned shared address
+    unsigned ring_w = 0;
+    if (NODES)
+        ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
+                 (unsigned)(warp * kRingWarpBytes);
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;
@@ -945,6 +1009,14 @@ __global__ void __launch_bounds__(kSABlock, 1)
             for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
                 const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
                 float *frow = Fblk + jl * nEpad;
+                if constexpr (EMIS == 1 && NODES) {
+                    for (int g0 = 0; g0 < cnt; g0 += 64)
+                        atm_group_nodes<0, true>(g0, cnt, lane, phi_out, cs, ph, mun, S0, Pm, n_fp,
+                                                 top, A, inv_dlnE, spk, nE, nch, en.step,
+                                                 en.inv_step, pk0, pkl, lz_safe, ring_w, frow,
+                                                 plan.err, S1, cw);
+                    continue;
+                }
                 for (int g0 = 0; g0 < cnt; g0 += 32) {
                     const int m = g0 + lane;
                     const bool on = m < cnt;
@@ -1048,7 +1120,8 @@ MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, cons
     MapLayout lay;
     int off = 0;
     auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
-    const int slab = p.emission == 1 ? A.nE * A.nmu_pad : 0;
+    const bool nodes = node_walk(p, en);
+    const int slab = p.emission == 1 ? (A.nE + (nodes ? kSlabMargin : 0)) * A.nmu_pad : 0;
     lay.tmpl = take(4 * (plan.n_fp + 1));
     lay.elems = 0;
     lay.cs = take(n_phi_max);
@@ -1060,6 +1133,7 @@ MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, cons
     lay.E = take(en.nEpad);
     lay.E3 = take(en.nEpad);
     lay.fblk = take(plan.pt * en.nEpad);
+    lay.ring = take(nodes ? ring_floats() : 0);
     lay.total = off;
     return lay;
 }
@@ -1132,15 +1206,6 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
 
 }  // namespace
 
-// the node-major walk applies (atmosphere emission, uniform energy step)
-static bool node_walk(const Params &p, const EnergyDev &en)
-{
-    return p.emission == 1 && en.sliding && en.step > 0.0f;
-}
-
-// rings of the block's warps plus the slack that aligns them to 4096 bytes
-static int ring_floats() { return (kSABlock / 32 * kRingWarpBytes + 4096) / 4; }
-
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max)
 {
@@ -1178,7 +1243,8 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
                                                         elemx, status, partials);
             return cudaGetLastError();
         };
-        return p.emission == 1 ? go(k_shift_add_map<1>) : go(k_shift_add_map<0>);
+        if (p.emission == 0) return go(k_shift_add_map<0, false>);
+        return node_walk(p, en) ? go(k_shift_add_map<1, true>) : go(k_shift_add_map<1, false>);
     }
     // persistent schedule: the queue counter must start at zero on the stream
     if (plan.queue) {

@@ -57,6 +57,13 @@ c = synth.crescent_extreme(n_theta=24, n_phi=24, n_phase=32, n_E=48, n_chan=8, a
 ctx = context(c)
 out["crescent"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
 ctx.sync()
+hm = synth.healpix_map(n_side=8, n_phase=16, n_E=96, n_chan=8, atm=atm, lens=lens)
+hm.E_keV = synth.logspace(0.6, 2.6, 96)
+hm.R = synth.response(hm.E_keV, 8)
+hm.sigma_ism = synth.sigma_ism(hm.E_keV)
+ctx = context(hm)
+out["atm_map_nodes"] = ctx.profile(ppm.DeviceParams(hm.inst)).cpu().numpy()
+ctx.sync()
 m = synth.bb_small(n_phase=16, n_E=16, lens=lens)
 m.inst.grid = 1; m.inst.n_theta[:] = 12; m.inst.n_phi[:] = 48
 m.inst.logT_map = np.full((1, 12 * 144), 6.05)

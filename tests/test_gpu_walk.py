@@ -212,3 +212,18 @@ def test_node_walk_cuda_graph_replay(synth, atm, small_lens):
         torch.cuda.synchronize()
         assert torch.equal(got_ll, ref_ll)
         assert torch.equal(torch.nan_to_num(got_g), torch.nan_to_num(ref_g))
+
+
+def test_node_walk_temperature_map(orc, synth, atm, small_lens):
+    """A HEALPix temperature map (N_side 12) on a 96-energy grid of 0.48 node
+    per step: the map kernel's node-major walk (two slabs per logT cell,
+    each element's own cell weight) against the oracle and the energy walk."""
+    w = synth.healpix_map(n_side=12, n_phase=24, n_E=96, n_chan=8, atm=atm, lens=small_lens)
+    w.E_keV = synth.logspace(0.6, 2.6, 96)
+    w.R = synth.response(w.E_keV, 8)
+    w.sigma_ism = synth.sigma_ism(w.E_keV)
+    assert 0.34 <= _step(w, atm) <= 0.498
+    node, energy = _both_walks(w)
+    assert not np.array_equal(node, energy)
+    assert max_rel(node, energy) < TOL_WALKS
+    assert max_rel(node, orc.profile(w)) < TOL_ATM
