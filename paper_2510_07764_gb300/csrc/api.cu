@@ -848,7 +848,7 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
         StageTimer t(ctx, 1, st);
         PPM_CUDA(launch_shift_add(P, plan, A, en, w->recs, w->tmpl, w->elems, w->status,
                                   w->partials, ctx->plan.n_phi_max, st, 2 * ctx->sm_count,
-                                  w->elemx),
+                                  w->elemx, ctx->smem_optin),
                  "shift-and-add kernel");
         t.done(1);
     }

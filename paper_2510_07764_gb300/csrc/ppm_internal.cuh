@@ -151,12 +151,14 @@ cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
 
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max);
-// grid_blocks: resident blocks of the persistent schedule (ignored without plan.queue)
+// grid_blocks: resident blocks of the persistent schedule (ignored without plan.queue);
+// smem_optin: the device's opt-in shared memory per block (0: temperature maps
+// take 256-thread blocks)
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
                              int n_phi_max, cudaStream_t st, int grid_blocks = 0,
-                             const float2 *elemx = nullptr);
+                             const float2 *elemx = nullptr, size_t smem_optin = 0);
 
 cudaError_t launch_reduce(const PlanDev &plan, const EnergyDev &en, const float *partials,
                           const int *status, int total_rows, float *Ft, cudaStream_t st);

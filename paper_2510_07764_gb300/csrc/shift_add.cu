@@ -410,7 +410,7 @@ static bool node_walk(const Params &p, const EnergyDev &en)
 }
 
 // rings of the block's warps plus the slack that aligns them to 4096 bytes
-static int ring_floats() { return (kSABlock / 32 * kRingWarpBytes + 4096) / 4; }
+static int ring_floats(int warps = kSABlock / 32) { return (warps * kRingWarpBytes + 4096) / 4; }
 
 __device__ __forceinline__ void ring_put(unsigned kk, unsigned colbase, float v)
 {
@@ -891,26 +891,30 @@ __global__ void __launch_bounds__(kSABlock, 2)
 
 // ---------------------------------------------------------------------------
 // Full-surface temperature maps (Sect. 2.6): every element has its own logT.
-// One element per lane (scalar code).  For each logT cell used by a ring the
-// two logg-interpolated table planes of the cell are staged and an element's
-// spectrum is (1 - w) I_lo + w I_hi with its own weight w, i.e. each node is
-// contracted against both planes with the mu weights scaled by (1 - w) and w.
-// The analytic blackbody uses each element's kT.  Same items, partial tiles
-// and reduction as k_shift_add.
+// For each logT cell used by a ring the two logg-interpolated table planes of
+// the cell are staged and an element's spectrum is (1 - w) I_lo + w I_hi with
+// its own weight w, i.e. each node is contracted against both planes with the
+// mu weights scaled by (1 - w) and w.  The node-major walk (two element slots
+// per lane, the map form of atm_group_nodes) runs in NT = 512-thread blocks
+// where the two slabs and sixteen rings fit in shared memory: one block per SM
+// then keeps 16 warps resident, as two blocks of the spot kernel do.  The
+// energy walk takes one element per lane (scalar code).  The analytic
+// blackbody uses each element's kT.  Same items, partial tiles and reduction
+// as k_shift_add.
 // ---------------------------------------------------------------------------
 struct MapLayout {
     int tmpl, elems, cs, cw, munodes, slab, slab2, pk, E, E3, fblk, ring, total;
 };
 
-template <int EMIS, bool NODES>
-__global__ void __launch_bounds__(kSABlock, 1)
+template <int EMIS, bool NODES, int NT = kSABlock>
+__global__ void __launch_bounds__(NT, 1)
     k_shift_add_map(Params p, PlanDev plan, AtmDev A, EnergyDev en, MapLayout lay,
                     const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
                     const float *__restrict__ elems, const float2 *__restrict__ elemx,
                     const int *__restrict__ status, float *__restrict__ partials)
 {
     extern __shared__ float sm[];
-    __shared__ int s_wsum[kSABlock / 32], s_cnt;
+    __shared__ int s_wsum[NT / 32], s_cnt;
     if (NODES)  // rows past the table that the node-major walk may read
         for (int i = threadIdx.x; i < kSlabMargin * A.nmu_pad; i += blockDim.x) {
             sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
@@ -1000,13 +1004,13 @@ __global__ void __launch_bounds__(kSABlock, 1)
                 __syncthreads();
                 if (tid == 0) {
                     int tot = 0;
-                    for (int w = 0; w < kSABlock / 32; ++w) tot += s_wsum[w];
+                    for (int w = 0; w < NT / 32; ++w) tot += s_wsum[w];
                     s_cnt += tot;
                 }
                 __syncthreads();
             }
             const int cnt = s_cnt;
-            for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
+            for (int jl = warp; jl < it.nj; jl += NT / 32) {
                 const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
                 float *frow = Fblk + jl * nEpad;
                 if constexpr (EMIS == 1 && NODES) {
@@ -1115,7 +1119,7 @@ __global__ void __launch_bounds__(kSABlock, 1)
 }
 
 MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
-                     int n_phi_max)
+                     int n_phi_max, int nt)
 {
     MapLayout lay;
     int off = 0;
@@ -1133,7 +1137,7 @@ MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, cons
     lay.E = take(en.nEpad);
     lay.E3 = take(en.nEpad);
     lay.fblk = take(plan.pt * en.nEpad);
-    lay.ring = take(nodes ? ring_floats() : 0);
+    lay.ring = take(nodes ? ring_floats(nt / 32) : 0);
     lay.total = off;
     return lay;
 }
@@ -1209,7 +1213,9 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
                             const EnergyDev &en, int n_phi_max)
 {
-    if (p.logT_map) return (size_t)map_layout(p, plan, A, en, n_phi_max).total * sizeof(float);
+    // the 256-thread map layout is the minimum; 512 threads are taken only where they fit
+    if (p.logT_map)
+        return (size_t)map_layout(p, plan, A, en, n_phi_max, kSABlock).total * sizeof(float);
     int off = 0;
     auto take = [&](int n) { off += (n + 3) & ~3; };
     take(4 * (plan.n_fp + 1));
@@ -1228,23 +1234,28 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
                              const EnergyDev &en, const RingRec *recs, const float *tmpl,
                              const float *elems, const int *status, float *partials,
                              int n_phi_max, cudaStream_t st, int grid_blocks,
-                             const float2 *elemx)
+                             const float2 *elemx, size_t smem_optin)
 {
     if (plan.n_items <= 0) return cudaSuccess;
     if (p.logT_map) {
         // temperature maps: one block per item (the static schedule)
-        const MapLayout lay = map_layout(p, plan, A, en, n_phi_max);
-        const size_t bytes = (size_t)lay.total * sizeof(float);
-        auto go = [&](auto kern) -> cudaError_t {
+        auto go = [&](auto kern, int nt) -> cudaError_t {
+            const MapLayout lay = map_layout(p, plan, A, en, n_phi_max, nt);
+            const size_t bytes = (size_t)lay.total * sizeof(float);
             cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)bytes);
             if (r != cudaSuccess) return r;
-            kern<<<plan.n_items, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems,
-                                                        elemx, status, partials);
+            kern<<<plan.n_items, nt, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, elemx,
+                                                  status, partials);
             return cudaGetLastError();
         };
-        if (p.emission == 0) return go(k_shift_add_map<0, false>);
-        return node_walk(p, en) ? go(k_shift_add_map<1, true>) : go(k_shift_add_map<1, false>);
+        if (p.emission == 0) return go(k_shift_add_map<0, false>, kSABlock);
+        if (!node_walk(p, en)) return go(k_shift_add_map<1, false>, kSABlock);
+        // 512 threads where the layout (with sixteen rings) fits the opt-in limit
+        const size_t wide = (size_t)map_layout(p, plan, A, en, n_phi_max, 512).total * sizeof(float);
+        const size_t stat = (512 / 32 + 1) * sizeof(int);
+        if (wide + stat <= smem_optin) return go(k_shift_add_map<1, true, 512>, 512);
+        return go(k_shift_add_map<1, true>, kSABlock);
     }
     // persistent schedule: the queue counter must start at zero on the stream
     if (plan.queue) {
