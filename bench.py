@@ -49,7 +49,10 @@ CPU_RING_STRIDE = 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    # default: 200 single-evaluation steps (about 0.2 s timed on the two-spot
+    # workload, so that the clock sampler sees the region), 50 for the CPU
+    # reference arm and 3 for the multi-second batch workloads
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="atm_two_spot",
@@ -126,10 +129,13 @@ def workload_desc(w):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling of the SM clock and the throttle reasons.  Sampling
+    is live (its first sample has arrived) before the timed region starts;
+    only the samples time-stamped inside the region [t0, t1] are reported."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 20
 
     def __init__(self, gpu_id):
         self.gpu_id = gpu_id
@@ -137,7 +143,8 @@ class Clocks:
         self.path = os.path.join("/tmp", "ppm_clocks_%d.csv" % os.getpid())
 
     def start(self):
-        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+               "-lms", str(self.PERIOD_MS)]
         if self.gpu_id is not None:
             cmd += ["-i", str(self.gpu_id)]
         try:
@@ -145,8 +152,22 @@ class Clocks:
             self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 10.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
-    def stop(self):
+    @staticmethod
+    def _stamp(text):
+        from datetime import datetime
+        try:
+            return datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def stop(self, t0, t1):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -155,24 +176,26 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm, smax = float(parts[2]), float(parts[3])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+            rows.append((self._stamp(parts[0]), sm, smax,
+                         {n for n, v in zip(names, parts[6:10]) if v.lower().startswith("active")}))
         os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+        used = inside if inside else rows
+        return {"sm_mhz": statistics.median(r[1] for r in used) if used else None,
+                "sm_max_mhz": max(r[2] for r in used) if used else None,
+                "samples": len(inside), "sample_ms": self.PERIOD_MS,
+                "window": "timed region" if inside else "whole run (no sample inside)",
+                "reasons": sorted(set().union(*[r[3] for r in used])) if used else []}
 
 
 def profile_traffic():
@@ -411,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
            for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
+    t0 = time.time()
     for k in range(args.steps):
         flush.fill_(float(k))
         evs[k][0].record()
@@ -420,8 +444,9 @@ def run_ours(args, rank, world, local_rank):
             step()
         evs[k][1].record()
     torch.cuda.synchronize()
+    t1 = time.time()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t0, t1)
     if graph is not None:
         # graph replays record no stage events: three direct calls for the breakdown
         for _ in range(3):
@@ -546,8 +571,16 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
+def default_steps(args):
+    """Timed steps when --steps is not given."""
+    if args.steps is None:
+        args.steps = (50 if args.impl == "reference" else
+                      3 if args.workload in ("batch", "grad_batch") else 200)
+    return args
+
+
 def main():
-    args = parse()
+    args = default_steps(parse())
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -1,0 +1,82 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler keeps only the
+samples time-stamped inside the timed region, and the step defaults."""
+import os
+import sys
+import time
+from datetime import datetime
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+class _Done:
+    """Stands in for the nvidia-smi process once it has written its samples."""
+
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _line(t, sm, power_cap="Not Active"):
+    stamp = datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return ("%s, 0, %d, 2070, 900.00, 0x0000000000000000, Not Active, Not Active, "
+            "Not Active, %s\n" % (stamp, sm, power_cap))
+
+
+def _sampled(tmp_path, lines, t0, t1):
+    c = bench.Clocks(None)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.writelines(lines)
+    c.f = open(c.path)
+    c.proc = _Done()
+    return c.stop(t0, t1)
+
+
+def test_only_samples_inside_the_timed_region_count(tmp_path):
+    now = time.time()
+    lines = [_line(now - 1.0, 1000), _line(now + 0.10, 2070), _line(now + 0.12, 2055),
+             _line(now + 0.14, 2070, power_cap="Active"), _line(now + 2.0, 600)]
+    out = _sampled(tmp_path, lines, now, now + 0.2)
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2070.0
+    assert out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"]
+    assert out["window"] == "timed region"
+    assert not os.path.exists(tmp_path / "clocks.csv")
+
+
+def test_no_sample_inside_falls_back_and_says_so(tmp_path):
+    now = time.time()
+    out = _sampled(tmp_path, [_line(now - 1.0, 1980), _line(now + 5.0, 2070)], now, now + 0.05)
+    assert out["samples"] == 0
+    assert out["window"].startswith("whole run")
+    assert out["sm_mhz"] == (1980 + 2070) / 2
+
+
+def test_malformed_lines_are_skipped(tmp_path):
+    now = time.time()
+    lines = ["garbage\n", "[Not Supported], 0, N/A, N/A, , , , , , \n", _line(now + 0.01, 2070)]
+    out = _sampled(tmp_path, lines, now, now + 0.1)
+    assert out["samples"] == 1 and out["sm_mhz"] == 2070.0
+
+
+def test_missing_sampler_is_reported():
+    c = bench.Clocks(None)
+    c.proc = None
+    assert c.stop(0.0, 1.0)["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_step_defaults(monkeypatch):
+    def steps(*argv):
+        monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+        return bench.default_steps(bench.parse()).steps
+    assert steps() == 200
+    assert steps("--impl", "reference") == 50
+    assert steps("--workload", "batch") == 3
+    assert steps("--workload", "grad_batch") == 3
+    assert steps("--steps", "7") == 7
