@@ -49,11 +49,12 @@ CPU_RING_STRIDE = 16
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    # default: 200 single-evaluation steps (about 0.2 s timed on the two-spot
-    # workload, so that the clock sampler sees the region), 50 for the CPU
-    # reference arm and 3 for the multi-second batch workloads
+    # defaults: 10 warm-up and 200 timed single-evaluation steps (about 0.2 s
+    # timed on the two-spot workload, so that the clock sampler sees the
+    # region); 5 and 50 for the CPU reference arm; 3 and 3 for the
+    # multi-second batch workloads
     ap.add_argument("--steps", type=int, default=None)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="atm_two_spot",
                     choices=["atm_two_spot", "bb_small", "crescent_extreme", "batch", "grad_batch",
@@ -572,10 +573,12 @@ def run_ours(args, rank, world, local_rank):
 
 
 def default_steps(args):
-    """Timed steps when --steps is not given."""
+    """Timed and warm-up steps when --steps / --warmup are not given."""
+    batch = args.workload in ("batch", "grad_batch")
     if args.steps is None:
-        args.steps = (50 if args.impl == "reference" else
-                      3 if args.workload in ("batch", "grad_batch") else 200)
+        args.steps = 50 if args.impl == "reference" else 3 if batch else 200
+    if args.warmup is None:
+        args.warmup = 5 if args.impl == "reference" else 3 if batch else 10
     return args
 
 

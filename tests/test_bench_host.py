@@ -74,9 +74,10 @@ def test_missing_sampler_is_reported():
 def test_step_defaults(monkeypatch):
     def steps(*argv):
         monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
-        return bench.default_steps(bench.parse()).steps
-    assert steps() == 200
-    assert steps("--impl", "reference") == 50
-    assert steps("--workload", "batch") == 3
-    assert steps("--workload", "grad_batch") == 3
-    assert steps("--steps", "7") == 7
+        a = bench.default_steps(bench.parse())
+        return a.steps, a.warmup
+    assert steps() == (200, 10)
+    assert steps("--impl", "reference") == (50, 5)
+    assert steps("--workload", "batch") == (3, 3)
+    assert steps("--workload", "grad_batch") == (3, 3)
+    assert steps("--steps", "7", "--warmup", "4") == (7, 4)
