@@ -13,8 +13,8 @@
  * Conventions
  * -----------
  * - Every entry point returns a ppm_status; nothing throws across the ABI.
- *   On error ppm_last_error() returns a message for the calling thread's last
- *   failed call on that context.
+ *   On error ppm_last_error() returns a message for the last failed call on
+ *   that context (one message per context; see the thread-safety rule below).
  * - "device" pointers are CUDA global-memory pointers on the context's device;
  *   "host" pointers are ordinary process memory.  The caller owns every
  *   pointer it passes; the library never frees caller memory and keeps no
