@@ -145,6 +145,48 @@ def test_bad_resolution_is_rejected(synth, small_lens):
         assert e.value.status == ppm.PPM_EINVAL
 
 
+def test_invalid_arguments_are_rejected_and_the_context_recovers(orc, synth, atm, small_lens):
+    """Each documented argument rule of ppm_params / ppm_res returns
+    PPM_EINVAL with its message before anything is enqueued, and the context
+    stays usable: the next valid call matches the oracle."""
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = synth.atm_two_spot(n_theta=8, n_phi=12, n_phase=16, n_E=24, n_chan=8, atm=atm,
+                           lens=small_lens)
+    ctx = context(w)
+    one = dict(n_spots=1)  # the second spot's values stay in the arrays, unread
+    n_side = 4
+    tmap = np.full((1, 12 * n_side * n_side), 6.0)
+    cases = [
+        (dict(n_spots=3), "n_spots"),
+        (dict(oblate=2), "oblate"),
+        (dict(emission=2), "emission"),
+        (dict(n_fp=4), "n_fp"),
+        (dict(grid=2), "grid must be"),
+        (dict(phase_sub=3), "phase_sub"),
+        (dict(logT_map=tmap, **one), "needs grid"),
+        (dict(logT_map=tmap, grid=1, n_theta=n_side), "needs n_spots = 1"),
+        (dict(grid=1, n_theta=2000), "N_side"),
+    ]
+    for kw, msg in cases:
+        inst = w.inst.replace(**kw)
+        with pytest.raises(ppm.PPMError, match=msg) as e:
+            ctx.profile(ppm.DeviceParams(inst))
+        assert e.value.status == ppm.PPM_EINVAL, kw
+    # a temperature map with a non-default interpolation strategy
+    ctx.set_interpolation("b")
+    try:
+        inst = w.inst.replace(logT_map=tmap, grid=1, n_theta=n_side, **one)
+        with pytest.raises(ppm.PPMError, match="default interpolation") as e:
+            ctx.profile(ppm.DeviceParams(inst))
+        assert e.value.status == ppm.PPM_EINVAL
+    finally:
+        ctx.set_interpolation("d")
+    Ft, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(Ft, orc.profile(w)) < TOL_ATM
+
+
 def test_energies_past_table_edges(orc, synth, atm, small_lens):
     """Redshifted energies leave the table (E' up to ~12 keV > 10 keV, down to
     0.07 keV near the 0.05 keV edge): linear edge intervals and clamping."""
