@@ -24,8 +24,9 @@
  *   valid once the stream has completed (see ppm_sync).
  * - Argument errors are detected on the host before any work is enqueued and
  *   return PPM_EINVAL.  Per-instance physics range errors (compactness outside
- *   the lens table, temperature or gravity outside the atmosphere table) are
- *   reported through `inst_status` and do not fail the call.
+ *   the lens table, temperature or gravity outside the atmosphere table, a
+ *   NaN or infinite parameter value the instance uses) are reported through
+ *   `inst_status` and do not fail the call.
  * - Angles are radians, masses solar masses, radii km, distances kpc,
  *   energies keV, hydrogen columns 1e20 cm^-2, temperatures log10(T / K).
  * - A context is not thread-safe: calls on one context must be serialised
@@ -48,7 +49,7 @@ extern "C" {
 typedef enum {
     PPM_OK = 0,
     PPM_EINVAL = 1,    /* bad argument, missing table, unsupported size */
-    PPM_ERANGE = 2,    /* per-instance: parameters outside the tables */
+    PPM_ERANGE = 2,    /* per-instance: parameters outside the tables or not finite */
     PPM_ENOMEM = 3,    /* device or pinned-host allocation failed */
     PPM_ECUDA = 4,     /* a CUDA runtime call failed */
     PPM_ETIMEOUT = 5,  /* ppm_sync gave up waiting */

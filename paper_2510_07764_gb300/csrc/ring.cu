@@ -256,6 +256,14 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
                             beta < 1.0 && Re > Rs && p.incl_rad[b] >= 0.0 &&
                             p.incl_rad[b] <= kPI && isfinite(area);
             if (!use_map) in_range = in_range && zt > 0.0 && zt <= kPI && tc >= 0.0 && tc <= kPI;
+            // inputs that no comparison above reaches: a NaN or infinite value
+            // flags the instance instead of running through its profile (a
+            // mask needs finite geometry; mask_zeta <= 0, even -inf, is no mask)
+            in_range = in_range && isfinite(p.nh_1e20[b]);
+            if (!use_map)
+                in_range = in_range && isfinite(G.phic) && isfinite(p.logT[sidx]) && !isnan(mz) &&
+                           (!(mz > 0.0) || (isfinite(mz) && isfinite(p.mask_colat[sidx]) &&
+                                            isfinite(G.mask_phi)));
             if (p.emission == 1) {
                 in_range = in_range && logg >= A.logg[0] && logg <= A.logg[A.ng - 1];
                 if (!use_map) {

@@ -7,7 +7,7 @@ logL: a relative error eps per bin moves logL by at most eps * sum|d - lambda|
 import numpy as np
 import pytest
 
-from gpu_helpers import gpu_loglike, max_rel, rows_of
+from gpu_helpers import gpu_loglike, gpu_profile, max_rel, rows_of
 
 pytestmark = pytest.mark.gpu
 
@@ -161,3 +161,45 @@ def test_fine_grid_response_through_downsampling(orc, synth, atm, small_lens):
     ctx.set_response(w.R, w.sigma_ism)
     assert max_rel(mc1.cpu().numpy(), mc2.cpu().numpy()) < 1e-6
     assert abs(ll1[0] - ll2[0]) <= 1e-6 * abs(ll2[0])
+
+
+def test_non_finite_parameters_flag_their_instance(orc, synth, atm, small_lens):
+    """A NaN or infinite value in a parameter that no range comparison
+    reaches (spot azimuth, N_H, mask geometry) flags its own instance
+    (PPM_ERANGE, logL = -inf, zero profile rows) and leaves the others equal
+    to a clean run; so does an infinite mass.  mask_zeta = -inf is no mask."""
+    w = synth.atm_two_spot(n_theta=8, n_phi=8, n_phase=16, n_E=32, n_chan=8, atm=atm,
+                           lens=small_lens)
+    inst = w.inst.select([0] * 7)
+    inst.azim[1, 0] = np.nan
+    inst.nh_1e20[2] = np.nan
+    inst.mask_zeta[3, 1] = np.inf
+    inst.mask_colat[4, 1] = np.nan
+    inst.mask_azim[5, 1] = np.inf
+    inst.mass_msun[6] = np.inf
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV, atm=atm, R=w.R, sigma_ism=w.sigma_ism,
+                        counts=np.concatenate([w.counts] * 7), tau=w.tau)
+    ll, _, st = gpu_loglike(w2)
+    assert list(st) == [0, 2, 2, 2, 2, 2, 2]
+    assert np.isfinite(ll[0]) and np.all(ll[1:] == -np.inf)
+    ref, _, _ = gpu_loglike(w)
+    assert abs(ll[0] - ref[0]) <= 1e-6 * abs(ref[0])
+    Ft, st2 = gpu_profile(w2)
+    assert list(st2) == list(st)
+    assert np.isfinite(Ft).all() and not Ft[rows_of(w2, 1).start:].any()
+    # a spot without a mask may say so with -inf
+    w3 = synth.Workload("c", w.inst.copy(), small_lens, w.E_keV, atm=atm, R=w.R,
+                        sigma_ism=w.sigma_ism, counts=w.counts, tau=w.tau)
+    w3.inst.mask_zeta[0, 0] = -np.inf
+    ll3, _, st3 = gpu_loglike(w3)
+    assert st3[0] == 0 and abs(ll3[0] - ref[0]) <= 1e-6 * abs(ref[0])
+
+
+def test_non_finite_blackbody_temperature_flags_its_instance(synth, small_lens):
+    w = synth.bb_small(n_theta=8, n_phi=8, n_phase=16, n_E=16, lens=small_lens)
+    inst = w.inst.select([0, 0])
+    inst.logT[1, 0] = np.nan
+    w2 = synth.Workload("b", inst, small_lens, w.E_keV)
+    Ft, st = gpu_profile(w2)
+    assert list(st) == [0, 2]
+    assert np.isfinite(Ft).all() and Ft[:16].any() and not Ft[16:].any()
