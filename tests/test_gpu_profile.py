@@ -187,6 +187,35 @@ def test_invalid_arguments_are_rejected_and_the_context_recovers(orc, synth, atm
     assert max_rel(Ft, orc.profile(w)) < TOL_ATM
 
 
+def test_sync_times_out_on_a_busy_stream_and_recovers(synth, atm):
+    """ppm_sync is a bounded wait: with about 9 ms of shift-and-add work still
+    queued on the stream it returns PPM_ETIMEOUT after 0.1 ms instead of
+    blocking; a later sync with a long limit returns PPM_OK, and the results
+    are those of a single call."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = synth.atm_two_spot(atm=atm)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    s = torch.cuda.Stream()
+    first = ctx.profile(dp, stream=s)   # plan and workspace settle here
+    ctx.sync(stream=s, timeout=60.0)
+    ref = first.clone()
+    # outputs allocated up front: nothing in the loop may synchronise the device
+    outs = [torch.empty_like(ref) for _ in range(10)]
+    sts = [torch.empty(1, dtype=torch.int32, device=ref.device) for _ in range(10)]
+    torch.cuda.synchronize()
+    for o, st in zip(outs, sts):
+        ctx.profile(dp, out=o, status=st, stream=s)
+    with pytest.raises(ppm.PPMError) as e:
+        ctx.sync(stream=s, timeout=1e-4)
+    assert e.value.status == ppm.PPM_ETIMEOUT
+    ctx.sync(stream=s, timeout=60.0)
+    assert all(torch.equal(o, ref) for o in outs)
+    assert all(int(st[0]) == 0 for st in sts)
+
+
 def test_energies_past_table_edges(orc, synth, atm, small_lens):
     """Redshifted energies leave the table (E' up to ~12 keV > 10 keV, down to
     0.07 keV near the 0.05 keV edge): linear edge intervals and clamping."""
