@@ -51,3 +51,28 @@ def test_null_context_calls_fail_cleanly(libppm):
     assert _abi.ppm_build_lens(None, spec, None) == _abi.PPM_EINVAL
     assert _abi.ppm_sync(None, None, 1.0) == _abi.PPM_EINVAL
     assert _abi.ppm_last_error(None) == "null context"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libppm.so every entry point raises LibraryMissing: there is no
+    CPU fallback behind the binding."""
+    import paper_2510_07764_gb300 as ppm
+    from paper_2510_07764_gb300 import _abi
+    monkeypatch.setattr(_abi, "LIB_PATH", str(tmp_path / "libppm.so"))
+    monkeypatch.setattr(_abi, "_lib", None)
+    with pytest.raises(ppm.LibraryMissing):
+        ppm.Context(0)
+    with pytest.raises(ppm.LibraryMissing):
+        _abi.ppm_sync(None, None, 1.0)
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The package and the benchmark's GPU arm load no module of oracle/."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r); import paper_2510_07764_gb300, "
+            "paper_2510_07764_gb300.synth, paper_2510_07764_gb300._abi; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))" % ROOT)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                         timeout=300, check=True)
+    assert out.stdout.strip() == "False"
