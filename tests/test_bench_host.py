@@ -81,3 +81,28 @@ def test_step_defaults(monkeypatch):
     assert steps("--workload", "batch") == (3, 3)
     assert steps("--workload", "grad_batch") == (3, 3)
     assert steps("--steps", "7", "--warmup", "4") == (7, 4)
+
+
+def test_traffic_only_for_the_profiled_configuration(monkeypatch):
+    def cfg(*argv):
+        monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
+        return bench.profiled_config(bench.default_steps(bench.parse()))
+    assert cfg()
+    assert cfg("--steps", "2", "--warmup", "3", "--no-cpu-baseline", "--graph")
+    assert not cfg("--workload", "batch")
+    assert not cfg("--workload", "healpix_map")
+    assert not cfg("--interp", "a")
+    assert not cfg("--phase-sub", "4")
+    assert not cfg("--walk", "1")
+    assert not cfg("--autotune")
+
+
+def test_forward_kernel_names():
+    import numpy as np
+    from paper_2510_07764_gb300 import synth
+    w = synth.bb_small(n_theta=4, n_phi=4, n_phase=4, n_E=4)
+    assert bench.forward_kernel_name(w) == "k_shift_add<blackbody>"
+    w.inst.emission = 1
+    assert bench.forward_kernel_name(w) == "k_shift_add<atmosphere>"
+    w.inst.logT_map = np.zeros((1, 12))
+    assert bench.forward_kernel_name(w) == "k_shift_add_map<atmosphere>"
