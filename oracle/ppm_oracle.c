@@ -799,6 +799,31 @@ static void template_at(const real *phio, const real *F, const real *z,
 /* Status codes of the oracle */
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ERANGE = 2 };
 
+/* Reading (the paper is silent on non-finite inputs): a NaN or infinite
+ * parameter the instance uses lies outside every table and is a range error.
+ * An infinite distance is not: it is a valid limit (zero flux).  Spot and
+ * mask parameters count only without a temperature map; a mask radius <= 0
+ * (-inf included) means no mask, and a mask needs finite geometry. */
+static int params_finite(const orc_inst *in)
+{
+    const double g[] = {RE(in->mass_msun), RE(in->radius_km), RE(in->spin_hz),
+                        RE(in->incl_rad), RE(in->nh_1e20)};
+    for (int i = 0; i < 5; i++)
+        if (!isfinite(g[i])) return 0;
+    if (isnan(RE(in->dist_kpc))) return 0;
+    if (in->logT_map) return 1;
+    for (int sp = 0; sp < in->n_spots; sp++) {
+        const double mz = RE(in->mask_zeta[sp]);
+        if (!isfinite(RE(in->colat[sp])) || !isfinite(RE(in->azim[sp])) ||
+            !isfinite(RE(in->zeta[sp])) || !isfinite(RE(in->logT[sp])) || isnan(mz))
+            return 0;
+        if (mz > 0.0 && !(isfinite(mz) && isfinite(RE(in->mask_colat[sp])) &&
+                          isfinite(RE(in->mask_azim[sp]))))
+            return 0;
+    }
+    return 1;
+}
+
 /* F_t[j][k] for the selected output phases jsel (indices into
  * phi_out = j / n_phase) and energies ksel (indices into E_keV); NULL
  * selects all.  ring_stride > 1 evaluates every ring_stride-th ring only
@@ -815,6 +840,7 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
     if (in->emission == 1 && A == NULL) return ORC_EINVAL;
     const int use_map = in->logT_map != NULL;
     if (use_map && in->grid != 1) return ORC_EINVAL;
+    if (!params_finite(in)) return ORC_ERANGE;
     if (ring_stride < 1) ring_stride = 1;
     int NJ = jsel ? nj : in->n_phase;
     int NK = ksel ? nk : nE;
