@@ -188,7 +188,7 @@ def test_invalid_arguments_are_rejected_and_the_context_recovers(orc, synth, atm
 
 
 def test_sync_times_out_on_a_busy_stream_and_recovers(synth, atm):
-    """ppm_sync is a bounded wait: with about 9 ms of shift-and-add work still
+    """ppm_sync is a bounded wait: with about 36 ms of shift-and-add work still
     queued on the stream it returns PPM_ETIMEOUT after 0.1 ms instead of
     blocking; a later sync with a long limit returns PPM_OK, and the results
     are those of a single call."""
@@ -203,8 +203,8 @@ def test_sync_times_out_on_a_busy_stream_and_recovers(synth, atm):
     ctx.sync(stream=s, timeout=60.0)
     ref = first.clone()
     # outputs allocated up front: nothing in the loop may synchronise the device
-    outs = [torch.empty_like(ref) for _ in range(10)]
-    sts = [torch.empty(1, dtype=torch.int32, device=ref.device) for _ in range(10)]
+    outs = [torch.empty_like(ref) for _ in range(40)]
+    sts = [torch.empty(1, dtype=torch.int32, device=ref.device) for _ in range(40)]
     torch.cuda.synchronize()
     for o, st in zip(outs, sts):
         ctx.profile(dp, out=o, status=st, stream=s)
