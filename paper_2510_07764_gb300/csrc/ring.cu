@@ -9,7 +9,9 @@
 //     visibility, Doppler factor and aberration, flux of Sect. 2.5) and the
 //     invisible-segment fill;
 //   - the list of active elements of the ring (mask caps removed), compacted;
-//   - the ring's atmosphere cell in (logT, logg).
+//   - the ring's atmosphere cell in (logT, logg);
+//   - the instance's range status: compactness, temperature or gravity outside
+//     the tables, invalid geometry, or a non-finite parameter it uses.
 // Every visibility and masking decision is taken in FP64, as in the oracle;
 // the template is then stored in FP32 for the shift-and-add kernel.
 #include "ppm_internal.cuh"
