@@ -235,6 +235,20 @@ def _work(inst, b, nE):
     return float(inst.n_spots) * inst.n_theta[b] * inst.n_phi[b] * inst.n_phase[b] * nE
 
 
+def _rings(inst, b):
+    """Rings per spot in the oracle's loop (4 N_side - 1 on the HEALPix mesh)."""
+    n = int(inst.n_theta[b])
+    return 4 * n - 1 if getattr(inst, "grid", 0) == 1 else n
+
+
+def sample_factor(inst, stride, nE):
+    """Work of the whole workload over the work of instance 0's sample
+    (every stride-th ring, ring 0 first)."""
+    total = sum(_work(inst, b, nE) for b in range(inst.B))
+    R = _rings(inst, 0)
+    return total / _work(inst, 0, nE) * R / math.ceil(R / stride)
+
+
 def oracle_sample(w, stride):
     """Time the FP64 oracle on instance 0, every `stride`-th ring (profile,
     response and logL); returns (seconds, extrapolation factor to the whole
@@ -250,9 +264,7 @@ def oracle_sample(w, stride):
         C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
         oracle.loglike(C, w0.counts, w.tau)
     dt = time.perf_counter() - t0
-    nE = len(w.E_keV)
-    total = sum(_work(w.inst, b, nE) for b in range(w.inst.B))
-    return dt, stride * total / _work(w.inst, 0, nE)
+    return dt, sample_factor(w.inst, stride, len(w.E_keV))
 
 
 def _single(w, b):
@@ -302,9 +314,7 @@ def oracle_sample_parallel(w, stride, workers):
             C = oracle.counts_model(Ft, w.R, w.sigma_ism, float(w.inst.nh_1e20[0]))
             oracle.loglike(C, w0.counts, w.tau)
         dt = time.perf_counter() - t0
-    nE = len(w.E_keV)
-    total = sum(_work(w.inst, b, nE) for b in range(w.inst.B))
-    return dt, stride * total / _work(w.inst, 0, nE)
+    return dt, sample_factor(w.inst, stride, len(w.E_keV))
 
 
 def fd_evals(w):
@@ -344,6 +354,19 @@ def cpu_baseline(w, grad_mode=False):
                          if grad_mode else "")}
 
 
+REF_BUDGET_S = 120.0
+
+
+def reference_stride(first_s, stride, n_steps, budget_s=REF_BUDGET_S, max_stride=1 << 30):
+    """Ring stride of the reference arm's per-step sample: the stride of the
+    first step, widened in proportion when n_steps samples of that size
+    would exceed the budget (the sample's cost scales as 1 / stride), and at
+    most the number of rings of a spot."""
+    if n_steps * first_s <= budget_s:
+        return stride
+    return int(min(max_stride, math.ceil(stride * n_steps * first_s / budget_s)))
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -353,15 +376,22 @@ def run_reference(args, rank, world):
     grad_mode = args.workload == "grad_batch"
     mult = fd_evals(w) if grad_mode else 1
     times = []
+    stride = REF_RING_STRIDE
     for k in range(args.warmup + args.steps):
-        dt, factor = oracle_sample(w, REF_RING_STRIDE)
+        dt, factor = oracle_sample(w, stride)
+        if k == 0:
+            # widen the sample stride so that the whole run stays near the budget
+            stride = reference_stride(dt, stride, args.warmup + args.steps,
+                                      max_stride=max(1, int(w.inst.n_theta[0])))
         if k >= args.warmup:
             times.append(dt * factor * mult)
+    if not times:
+        times.append(dt * factor * mult)
     per_step = sum(times) / len(times)
     value = w.inst.B / per_step
     per_eval = per_step / w.inst.B
     sample = ("instance 0, every %dth ring per step, extrapolated by element x phase x energy "
-              "work to the whole workload" % REF_RING_STRIDE)
+              "work to the whole workload" % stride)
     unit = "evals/s" if w.R is not None else "profile evals/s"
     if grad_mode:
         sample += "; x%d evaluations per central-difference gradient" % mult

@@ -106,3 +106,22 @@ def test_forward_kernel_names():
     assert bench.forward_kernel_name(w) == "k_shift_add<atmosphere>"
     w.inst.logT_map = np.zeros((1, 12))
     assert bench.forward_kernel_name(w) == "k_shift_add_map<atmosphere>"
+
+
+def test_reference_stride_keeps_the_run_within_budget():
+    # 55 steps of 1.9 s fit 120 s only at a wider stride; 10 steps do not need one
+    assert bench.reference_stride(1.9, 64, 10, budget_s=120.0) == 64
+    s = bench.reference_stride(1.9, 64, 205, budget_s=120.0, max_stride=128)
+    assert s == 128                       # capped at the rings of a spot
+    s = bench.reference_stride(1.9, 64, 100, budget_s=120.0, max_stride=1000)
+    assert s >= 64 and 100 * 1.9 * 64 / s <= 120.0 + 1e-9
+
+
+def test_sample_factor_counts_the_rings_sampled():
+    from paper_2510_07764_gb300 import synth
+    w = synth.atm_two_spot(n_theta=128, n_phi=8, n_phase=4, n_E=4, n_chan=2)
+    assert bench.sample_factor(w.inst, 16, 4) == 16.0
+    assert bench.sample_factor(w.inst, 100, 4) == 64.0     # rings 0 and 100 of 128
+    assert bench.sample_factor(w.inst, 1, 4) == 1.0
+    h = synth.healpix_map(n_side=8, n_phase=4, n_E=4, n_chan=2)
+    assert bench.sample_factor(h.inst, 16, 4) == 31 / 2     # 4 N - 1 = 31 rings, 2 sampled
