@@ -299,13 +299,13 @@ def ring_template(w, spot: int, r: int, b: int = 0, lens_obj: Optional[Lens] = N
     inst = w.inst
     L = lens_obj or lens(w.lens)
     n = inst.n_fp + 1
-    info = np.zeros(14)
+    info = np.zeros(15)
     F, z, ph, mu = (np.zeros(n) for _ in range(4))
     ic = inst_c(inst, b)
     st = lib().orc_ring_template(C.byref(ic), C.byref(L.c), spot, r, _ptr(info),
                                  _ptr(F), _ptr(z), _ptr(ph), _ptr(mu))
     keys = ["theta", "dcos", "half", "R", "u", "f", "cos_eta", "sin_eta", "logg", "beta",
-            "gamma", "dphi", "n_active", "status"]
+            "gamma", "dphi", "n_active", "status", "dt_obl"]
     return dict(zip(keys, info)), F, z, ph, mu
 
 

@@ -691,6 +691,12 @@ static int inside_cap(const orc_inst *in, int spot, real theta_r, real phi_r)
  * Returns 1 if the ring contributes, 0 if it is invisible at i_fp = 0
  * (whole ring skipped), -1 if u lies outside the lens table.
  * ===================================================================== */
+/* radial delay of emission radius R relative to R_e (Eq. delta_t_oblate) */
+static real oblate_delay(const orc_star *s, const orc_ring *rg)
+{
+    return (s->Re - rg->R + s->Rs * r_log((s->Re - s->Rs) / (rg->R - s->Rs))) / C_MS;
+}
+
 static int ring_template(const orc_star *s, const orc_ring *rg, real dphi,
                          const orc_lens *L, int n_fp, real *F, real *z,
                          real *phio, real *mu)
@@ -701,8 +707,7 @@ static int ring_template(const orc_star *s, const orc_ring *rg, real dphi,
     real sq = r_sqrt(1.0 - rg->u);
     /* area element R^2 sqrt(1+f^2) dcos(theta) dphi / D^2 (Eq. area_oblate) */
     real area = rg->R * rg->R * r_sqrt(1.0 + rg->f * rg->f) * rg->dcos * dphi / (s->D * s->D);
-    /* radial delay of emission radius R relative to R_e (Eq. delta_t_oblate) */
-    real dt_obl = (s->Re - rg->R + s->Rs * r_log((s->Re - s->Rs) / (rg->R - s->Rs))) / C_MS;
+    real dt_obl = oblate_delay(s, rg);
     int inv_min = n_fp, inv_max = 0;
     int vis0 = 0;
     for (int i = 0; i <= n_fp; i++) {
@@ -953,9 +958,9 @@ int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
         F[i] = RE(t[i]); z[i] = RE(t[n + i]); phio[i] = RE(t[2 * n + i]); mu[i] = RE(t[3 * n + i]);
     }
     free(t);
-    double v[14] = {RE(rg.theta), RE(rg.dcos), RE(half), RE(rg.R), RE(rg.u), RE(rg.f),
+    double v[15] = {RE(rg.theta), RE(rg.dcos), RE(half), RE(rg.R), RE(rg.u), RE(rg.f),
                     RE(rg.cos_eta), RE(rg.sin_eta), RE(rg.logg), RE(rg.beta), RE(rg.gamma),
-                    RE(dphi), (double)nact, (double)st};
+                    RE(dphi), (double)nact, (double)st, RE(oblate_delay(&s, &rg))};
     memcpy(info, v, sizeof(v));
     return st;
 }

@@ -2,7 +2,9 @@
 Omega_c_def and the g(theta) fit) by invariants that do not restate its
 coefficients: equatorial symmetry, flattening toward the poles, the slope f
 against a numerical derivative of the oracle's own R(theta), gravity larger
-at the pole than at the equator, and the spherical, non-rotating limits."""
+at the pole than at the equator, the spherical, non-rotating limits, and
+the oblate delay (Eq. delta_t_oblate) as the coordinate time of a radial
+photon (Schwarzschild) from R(theta) out to R_e."""
 import math
 
 import numpy as np
@@ -23,7 +25,7 @@ def _rings(orc, synth, inst, lens):
     w = synth.Workload("star", inst, lens, synth.logspace(0.5, 2.0, 4))
     recs = [orc.ring_template(w, 0, r)[0] for r in range(int(inst.n_theta[0]))]
     return {k: np.array([rec[k] for rec in recs]) for k in ("theta", "R", "u", "f", "logg",
-                                                           "beta")}
+                                                           "beta", "dt_obl")}
 
 
 @pytest.fixture(scope="module")
@@ -84,3 +86,17 @@ def test_non_rotating_or_spherical_star_is_uniform(orc, synth, wide_lens, spin, 
         assert np.all(g["beta"] == 0.0)
     else:
         assert g["beta"][0] < g["beta"][len(g["beta"]) // 2]
+
+
+def test_oblate_delay_is_radial_photon_coordinate_time(orc, synth, wide_lens):
+    """Eq. delta_t_oblate against the radial null geodesic: a photon from
+    r = R(theta) to r = R_e takes coordinate time int dr / (c (1 - R_s / r))."""
+    from scipy.integrate import quad
+    c = 299792458.0
+    g = _rings(orc, synth, _star(synth, 600.0, n_theta=16), wide_lens)
+    Re = 12.0e3
+    for R, u, dt in zip(g["R"], g["u"], g["dt_obl"]):
+        Rs = u * R
+        ref = quad(lambda r: 1.0 / (1.0 - Rs / r), R, Re, epsabs=0.0, epsrel=1e-13)[0] / c
+        assert dt == pytest.approx(ref, rel=1e-9, abs=1e-18)
+    assert np.all(g["dt_obl"] > 0.0)      # every ring below the equator's radius
