@@ -165,6 +165,7 @@ def td(u: float, alpha: float) -> float:
 
 
 def td_out(u: float, alpha: float) -> float:
+    """c Delta t / R of an outgoing ray (Eq. salmi_td)."""
     return lib().orc_td_out(u, alpha)
 
 
@@ -204,6 +205,8 @@ _lens_cache = {}
 
 
 def lens(spec) -> Lens:
+    """The lens tables C_alpha, LF and TD of Sect. 2.8.2 (alpha march,
+    numerical differentiation, resampling), cached per grid."""
     key = tuple(getattr(spec, f) for f in ("u_min", "u_max", "n_u", "cpsi_min", "cpsi_max",
                                            "n_cpsi", "calpha_min", "calpha_max", "n_calpha",
                                            "dalpha"))
@@ -234,6 +237,7 @@ class Atm:
 
 
 def bb_intensity(E_keV: float, kT_keV: float) -> float:
+    """Blackbody specific intensity 2 E^3 / (h^3 c^2) / (e^{E/kT} - 1) (App. C)."""
     return lib().orc_bb_intensity(E_keV, kT_keV)
 
 
@@ -270,7 +274,10 @@ class OracleRangeError(RuntimeError):
 def profile(w, b: int = 0, jsel: Optional[Sequence[int]] = None,
             ksel: Optional[Sequence[int]] = None, ring_stride: int = 1,
             lens_obj: Optional[Lens] = None, atm_obj: Optional[Atm] = None) -> np.ndarray:
-    """F_t[j, k] (photons cm^-2 s^-1 keV^-1) of instance b of workload w.
+    """F_t[j, k] (photons cm^-2 s^-1 keV^-1) of instance b of workload w:
+    the shift-and-add of Sect. 2.8.3 (Eq. add_Ft) over the ring templates,
+    with the flux of Sect. 2.5 / App. C and the atmosphere interpolation of
+    Sect. 4.
 
     ``jsel``/``ksel`` restrict the output to selected phase/energy indices.
     """
@@ -295,7 +302,9 @@ def profile(w, b: int = 0, jsel: Optional[Sequence[int]] = None,
 
 
 def ring_template(w, spot: int, r: int, b: int = 0, lens_obj: Optional[Lens] = None):
-    """Ring record and template arrays (F, z, phi_o, mu) of one ring."""
+    """Ring record and template arrays (F, z, phi_o, mu) of one ring: the
+    star model of Sect. 2.1-2.2 and 2.4, the five template steps of Sect.
+    2.8.3 and its invisible-segment fill."""
     inst = w.inst
     L = lens_obj or lens(w.lens)
     n = inst.n_fp + 1
@@ -310,7 +319,8 @@ def ring_template(w, spot: int, r: int, b: int = 0, lens_obj: Optional[Lens] = N
 
 
 def counts_model(Ft: np.ndarray, R: np.ndarray, sigma: np.ndarray, nh_1e20: float) -> np.ndarray:
-    """C = F_t diag(exp(-N_H sigma)) R  (count rate per phase and channel)."""
+    """C = F_t diag(exp(-N_H sigma)) R, the count rate per phase and channel
+    (ISM attenuation of Sect. 2.7, response of Sect. 2.8.4)."""
     Ft = np.ascontiguousarray(Ft, dtype=np.float64)
     R = np.ascontiguousarray(R, dtype=np.float32)
     sg = np.ascontiguousarray(sigma, dtype=np.float32)
@@ -322,7 +332,9 @@ def counts_model(Ft: np.ndarray, R: np.ndarray, sigma: np.ndarray, nh_1e20: floa
 
 
 def loglike(Cm: np.ndarray, d: np.ndarray, tau: float, bkg: Optional[np.ndarray] = None) -> float:
-    """Poisson log-likelihood sum d ln(lam) - lam - lnGamma(d+1), lam = tau C + b."""
+    """Poisson log-likelihood sum d ln(lam) - lam - lnGamma(d+1), lam = tau C + b
+    (the likelihood whose chi^2 limit Sect. 5 uses and that Sect. 6
+    accumulates on the GPU)."""
     Cm = np.ascontiguousarray(Cm, dtype=np.float64)
     d = np.ascontiguousarray(d, dtype=np.int32)
     bg = None if bkg is None else np.ascontiguousarray(bkg, dtype=np.float32)
@@ -381,7 +393,8 @@ def loglike_tangent(w, v, b: int = 0, h: float = 1e-20):
 
 def grad_tangent(w, b: int = 0):
     """Gradient of logL (GRAD_PARAMS order) by forward mode, one direction per
-    parameter."""
+    parameter (the paper gives no derivative; this differentiates the same
+    piecewise-smooth recipe, branches held fixed)."""
     n = 5 + 4 * w.inst.n_spots
     g = np.zeros(n)
     for j in range(n):
@@ -395,7 +408,8 @@ def grad_tangent(w, b: int = 0):
 # response down-sampling (Sect. 2.7, matrix DS)
 # ---------------------------------------------------------------------------
 def downsample_matrix(E_model, E_lo, E_hi) -> np.ndarray:
-    """DS[i, e] = integral over detector bin e of the linear interpolant on
+    """Down-sampling matrix DS of Sect. 2.7 (Eq. RSP).
+    DS[i, e] = integral over detector bin e of the linear interpolant on
     E_model that is 1 at node i and 0 at the others (np.interp: constant
     beyond the ends).  Written from the definition: the bin is cut at every
     model node inside it, where the integrand is linear, and each piece is
