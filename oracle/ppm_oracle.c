@@ -829,7 +829,9 @@ static int params_finite(const orc_inst *in)
     return 1;
 }
 
-/* F_t[j][k] for the selected output phases jsel (indices into
+/* Shift-and-add of Sect. 2.8.3 (Eq. add_Ft) with the flux of Sect. 2.5 /
+ * App. C and the atmosphere interpolation of Sect. 4:
+ * F_t[j][k] for the selected output phases jsel (indices into
  * phi_out = j / n_phase) and energies ksel (indices into E_keV); NULL
  * selects all.  ring_stride > 1 evaluates every ring_stride-th ring only
  * (used to time a bounded sample).  Ft has n_j * n_k entries, row-major. */
@@ -930,9 +932,10 @@ int orc_profile(const orc_inst *in, const orc_lens *L, const orc_atm *A,
     return status;
 }
 
-/* Ring quantities and template for tests: fills info[0..15] =
+/* Ring quantities (Sect. 2.1-2.2, 2.4; Eq. delta_t_oblate) and template
+ * (Sect. 2.8.3) for tests: fills info[0..14] =
  * {theta, dcos, half_width, R, u, f, cos_eta, sin_eta, logg, beta, gamma,
- *  area_dphi, n_active, status} and the four template arrays. */
+ *  dphi, n_active, status, dt_obl} and the four template arrays. */
 int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
                       double *info, double *F, double *z, double *phio, double *mu)
 {
@@ -969,7 +972,8 @@ int orc_ring_template(const orc_inst *in, const orc_lens *L, int spot, int r,
  * ISM, response and Poisson likelihood (Sect. 2.7, 2.8.4, 6)
  * ===================================================================== */
 
-/* C[j][c] = sum_k Ft[j][k] ATT_k R[k][c], ATT_k = exp(-N_H sigma_k) */
+/* C[j][c] = sum_k Ft[j][k] ATT_k R[k][c], ATT_k = exp(-N_H sigma_k)
+ * (ISM attenuation of Sect. 2.7, response contraction of Sect. 2.8.4) */
 void orc_counts(const real *Ft, int n_phase, int nE, const float *R, int nc,
                 const float *sigma, real nh_1e20, real *C)
 {
