@@ -125,3 +125,24 @@ def test_sample_factor_counts_the_rings_sampled():
     assert bench.sample_factor(w.inst, 1, 4) == 1.0
     h = synth.healpix_map(n_side=8, n_phase=4, n_E=4, n_chan=2)
     assert bench.sample_factor(h.inst, 16, 4) == 31 / 2     # 4 N - 1 = 31 rings, 2 sampled
+
+
+def test_reference_arm_prints_its_json_line():
+    """bench.py --impl reference runs the oracle on the host and prints one
+    JSON line with the keys the reference arm's contract names."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--workload", "bb_small", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=600, check=True, cwd=ROOT)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["unit"] == "profile evals/s" and line["higher_is_better"] is True
+    assert (line["steps"], line["warmup"], line["n_gpus"]) == (2, 1, 1)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1
+    assert "ring" in cb["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 \
+        and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "bb_small"
