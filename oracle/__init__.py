@@ -81,39 +81,44 @@ class InstC(C.Structure):
                 ("logT_map", C.POINTER(C.c_double))]
 
 
+def declare(L):
+    """Set the ctypes signatures of an ordinary oracle build ``L`` (a CDLL);
+    the tests use it on mutated copies of the oracle that check its pins."""
+    d = C.c_double
+    for name in ("orc_psi_out", "orc_td_out", "orc_rho", "orc_psi", "orc_td"):
+        f = getattr(L, name)
+        f.restype = d
+        f.argtypes = [d, d]
+    L.orc_lens_build.restype = C.c_int
+    L.orc_lens_build.argtypes = [C.POINTER(LensSpecC), C.c_void_p, C.c_void_p, C.c_void_p]
+    L.orc_lens_lookup.restype = C.c_int
+    L.orc_lens_lookup.argtypes = [C.POINTER(LensC), d, d, C.POINTER(d), C.POINTER(d)]
+    L.orc_td_lookup.restype = d
+    L.orc_td_lookup.argtypes = [C.POINTER(LensC), d, d]
+    L.orc_atm_interp.restype = d
+    L.orc_atm_interp.argtypes = [C.POINTER(AtmC), d, d, d, d]
+    L.orc_bb_intensity.restype = d
+    L.orc_bb_intensity.argtypes = [d, d]
+    L.orc_profile.restype = C.c_int
+    L.orc_profile.argtypes = [C.POINTER(InstC), C.POINTER(LensC), C.POINTER(AtmC),
+                              C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                              C.c_int, C.c_int, C.c_void_p]
+    L.orc_ring_template.restype = C.c_int
+    L.orc_ring_template.argtypes = [C.POINTER(InstC), C.POINTER(LensC), C.c_int, C.c_int,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.orc_counts.restype = None
+    L.orc_counts.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                             d, C.c_void_p]
+    L.orc_loglike.restype = d
+    L.orc_loglike.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, d]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        d = C.c_double
-        for name in ("orc_psi_out", "orc_td_out", "orc_rho", "orc_psi", "orc_td"):
-            f = getattr(L, name)
-            f.restype = d
-            f.argtypes = [d, d]
-        L.orc_lens_build.restype = C.c_int
-        L.orc_lens_build.argtypes = [C.POINTER(LensSpecC), C.c_void_p, C.c_void_p, C.c_void_p]
-        L.orc_lens_lookup.restype = C.c_int
-        L.orc_lens_lookup.argtypes = [C.POINTER(LensC), d, d, C.POINTER(d), C.POINTER(d)]
-        L.orc_td_lookup.restype = d
-        L.orc_td_lookup.argtypes = [C.POINTER(LensC), d, d]
-        L.orc_atm_interp.restype = d
-        L.orc_atm_interp.argtypes = [C.POINTER(AtmC), d, d, d, d]
-        L.orc_bb_intensity.restype = d
-        L.orc_bb_intensity.argtypes = [d, d]
-        L.orc_profile.restype = C.c_int
-        L.orc_profile.argtypes = [C.POINTER(InstC), C.POINTER(LensC), C.POINTER(AtmC),
-                                  C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
-                                  C.c_int, C.c_int, C.c_void_p]
-        L.orc_ring_template.restype = C.c_int
-        L.orc_ring_template.argtypes = [C.POINTER(InstC), C.POINTER(LensC), C.c_int, C.c_int,
-                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
-        L.orc_counts.restype = None
-        L.orc_counts.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
-                                 d, C.c_void_p]
-        L.orc_loglike.restype = d
-        L.orc_loglike.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, d]
-        _lib = L
+        _lib = declare(C.CDLL(_LIB))
     return _lib
 
 
