@@ -577,10 +577,12 @@ static void ring_of_spot(const orc_inst *in, int spot, int r, real *theta,
     if (RE(den) <= 0.0) {
         *half = RE(num) <= 0.0 ? ORC_PI : 0.0;
     } else {
+        /* a clamped half-width is a constant (pi: the ring encircles the
+         * pole inside the cap; 0: it misses the cap) and has no derivative */
         real a = num / den;
-        if (RE(a) < -1.0) a = -1.0;
-        if (RE(a) > 1.0) a = 1.0;
-        *half = r_acos(a);
+        if (RE(a) <= -1.0) *half = ORC_PI;
+        else if (RE(a) >= 1.0) *half = 0.0;
+        else *half = r_acos(a);
     }
 }
 

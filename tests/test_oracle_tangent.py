@@ -80,3 +80,25 @@ def test_tangent_is_linear_in_the_direction(orc, small_two_cap):
     g = orc.grad_tangent(small_two_cap)
     v = np.linspace(-1.0, 1.0, 13) * np.asarray(SCALE)
     assert orc.loglike_tangent(small_two_cap, v)[1] == pytest.approx(float(g @ v), rel=1e-11)
+
+
+def test_tangent_with_caps_over_the_poles(orc, synth, atm, small_lens):
+    """Caps that contain a pole: the rings that encircle it have the clamped
+    half-width pi, a constant with no derivative (the same branch-fixed
+    function the ordinary build evaluates).  Forward mode against central
+    differences, as above."""
+    w = synth.atm_two_spot(n_theta=8, n_phi=12, n_phase=16, n_E=24, n_chan=12, atm=atm,
+                           lens=small_lens)
+    i = w.inst
+    i.incl_rad[0] = 40 * DEG
+    i.colat[0] = [0.3, math.pi - 0.25]
+    i.azim[0] = [0.3, 2.0]
+    i.zeta[0] = [0.5, 0.4]
+    i.logT[0] = [6.112, 6.023]
+    i.mask_zeta[0] = [0.0, 0.0]
+    g = orc.grad_tangent(w)
+    assert np.all(np.isfinite(g))
+    fd = oracle_fd(orc, w, rel=1e-5)
+    sc = np.asarray(SCALE)
+    tol = 1e-5 * np.abs(fd) + 1e-7 * np.max(np.abs(fd) * sc) / sc
+    assert np.all(np.abs(g - fd) <= tol), np.abs(g / fd - 1)
