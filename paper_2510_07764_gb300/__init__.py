@@ -16,7 +16,7 @@ from . import _abi
 from ._abi import (PPM_EINVAL, PPM_ENOMEM, PPM_ENOTREADY, PPM_ERANGE, PPM_ETIMEOUT, PPM_OK,
                    LibraryMissing)
 
-__all__ = ["Context", "DeviceParams", "PPMError", "LibraryMissing", "LogLikelihood",
+__all__ = ["Context", "DeviceParams", "InstanceView", "PPMError", "LibraryMissing", "LogLikelihood",
            "GRAD_NAMES", "N_GRAD", "PPM_OK", "PPM_ERANGE", "PPM_EINVAL", "PPM_ENOMEM", "PPM_ETIMEOUT",
            "PPM_ENOTREADY"]
 
@@ -115,6 +115,43 @@ class DeviceParams:
         for f in _abi.PARAM_FIELDS:
             setattr(p, f, self.t[f].data_ptr())
         p.logT_map = None if self.t_map is None else self.t_map.data_ptr()
+        return p
+
+    def instance(self, b: int) -> "InstanceView":
+        """Instance b alone, as a one-instance argument of the same calls; it
+        points into these device arrays (no copy)."""
+        return InstanceView(self, b)
+
+
+# per-spot parameter arrays ([B, n_spots]); the others have one value per instance
+_SPOT_FIELDS = ("colat", "azim", "zeta", "logT", "mask_colat", "mask_azim", "mask_zeta")
+
+
+class InstanceView:
+    """One instance of a DeviceParams (B = 1) sharing its device arrays: the
+    pointers of its ppm_params and ppm_res are offset to instance b."""
+
+    def __init__(self, dp: DeviceParams, b: int):
+        if not 0 <= b < dp.B:
+            raise IndexError("instance %d of %d" % (b, dp.B))
+        self.parent, self.b = dp, b
+        self.B, self.n_spots, self.oblate, self.emission = 1, dp.n_spots, dp.oblate, dp.emission
+        self.rows = int(dp.n_phase[b])
+        self.row0 = int(dp.n_phase[:b].sum())
+        ip = C.POINTER(C.c_int)
+        at = lambda a: C.cast(a.ctypes.data + 4 * b, ip)
+        self.res = _abi.ppm_res(at(dp.n_theta), at(dp.n_phi), at(dp.n_phase), dp.n_fp, dp.grid,
+                                dp.phase_sub)
+        self._pix0 = int(sum(12 * int(n) ** 2 for n in dp.n_theta[:b])) if dp.grid == 1 else 0
+
+    def struct(self) -> _abi.ppm_params:
+        dp = self.parent
+        p = _abi.ppm_params()
+        p.B, p.n_spots, p.oblate, p.emission = 1, self.n_spots, self.oblate, self.emission
+        for f in _abi.PARAM_FIELDS:
+            per = self.n_spots if f in _SPOT_FIELDS else 1
+            setattr(p, f, dp.t[f].data_ptr() + 8 * per * self.b)
+        p.logT_map = None if dp.t_map is None else dp.t_map.data_ptr() + 8 * self._pix0
         return p
 
 
@@ -316,8 +353,14 @@ def LogLikelihood(theta, ctx: "Context", dp: DeviceParams, counts, tau: float, b
 
     theta: [B, 13] float64 CUDA tensor (``GRAD_NAMES`` order, requires_grad as
     needed); the other parameters (spin, masks, resolutions) come from ``dp``.
-    The forward call computes logL and its gradient together through
-    ppm_loglike_grad; backward scales the stored gradient."""
+    When autograd needs the gradient (grad mode on and theta requiring it) the
+    forward call computes logL and its gradient together through
+    ppm_loglike_grad and backward scales the stored gradient; otherwise it
+    runs the forward likelihood alone (ppm_loglike)."""
+    import torch
+    if not (torch.is_grad_enabled() and theta.requires_grad):
+        dp.set_theta(theta.detach())
+        return ctx.loglike(dp, counts, tau, bkg=bkg, counts_shared=counts_shared)
     global _LOGLIKE_FN
     if _LOGLIKE_FN is None:
         _LOGLIKE_FN = _loglike_function()

@@ -76,8 +76,9 @@ def test_step_defaults(monkeypatch):
         monkeypatch.setattr(sys, "argv", ["bench.py", *argv])
         a = bench.default_steps(bench.parse())
         return a.steps, a.warmup
-    assert steps() == (200, 10)
-    assert steps("--impl", "reference") == (50, 5)
+    assert steps() == (20, 5)                              # the suite's headline
+    assert steps("--workload", "atm_two_spot") == (200, 10)
+    assert steps("--impl", "reference") == (20, 5)
     assert steps("--workload", "batch") == (3, 3)
     assert steps("--workload", "grad_batch") == (3, 3)
     assert steps("--steps", "7", "--warmup", "4") == (7, 4)

@@ -24,9 +24,7 @@ def _worker(rank, world, port, q):
     try:
         import bench
 
-        class A:
-            workload, batch = "batch", 6
-        w = bench.make_workload(A, rank)
+        w = bench.make_workload("batch", None, rank, B=6)
         mx = bench.max_over_ranks([1.0 + rank, 10.0 - rank, 0.5])
         q.put((rank, [float(x) for x in w.inst.mass_msun], mx))
     finally:
