@@ -241,17 +241,28 @@ ppm_status ppm_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res,
  * time -- for example a sampler that has already handed the rest of the
  * device memory to its own pool, or one that cannot afford the
  * device-wide synchronisation that cudaMalloc/cudaFree imply while other
- * work is in flight.  It computes exactly what ppm_profile computes (same
- * kernels, same arguments and layouts) but takes every per-call buffer from
- * a fixed 64 MiB array in the library's device memory, which every GPU that
- * loads the library holds until the process exits, and builds its plan in a
- * fixed host buffer: it calls no cudaMalloc, cudaFree or other allocating
- * routine.  The context's tables must already be set by the usual setters.
+ * work is in flight.  It computes what ppm_profile computes, with the same
+ * kernels and buffer layouts and a plan built by ppm_profile's phase-tile and
+ * ring-group rules under the context's tile settings (no persistent queue;
+ * items in plan order), so that its output equals ppm_profile's bit for bit
+ * unless its ring groups had to be widened (below).  It takes every per-call
+ * buffer from a fixed 64 MiB array in the library's device memory, which
+ * every GPU that loads the library holds until the process exits, and builds
+ * its plan in a fixed 1 MiB host buffer: it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The context's tables must already be set by the
+ * usual setters.  Temperature maps are not supported (PPM_EINVAL).
  *
- * - Problems whose per-call buffers exceed 64 MiB (after widening ring
- *   groups) or whose plan exceeds 1 MiB of host staging return PPM_EINVAL
- *   with a message; nothing is enqueued.  (The default two-spot 128x128
- *   workload with 128 phases and 256 energies fits.)
+ * - Problems whose per-call buffers exceed 64 MiB with ppm_profile's ring
+ *   groups are retried with groups 2, 4, ... times wider (the sums are then
+ *   grouped differently, equal to rounding); problems that exceed it even
+ *   with one group per spot, or whose plan exceeds 1 MiB of host staging,
+ *   return PPM_EINVAL with a message; nothing is enqueued.  (The default
+ *   two-spot 128x128 workload with 128 phases and 256 energies fits.)
+ * - The plan is copied from the fixed host buffer with a pageable
+ *   cudaMemcpyAsync, which returns only once the buffer has been consumed:
+ *   the call can therefore wait on the host for the work already queued on
+ *   `stream`.  A stream that is being captured is refused with PPM_EINVAL
+ *   before anything is enqueued.
  * - The first call on a device looks up the array's device address on that
  *   device; make that first call before any stream capture.
  * - All calls in the process share the one array per device, which keeps the

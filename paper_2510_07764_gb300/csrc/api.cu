@@ -1209,7 +1209,9 @@ void *g_noalloc_dev[kNoAllocMaxDevices];   // device address of the array, per d
 
 // Sizes of one allocation-free plan (no containers: counts only).
 struct NoAllocPlan {
-    int pt, g, n_items, n_tiles, total_rings, total_rows, n_phi_max, nEpad;
+    int pt, n_items, n_tiles, total_rings, total_rows, n_phi_max, nEpad;
+    double target;  // work per item that sets the ring-group width
+    long long widen;  // ring groups widened by this factor to fit the array
     size_t total_elems;
     size_t o_inst, o_items, o_tiles, host_bytes;        // host staging layout
     size_t o_E, o_E3, o_pk, o_invE;                     // (also mirrored on the device)
@@ -1218,17 +1220,27 @@ struct NoAllocPlan {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-void noalloc_sizes(const ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, int pt, int g,
-                   NoAllocPlan *L)
+// ring-group width of instance b: the rule of ppm_profile's plan (groups of
+// about `target` element x phase x energy work per item), times L->widen
+int noalloc_group(const ppm_ctx *ctx, const ppm_res *res, int b, const NoAllocPlan *L)
 {
-    L->pt = pt;
-    L->g = g;
+    const int nr = rings_per_spot(res, b);
+    const int nq = res->n_phase[b] * res->phase_sub;
+    const double ring_cost = (double)slots_per_ring(res, b) * std::min(L->pt, nq) *
+                             (double)ctx->E.size();
+    const double gb = std::max(1.0, std::floor(L->target / ring_cost));
+    return (int)std::min<double>(nr, gb * (double)L->widen);
+}
+
+void noalloc_sizes(const ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, NoAllocPlan *L)
+{
+    const int pt = L->pt;
     L->n_items = L->n_tiles = L->total_rings = L->total_rows = L->n_phi_max = 0;
     L->total_elems = 0;
     for (int b = 0; b < p->B; ++b) {
         const int nr = rings_per_spot(res, b), ns = slots_per_ring(res, b);
         const int tiles = (res->n_phase[b] * res->phase_sub + pt - 1) / pt;
-        const int gb = std::min(g, nr);
+        const int gb = noalloc_group(ctx, res, b, L);
         const int groups = (nr + gb - 1) / gb;
         L->n_tiles += tiles;
         L->n_items += tiles * p->n_spots * groups;
@@ -1271,6 +1283,16 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
         return fail(ctx, PPM_EINVAL, "device index beyond %d", kNoAllocMaxDevices);
     DeviceGuard guard(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    // the plan is uploaded from a static host buffer that the next call
+    // rewrites: a stream being captured is refused before anything is enqueued
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+        if (e != cudaSuccess) cudaGetLastError();
+        if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+            return fail(ctx, PPM_EINVAL,
+                        "ppm_profile_noalloc refuses a stream that is being captured");
+    }
     // one-time set-up on this device (the current device is ctx->device here)
     if (!g_noalloc_dev[ctx->device]) {
         void *ptr = nullptr;
@@ -1279,27 +1301,34 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     }
     unsigned char *dev = static_cast<unsigned char *>(g_noalloc_dev[ctx->device]);
 
-    // plan: the ppm_profile heuristics, with ring groups widened until the
-    // per-call buffers fit the fixed device array
+    // plan: ppm_profile's phase tile and ring-group rules with the context's
+    // tile settings (so that the items, and hence the sums, are the same as
+    // ppm_profile's), the ring groups widened by 2, 4, ... only when the
+    // per-call buffers would not fit the fixed device array; no persistent
+    // queue, items launched in plan order
     long long T32 = 0;
     int max_theta = 1;
+    double total = 0.0;
     for (int b = 0; b < p->B; ++b) {
         T32 += (long long)p->n_spots * rings_per_spot(res, b) *
                ((res->n_phase[b] * res->phase_sub + kPT - 1) / kPT);
         max_theta = std::max(max_theta, rings_per_spot(res, b));
+        total += (double)p->n_spots * rings_per_spot(res, b) * slots_per_ring(res, b) *
+                 res->n_phase[b] * res->phase_sub * (double)ctx->E.size();
     }
     const float step = walk_step_of(ctx);
-    const int pt = (node_walk_on(ctx, p, step) || T32 < (long long)ctx->sm_count * 16) ? 16 : kPT;
-    long long T = 0;
-    for (int b = 0; b < p->B; ++b)
-        T += (long long)p->n_spots * rings_per_spot(res, b) *
-             ((res->n_phase[b] * res->phase_sub + pt - 1) / pt);
-    int g = (int)std::max<long long>(1, T / std::max<long long>((long long)ctx->sm_count * 12, 1));
+    int pt = (node_walk_on(ctx, p, step) || T32 < (long long)ctx->sm_count * 16) ? 16 : kPT;
+    if (ctx->tile_pt == 16 || ctx->tile_pt == 32) pt = ctx->tile_pt;
+    if (const char *env = getenv("PPM_PHASE_TILE")) {
+        const int v = atoi(env);
+        if (v == 16 || v == 32) pt = v;
+    }
     NoAllocPlan L;
-    for (;;) {
-        noalloc_sizes(ctx, p, res, pt, g, &L);
-        if (L.device_bytes <= kNoAllocDeviceBytes || g >= max_theta) break;
-        g = std::min(2 * g, max_theta);
+    L.pt = pt;
+    L.target = std::max(1.0, total / ((double)ctx->sm_count * 2.0 * (double)ctx->tile_waves));
+    for (L.widen = 1;; L.widen *= 2) {
+        noalloc_sizes(ctx, p, res, &L);
+        if (L.device_bytes <= kNoAllocDeviceBytes || L.widen >= max_theta) break;
     }
     if (L.device_bytes > kNoAllocDeviceBytes)
         return fail(ctx, PPM_EINVAL,
@@ -1332,7 +1361,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
         rings += p->n_spots * ip.n_theta;
         elems += (size_t)p->n_spots * ip.n_theta * ip.n_phi;
         rows += ip.n_phase;
-        const int gb = std::min(L.g, ip.n_theta);
+        const int gb = noalloc_group(ctx, res, b, &L);
         for (int t = 0; t < ip.tiles; ++t) {
             const int begin = items;
             for (int sp = 0; sp < p->n_spots; ++sp)
@@ -1403,7 +1432,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     float *tmpl = reinterpret_cast<float *>(dev + L.o_tmpl);
     float *el = reinterpret_cast<float *>(dev + L.o_elems);
     float *part = reinterpret_cast<float *>(dev + L.o_part);
-    // pageable source: the copy has consumed the staging buffer when it returns
+    // pageable source: the copy has consumed the staging buffer when it
+    // returns, which can mean waiting for the work already queued on st
     PPM_CUDA(cudaMemcpyAsync(dev, h, L.host_bytes, cudaMemcpyHostToDevice, st), "upload plan");
     // the array keeps the previous call's contents: status must start at zero
     PPM_CUDA(cudaMemsetAsync(dev + L.o_status, 0, sizeof(int) * p->B, st), "clear status");
