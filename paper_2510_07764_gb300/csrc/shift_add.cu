@@ -393,19 +393,14 @@ __device__ __forceinline__ void atm_group(int g0, int n_act, int lane, float phi
 // slot stores its values in its own column of a ring of 16 energy rows
 // (row = energy mod 16); once every slot of the warp has passed a block of
 // 8 energies the warp sums the block's rows (fixed order) into the phase
-// row.  An interval stores at the rows base, base + 1 and base + 2 of its
-// first energy (one row address, immediate offsets), so the ring has two
-// shadow rows 16 and 17 after row 15 that stand for rows 0 and 1: the block
-// sums of rows 0 and 1 add their shadow rows and clear both, and a group of
-// slots starts with all four cleared.  A slot starts with up to two virtual
-// energies below energy 0 in its first interval and may run up to five past
-// the last one: their rows are rewritten by real energies before they are
-// summed, or have been summed already, or lie beyond nE.
+// row.  A slot starts with up to two virtual energies below energy 0 in its
+// first interval and may run up to five past the last one: their rows are
+// rewritten by real energies before they are summed, or have been summed
+// already, or lie beyond nE.
 // ---------------------------------------------------------------------------
 constexpr int kRingRows = 16;
 constexpr int kRingBlock = 8;
-constexpr int kRingRowBytes = 64 * 4;               // 64 columns of FP32 per row
-constexpr int kRingWarpBytes = (kRingRows + 2) * kRingRowBytes;  // with the shadow rows
+constexpr int kRingWarpBytes = kRingRows * 64 * 4;  // 64 columns of FP32 per row
 constexpr int kSlabMargin = 3;  // rows past the table read by slots past their last interval
 
 // the node-major walk applies (atmosphere emission, uniform energy step)
@@ -414,42 +409,13 @@ static bool node_walk(const Params &p, const EnergyDev &en)
     return p.emission == 1 && en.sliding && en.step > 0.0f;
 }
 
-// rings of the block's warps plus the slack that aligns them to 16 bytes
-static int ring_floats(int warps = kSABlock / 32) { return (warps * kRingWarpBytes + 16) / 4; }
+// rings of the block's warps plus the slack that aligns them to 4096 bytes
+static int ring_floats(int warps = kSABlock / 32) { return (warps * kRingWarpBytes + 4096) / 4; }
 
-// the warp's ring at the 16-byte aligned shared address at or after `base`
-__device__ __forceinline__ unsigned ring_base(const float *base, int warp)
+__device__ __forceinline__ void ring_put(unsigned kk, unsigned colbase, float v)
 {
-    return (((unsigned)__cvta_generic_to_shared(base) + 15u) & ~15u) +
-           (unsigned)(warp * kRingWarpBytes);
-}
-
-// one interval's values at rows base, base + 1 and (when `third`) base + 2
-// of a column: `a` is the shared address of row base of that column
-__device__ __forceinline__ void ring_put3(unsigned a, float v1, float v2, float v3, bool third)
-{
-    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v1));
-    asm volatile("st.shared.f32 [%0+256], %1;" ::"r"(a), "f"(v2));
-    if (third) asm volatile("st.shared.f32 [%0+512], %1;" ::"r"(a), "f"(v3));
-}
-
-__device__ __forceinline__ void ring_put4(unsigned a, float4 v)
-{
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y),
-                 "f"(v.z), "f"(v.w));
-}
-
-// four consecutive slab words at shared address a (a stencil's mu rows)
-__device__ __forceinline__ float4 slab4(unsigned a)
-{
-    float4 v;
-    asm("ld.shared.f32 %0, [%4];\n\t"
-        "ld.shared.f32 %1, [%4+4];\n\t"
-        "ld.shared.f32 %2, [%4+8];\n\t"
-        "ld.shared.f32 %3, [%4+12];"
-        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "r"(a));
-    return v;
+    // row (kk >> 8) & 15 of the ring; colbase has no bits in 0xF00
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"((kk & 0xF00u) | colbase), "f"(v));
 }
 
 template <bool CLIP>
@@ -495,11 +461,6 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     unsigned kkv[2];
     int ofv[2], nit = 0;
     bool slow[2];
-    // rows 0, 1 and the shadow rows 16, 17 start cleared (one float4 each)
-    __syncwarp();
-    ring_put4(ring + 16u * lane, make_float4(0.f, 0.f, 0.f, 0.f));
-    ring_put4(ring + 16u * lane + 16u * kRingRowBytes, make_float4(0.f, 0.f, 0.f, 0.f));
-    __syncwarp();
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int m = g0 + lane + 32 * e;
@@ -558,21 +519,14 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     float2 t = make_float2(tv[0], tv[1]);
     const float2 d2 = make_float2(d, d), m1 = make_float2(-1.0f, -1.0f);
     unsigned kk0 = kkv[0], kk1 = kkv[1];
-    // shared byte addresses of the slots' highest stencil rows (slab2: the
-    // map form's second slab)
-    const unsigned sb = (unsigned)__cvta_generic_to_shared(slab);
-    const unsigned sb2 = MAP ? (unsigned)__cvta_generic_to_shared(slab2) : 0u;
-    const unsigned pm4 = 4u * (unsigned)Pm;
-    unsigned na0 = sb + 4u * (unsigned)ofv[0], na1 = sb + 4u * (unsigned)ofv[1];
-    unsigned nb0 = sb2 + 4u * (unsigned)ofv[0], nb1 = sb2 + 4u * (unsigned)ofv[1];
+    int of0 = ofv[0], of1 = ofv[1];
     const unsigned cb0 = ring + 4u * lane, cb1 = ring + 128u + 4u * lane;
     // lane (row rr = lane >> 2, quarter q = lane & 3) of a block sum adds the
     // float4 columns q + 4 ((i + rr) & 3), i = 0 .. 3 (no bank conflicts)
     const int rr = lane >> 2, qq = lane & 3;
     unsigned fa[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        fa[i] = ring + (unsigned)kRingRowBytes * rr + 16u * (qq + 4 * ((i + rr) & 3));
+    for (int i = 0; i < 4; ++i) fa[i] = ring + 256u * rr + 16u * (qq + 4 * ((i + rr) & 3));
     int r0 = 0;                       // first energy of the ring block not yet summed
     int lim = kRingBlock << 8;        // (r0 + 8) << 8
 
@@ -580,22 +534,10 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     auto flush = [&]() {
         __syncwarp();
         float4 v[4];
-        // rows 8-15 for odd blocks
+        // rows 8-15 for odd blocks (fa[i] < ring + 2048, so the OR adds)
         const unsigned hi = ((unsigned)r0 & 8u) << 8;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = ring_get4(fa[i] + hi);
-        if (hi == 0u && rr < 2) {
-            // rows 0 and 1: add the shadow rows 16 and 17, then clear both
-            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const unsigned sh = fa[i] + 16u * kRingRowBytes;
-                const float4 u = ring_get4(sh);
-                v[i].x += u.x; v[i].y += u.y; v[i].z += u.z; v[i].w += u.w;
-                ring_put4(fa[i], z);
-                ring_put4(sh, z);
-            }
-        }
+        for (int i = 0; i < 4; ++i) v[i] = ring_get4(fa[i] | hi);
         float2 s01 = __fadd2_rn(__fadd2_rn(make_float2(v[0].x, v[0].y), make_float2(v[0].z, v[0].w)),
                                 __fadd2_rn(make_float2(v[1].x, v[1].y), make_float2(v[1].z, v[1].w)));
         float2 s23 = __fadd2_rn(__fadd2_rn(make_float2(v[2].x, v[2].y), make_float2(v[2].z, v[2].w)),
@@ -618,23 +560,20 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         // node n + 3, loaded first so the loads overlap the evaluations (slots
         // past their last interval read the margin rows; those values only
         // reach virtual energies)
-        na0 += pm4;
-        na1 += pm4;
-        PPM_CHECK(na0 + 12u < sb + 4u * (unsigned)((A.nE + kSlabMargin) * Pm) &&
-                      na1 + 12u < sb + 4u * (unsigned)((A.nE + kSlabMargin) * Pm),
+        of0 += Pm;
+        of1 += Pm;
+        PPM_CHECK(of0 + 3 < (A.nE + kSlabMargin) * Pm && of1 + 3 < (A.nE + kSlabMargin) * Pm,
                   errp);
-        const float4 q0 = slab4(na0), q1 = slab4(na1);
-        const float2 r0v = make_float2(q0.x, q1.x), r1v = make_float2(q0.y, q1.y);
-        const float2 r2v = make_float2(q0.z, q1.z), r3v = make_float2(q0.w, q1.w);
+        const float *q0 = slab + of0, *q1 = slab + of1;
+        const float2 r0v = make_float2(q0[0], q1[0]), r1v = make_float2(q0[1], q1[1]);
+        const float2 r2v = make_float2(q0[2], q1[2]), r3v = make_float2(q0[3], q1[3]);
         float2 s0v, s1v, s2v, s3v;
         if (MAP) {
-            nb0 += pm4;
-            nb1 += pm4;
-            const float4 p0 = slab4(nb0), p1 = slab4(nb1);
-            s0v = make_float2(p0.x, p1.x);
-            s1v = make_float2(p0.y, p1.y);
-            s2v = make_float2(p0.z, p1.z);
-            s3v = make_float2(p0.w, p1.w);
+            const float *p0 = slab2 + of0, *p1 = slab2 + of1;
+            s0v = make_float2(p0[0], p1[0]);
+            s1v = make_float2(p0[1], p1[1]);
+            s2v = make_float2(p0[2], p1[2]);
+            s3v = make_float2(p0[3], p1[3]);
         }
         const float2 t2 = __fadd2_rn(t, d2);
         const float2 t3 = __fadd2_rn(t2, d2);
@@ -642,12 +581,15 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
         const float2 v2 = horner2<CLIP>(t2, K0, K1, K2, K3);
         const float2 v3 = horner2<CLIP>(t3, K0, K1, K2, K3);
         const bool th0 = t3.x < 1.0f, th1 = t3.y < 1.0f;
-        // rows of the interval's first energies (row 14 or 15 continues into
-        // the shadow rows)
-        ring_put3(cb0 + (kk0 & 0xF00u), v1.x, v2.x, v3.x, th0);
-        ring_put3(cb1 + (kk1 & 0xF00u), v1.y, v2.y, v3.y, th1);
-        kk0 += th0 ? 768u : 512u;
-        kk1 += th1 ? 768u : 512u;
+        const unsigned k3a = kk0 + 512u, k3b = kk1 + 512u;
+        ring_put(kk0, cb0, v1.x);
+        ring_put(kk1, cb1, v1.y);
+        ring_put(kk0 + 256u, cb0, v2.x);
+        ring_put(kk1 + 256u, cb1, v2.y);
+        if (th0) ring_put(k3a, cb0, v3.x);
+        if (th1) ring_put(k3b, cb1, v3.y);
+        kk0 = th0 ? k3a + 256u : k3a;
+        kk1 = th1 ? k3b + 256u : k3b;
         t = __fadd2_rn(t3, m1);
         if (th0) t.x += d;
         if (th1) t.y += d;
@@ -796,10 +738,11 @@ __global__ void __launch_bounds__(kSABlock, 2)
     const float inv_dlnE = (EMIS == 1) ? (float)(1.0 / A.dlnE) : 0.0f;
     const int Pm = A.nmu_pad;
     const bool inst_ok = status[it.b] == 0;
-    // this warp's ring (node-major walk): 16-byte aligned shared address
+    // this warp's ring (node-major walk): 4096-byte aligned shared address
     unsigned ring_w = 0;
     if (NODES)
-        ring_w = ring_base(sm + lay.ring, warp);
+        ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
+                 (unsigned)(warp * kRingWarpBytes);
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;
@@ -1007,10 +950,11 @@ __global__ void __launch_bounds__(NT, 1)
     const float pk0 = spk[0], pkl = spk[nE - 1];
     const float lz_safe = 1.25f - pk0;
     const bool sliding = en.sliding != 0;
-    // this warp's ring (node-major walk): 16-byte aligned shared address
+    // this warp's ring (node-major walk): 4096-byte aligned shared address
     unsigned ring_w = 0;
     if (NODES)
-        ring_w = ring_base(sm + lay.ring, warp);
+        ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
+                 (unsigned)(warp * kRingWarpBytes);
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;

@@ -312,3 +312,42 @@ def test_gradient_ascent_recovers_parameters(synth, atm, small_lens):
     err0 = torch.abs(start - truth)[0, [2, 5]]
     err1 = torch.abs(theta.detach() - truth)[0, [2, 5]]
     assert torch.all(err1 < 0.3 * err0), (err0, err1)
+
+
+def test_grad_full_size_against_the_oracle():
+    """The differentiated workload as the benchmark times it (1024 two-cap
+    instances at 128 x 128 elements, 128 phases, 256 energies, 300 channels,
+    default lens grid, one ppm_loglike_grad call over the batch) against the
+    FP64 oracle's forward-mode derivatives of the same instances, written by
+    tests/golden/make_grad_golden.py: every gradient component at 1e-3
+    relative (floor 1e-5 of the largest scale-weighted component) and three
+    seeded directional derivatives at 1e-3 relative."""
+    import json
+    import os
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from paper_2510_07764_gb300 import synth
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "grad_batch_full.json")))
+    w = synth.grad_batch()
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    ll, g = ctx.loglike_grad(dp, cnt, w.tau)
+    ctx.sync()
+    ll, g = ll.cpu().numpy(), g.cpu().numpy()
+    st = ctx.last_status.cpu().numpy()
+    assert len(gold["instances"]) >= 3
+    for rec in gold["instances"]:
+        b = rec["b"]
+        ref = np.asarray(rec["grad"])
+        assert st[b] == 0 and np.isfinite(rec["logL"])
+        d = w.counts[b * 128:(b + 1) * 128]             # 128 phases per instance
+        assert abs(ll[b] - rec["logL"]) <= 1e-3 * float(np.sum(np.abs(d))) + 1e-6 * abs(rec["logL"])
+        assert np.all(np.abs(g[b] - ref) <= grad_tol(ref)), \
+            (b, np.abs(g[b] - ref) / np.abs(ref))
+        for v, dv in zip(rec["directions"], rec["directional"]):
+            v = np.asarray(v)
+            gv = float(g[b] @ v)
+            assert abs(gv - dv) <= 1e-3 * abs(dv) + 1e-5 * float(np.sum(np.abs(ref * v))), \
+                (b, gv, dv)
