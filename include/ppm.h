@@ -338,7 +338,7 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
  * same setting.  The setting applies to later calls of the context.
  *
  * ppm_autotune runs the forward profile of (p, res) once per candidate
- * (phase_tile 16/32 x waves 8/16/32 x persistent 0/1, one untimed and one
+ * (phase_tile 16/32 x waves 8/16/32/64 x persistent 0/1, one untimed and one
  * timed pass each, synchronising `stream`), keeps the fastest, and returns
  * it in *best (ms = its time; walk is left as set).  Results do not depend
  * on the choice (the partial sums are added in a fixed order).

@@ -1077,7 +1077,7 @@ ppm_status ppm_autotune(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, v
     ppm_tiles top = cur;
     top.ms = INFINITY;
     ppm_status s = PPM_OK;
-    const int pts[] = {16, 32}, waves[] = {8, 16, 32}, pers[] = {0, 1};
+    const int pts[] = {16, 32}, waves[] = {8, 16, 32, 64}, pers[] = {0, 1};
     for (int a : pts)
         for (int wv : waves)
             for (int q : pers) {

@@ -25,16 +25,30 @@ struct RingGeo {
     double theta, st, ct, half, dphi, R, u, sq1u, cos_eta, sin_eta, logg, beta, gamma;
     double area, dt_obl, nu, sini, cosi, phic, mask_c, mask_ct, mask_st, mask_phi;
     double phi0, cap_c, cap_ct, cap_st;  // HEALPix mesh: first azimuth, emitter cap
-    int ok, has_mask, n_el;
+    // per-ring parts of the template points: the lens tables' u cell and
+    // weight, 1 / sqrt(1 - u), R / c
+    double tu, inv_sq, Rc;
+    int iu, ok, has_mask, n_el;
 };
 
-__device__ bool lens_lookup(const LensDev &L, double u, double cpsi, double *ca, double *lf)
+// The u (compactness) part of the bilinear lens lookups, the same for every
+// template point of a ring: cell iu and weight tu.
+__device__ __forceinline__ void lens_u(const LensDev &L, double u, int *iu, double *tu)
 {
-    double fu = (u - L.u_min) / (L.u_max - L.u_min) * (L.n_u - 1);
-    double fc = (cpsi - L.cpsi_min) / (L.cpsi_max - L.cpsi_min) * (L.n_cpsi - 1);
-    int iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    const double fu = (u - L.u_min) / (L.u_max - L.u_min) * (L.n_u - 1);
+    *iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    *tu = fu - *iu;
+}
+
+// C_alpha and LF at (u, cpsi), bilinear; the u cell and weight come from
+// lens_u, the cpsi position is (cpsi - cpsi_min) * sc with
+// sc = (n_cpsi - 1) / (cpsi_max - cpsi_min).  False where a corner is invalid.
+__device__ bool lens_lookup_u(const LensDev &L, int iu, double tu, double cpsi, double sc,
+                              double *ca, double *lf)
+{
+    double fc = (cpsi - L.cpsi_min) * sc;
     int ic = min(max((int)floor(fc), 0), L.n_cpsi - 2);
-    double tu = fu - iu, tc = fc - ic;
+    double tc = fc - ic;
     size_t k00 = (size_t)iu * L.n_cpsi + ic, k10 = k00 + L.n_cpsi;
     double a00 = L.Ca[k00], a01 = L.Ca[k00 + 1], a10 = L.Ca[k10], a11 = L.Ca[k10 + 1];
     if (isnan(a00) || isnan(a01) || isnan(a10) || isnan(a11)) return false;
@@ -44,14 +58,14 @@ __device__ bool lens_lookup(const LensDev &L, double u, double cpsi, double *ca,
     return true;
 }
 
-__device__ double td_lookup(const LensDev &L, double u, double ca)
+// TD at (u, ca), bilinear, ca clamped to its grid; sc = (n_calpha - 1) /
+// (ca_max - ca_min)
+__device__ double td_lookup_u(const LensDev &L, int iu, double tu, double ca, double sc)
 {
     ca = fmin(fmax(ca, L.ca_min), L.ca_max);
-    double fu = (u - L.u_min) / (L.u_max - L.u_min) * (L.n_u - 1);
-    double fc = (ca - L.ca_min) / (L.ca_max - L.ca_min) * (L.n_calpha - 1);
-    int iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    double fc = (ca - L.ca_min) * sc;
     int ic = min(max((int)floor(fc), 0), L.n_calpha - 2);
-    double tu = fu - iu, tc = fc - ic;
+    double tc = fc - ic;
     size_t k00 = (size_t)iu * L.n_calpha + ic, k10 = k00 + L.n_calpha;
     return (1.0 - tu) * ((1.0 - tc) * L.TD[k00] + tc * L.TD[k00 + 1]) +
            tu * ((1.0 - tc) * L.TD[k10] + tc * L.TD[k10 + 1]);
@@ -238,6 +252,9 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
             G.n_el = n_el; G.dphi = dphi; G.phi0 = phi0;
             G.cap_c = c_zt; G.cap_ct = c_tc; G.cap_st = s_tc;
             G.R = R; G.u = u; G.sq1u = sq;
+            lens_u(L, u, &G.iu, &G.tu);
+            G.inv_sq = 1.0 / sq;
+            G.Rc = R / kC;
             G.cos_eta = 1.0 / sf;
             G.sin_eta = f / sf;
             G.logg = logg;
@@ -287,18 +304,28 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
     const size_t tbase = (size_t)g * 4 * (n_fp + 1);
     if (G.ok) {
         const LensDev Lc = L;
+        // FP64 is scarce on this GPU: the per-ring parts of the lookups are
+        // hoisted and the per-point divisions become products with
+        // reciprocals taken once (results change at the level of FP64 rounding)
+        const int iu = G.iu;
+        const double tu = G.tu;
+        const double sc_c = (Lc.n_cpsi - 1) / (Lc.cpsi_max - Lc.cpsi_min);
+        const double sc_a = (Lc.n_calpha - 1) / (Lc.ca_max - Lc.ca_min);
+        const double inv_nfp = 1.0 / (double)n_fp;
         for (int i = threadIdx.x; i < n_fp; i += blockDim.x) {
+            const double x = (double)i * inv_nfp;  // i / n_fp
             double sphi, cphi;
-            sincospi(2.0 * (double)i / (double)n_fp, &sphi, &cphi);
+            sincospi(2.0 * x, &sphi, &cphi);
             // step 2: cos psi
             const double cpsi = G.sini * G.st * cphi + G.cosi * G.ct;
             bool vis = false;
             double ca, lf;
             // step 3: lens table; beyond its cos psi range the point is invisible
-            if (cpsi >= Lc.cpsi_min && lens_lookup(Lc, G.u, cpsi, &ca, &lf)) {
+            if (cpsi >= Lc.cpsi_min && lens_lookup_u(Lc, iu, tu, cpsi, sc_c, &ca, &lf)) {
                 const double sa = sqrt(fmax(0.0, 1.0 - ca * ca));
-                const double sp = sqrt(fmax(0.0, 1.0 - cpsi * cpsi));
-                const double ratio = sp > 1e-12 ? sa / sp : sqrt(lf);
+                const double sp2 = fmax(0.0, 1.0 - cpsi * cpsi);
+                // sin(alpha) / sin(psi); its limit sqrt(LF) where sin(psi) < 1e-12
+                const double ratio = sp2 > 1e-24 ? sa * rsqrt(sp2) : sqrt(lf);
                 // step 4: Eq. sigma_relation
                 const double csig = ca * G.cos_eta +
                                     ratio * G.sin_eta * (G.cosi * G.st - G.sini * G.ct * cphi);
@@ -306,12 +333,13 @@ __global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L,
                 if (csig >= 0.0) {
                     vis = true;
                     const double cxi = -ratio * G.sini * sphi;
-                    const double delta = 1.0 / (G.gamma * (1.0 - G.beta * cxi));
+                    const double den = G.gamma * (1.0 - G.beta * cxi);  // 1 / delta
+                    const double delta = 1.0 / den;
                     const double mu = delta * csig;
                     sF[i] = G.sq1u * delta * delta * delta * mu * lf * G.gamma * G.area;
-                    sZ[i] = 1.0 / (delta * G.sq1u);
-                    const double dt = G.R / kC * td_lookup(Lc, G.u, ca) + G.dt_obl;
-                    sPh[i] = (double)i / (double)n_fp + G.nu * dt;
+                    sZ[i] = den * G.inv_sq;                             // 1 / (delta sqrt(1-u))
+                    const double dt = G.Rc * td_lookup_u(Lc, iu, tu, ca, sc_a) + G.dt_obl;
+                    sPh[i] = x + G.nu * dt;
                     sMu[i] = mu;
                 }
             }

@@ -113,33 +113,65 @@ __device__ __forceinline__ Dual dsqrt(const Dual &a)
     const double s = sqrt(a.v);
     return chain(a, s, s > 0.0 ? 0.5 / s : 0.0);
 }
+// 1 / sqrt(a) for a > 0, derivative -0.5 a^(-3/2) (no FP64 division)
+__device__ __forceinline__ Dual drsqrt(const Dual &a)
+{
+    const double r = rsqrt(a.v);
+    return chain(a, r, -0.5 * r * r * r);
+}
+// sqrt(a) for a >= 0 through one reciprocal square root (derivative 0 at 0)
+__device__ __forceinline__ Dual dsqrt_r(const Dual &a)
+{
+    if (!(a.v > 0.0)) return chain(a, 0.0, 0.0);
+    const double r = rsqrt(a.v);
+    return chain(a, a.v * r, 0.5 * r);
+}
 __device__ __forceinline__ Dual dsin(const Dual &a) { return chain(a, sin(a.v), cos(a.v)); }
 __device__ __forceinline__ Dual dcos(const Dual &a) { return chain(a, cos(a.v), -sin(a.v)); }
 __device__ __forceinline__ Dual dlog(const Dual &a) { return chain(a, log(a.v), 1.0 / a.v); }
 __device__ __forceinline__ Dual dabs(const Dual &a) { return a.v < 0.0 ? -a : a; }
 
-// bilinear interpolant on a uniform grid and its two partial derivatives
+// Bilinear interpolant on a uniform grid and its two partial derivatives.
+// The x (compactness) cell ix and weight tx are taken once per ring, and the
+// grid scales sx = (nx - 1) / (x1 - x0) and sy likewise are precomputed: no
+// FP64 division per point.
 struct Bilin {
     double v, dx, dy;
     bool nan;
 };
-__device__ __forceinline__ Bilin bilin(const double *T, int nx, int ny, double x0, double x1,
-                                       double y0, double y1, double x, double y)
+__device__ __forceinline__ Bilin bilin_u(const double *T, int ny, int ix, double tx, double sx,
+                                         double y0, double sy, double y)
 {
-    const double hx = (x1 - x0) / (nx - 1), hy = (y1 - y0) / (ny - 1);
-    const double fx = (x - x0) / (x1 - x0) * (nx - 1);
-    const double fy = (y - y0) / (y1 - y0) * (ny - 1);
-    const int ix = min(max((int)floor(fx), 0), nx - 2);
+    const double fy = (y - y0) * sy;
     const int iy = min(max((int)floor(fy), 0), ny - 2);
-    const double tx = fx - ix, ty = fy - iy;
+    const double ty = fy - iy;
     const size_t k00 = (size_t)ix * ny + iy, k10 = k00 + ny;
     const double a00 = T[k00], a01 = T[k00 + 1], a10 = T[k10], a11 = T[k10 + 1];
     Bilin b;
     b.nan = isnan(a00) || isnan(a01) || isnan(a10) || isnan(a11);
     b.v = (1.0 - tx) * ((1.0 - ty) * a00 + ty * a01) + tx * ((1.0 - ty) * a10 + ty * a11);
-    b.dx = ((1.0 - ty) * (a10 - a00) + ty * (a11 - a01)) / hx;
-    b.dy = ((1.0 - tx) * (a01 - a00) + tx * (a11 - a10)) / hy;
+    b.dx = ((1.0 - ty) * (a10 - a00) + ty * (a11 - a01)) * sx;
+    b.dy = ((1.0 - tx) * (a01 - a00) + tx * (a11 - a10)) * sy;
     return b;
+}
+
+// per-ring constants of the template points' lookups
+struct LensU {
+    int iu;
+    double tu, su, sc, sa, inv_nfp;
+};
+
+__device__ __forceinline__ LensU lens_u(const LensDev &L, double u, int n_fp)
+{
+    LensU U;
+    U.su = (L.n_u - 1) / (L.u_max - L.u_min);
+    const double fu = (u - L.u_min) * U.su;
+    U.iu = min(max((int)floor(fu), 0), L.n_u - 2);
+    U.tu = fu - U.iu;
+    U.sc = (L.n_cpsi - 1) / (L.cpsi_max - L.cpsi_min);
+    U.sa = (L.n_calpha - 1) / (L.ca_max - L.ca_min);
+    U.inv_nfp = 1.0 / (double)n_fp;
+    return U;
 }
 
 __device__ __forceinline__ Dual lift2(const Bilin &b, const Dual &x, const Dual &y)
@@ -153,6 +185,7 @@ __device__ __forceinline__ Dual lift2(const Bilin &b, const Dual &x, const Dual 
 
 struct RingDual {
     Dual st, ct, R, u, sq1u, cos_eta, sin_eta, beta, gamma, area, dt_obl, sini, cosi, logg, half;
+    Dual inv_sq, Rc;  // 1 / sqrt(1 - u), R / c
     double nu, phic;
     int ok;
 };
@@ -195,6 +228,8 @@ __device__ void ring_setup(const Params &p, int b, int sidx, int r, int n_theta,
     const Dual f = -2.0 * o2 * Re * ct * st / (R * sq);
     const Dual nf = dsqrt(1.0 + f * f);
     G.R = R; G.u = u; G.sq1u = sq;
+    G.inv_sq = 1.0 / sq;
+    G.Rc = R * (1.0 / kC);
     G.cos_eta = 1.0 / nf;
     G.sin_eta = f / nf;
     Dual gg = g0;
@@ -222,37 +257,40 @@ __device__ void ring_setup(const Params &p, int b, int sidx, int r, int n_theta,
     G.ok = half.v > 0.0;
 }
 
-// tangents of (F, z, mu, phi_o) at fine point i, contracted with the adjoints
-__device__ __forceinline__ void point_tangent(const RingDual &G, const LensDev &L, int i, int n_fp, double gF,
-                              double gZ, double gM, double gP, double *acc)
+// tangents of (F, z, mu, phi_o) at fine point i, contracted with the adjoints.
+// FP64 is scarce on this GPU: the lookups' per-ring parts come from U and
+// the per-point divisions are products with reciprocals (results change at
+// the level of FP64 rounding).
+__device__ __forceinline__ void point_tangent(const RingDual &G, const LensDev &L, const LensU &U,
+                                              int i, double gF, double gZ, double gM, double gP,
+                                              double *acc)
 {
     double sphi, cphi;
-    sincospi(2.0 * (double)i / (double)n_fp, &sphi, &cphi);
+    sincospi(2.0 * ((double)i * U.inv_nfp), &sphi, &cphi);
     const Dual cpsi = G.sini * G.st * cphi + G.cosi * G.ct;
-    const Bilin bc = bilin(L.Ca, L.n_u, L.n_cpsi, L.u_min, L.u_max, L.cpsi_min, L.cpsi_max,
-                           G.u.v, cpsi.v);
-    const Bilin bl = bilin(L.LF, L.n_u, L.n_cpsi, L.u_min, L.u_max, L.cpsi_min, L.cpsi_max,
-                           G.u.v, cpsi.v);
+    const Bilin bc = bilin_u(L.Ca, L.n_cpsi, U.iu, U.tu, U.su, L.cpsi_min, U.sc, cpsi.v);
+    const Bilin bl = bilin_u(L.LF, L.n_cpsi, U.iu, U.tu, U.su, L.cpsi_min, U.sc, cpsi.v);
     if (bc.nan || bl.nan) return;  // cannot happen for a point the forward saw as visible
     const Dual ca = lift2(bc, G.u, cpsi);
     const Dual lf = lift2(bl, G.u, cpsi);
-    const Dual sa = dsqrt(1.0 - ca * ca);
-    const Dual sp = dsqrt(1.0 - cpsi * cpsi);
-    const Dual ratio = sp.v > 1e-12 ? sa / sp : dsqrt(lf);
+    const Dual sa = dsqrt_r(1.0 - ca * ca);
+    const Dual sp2 = 1.0 - cpsi * cpsi;
+    // sin(alpha) / sin(psi); its limit sqrt(LF) where sin(psi) < 1e-12
+    const Dual ratio = sp2.v > 1e-24 ? sa * drsqrt(sp2) : dsqrt(lf);
     const Dual csig = ca * G.cos_eta + ratio * G.sin_eta * (G.cosi * G.st - G.sini * G.ct * cphi);
     const Dual cxi = -(ratio * G.sini * sphi);
-    const Dual delta = 1.0 / (G.gamma * (1.0 - G.beta * cxi));
+    const Dual den = G.gamma * (1.0 - G.beta * cxi);  // 1 / delta
+    const Dual delta = 1.0 / den;
     const Dual mu = delta * csig;
     const Dual F = G.sq1u * delta * delta * delta * mu * lf * G.gamma * G.area;
-    const Dual z = 1.0 / (delta * G.sq1u);
+    const Dual z = den * G.inv_sq;                     // 1 / (delta sqrt(1 - u))
     // time delay: TD bilinear in (u, cos alpha), cos alpha clamped to the table
     Dual cac = ca;
     if (ca.v < L.ca_min) cac = dconst(L.ca_min);
     if (ca.v > L.ca_max) cac = dconst(L.ca_max);
-    const Bilin bt = bilin(L.TD, L.n_u, L.n_calpha, L.u_min, L.u_max, L.ca_min, L.ca_max, G.u.v,
-                           cac.v);
+    const Bilin bt = bilin_u(L.TD, L.n_calpha, U.iu, U.tu, U.su, L.ca_min, U.sa, cac.v);
     const Dual td = lift2(bt, G.u, cac);
-    const Dual dt = G.R / kC * td + G.dt_obl;
+    const Dual dt = G.Rc * td + G.dt_obl;
 #pragma unroll
     for (int d = 0; d < ND; ++d)
         acc[d] += gF * F.d[d] + gZ * z.d[d] + gM * mu.d[d] + gP * G.nu * dt.d[d];
@@ -345,8 +383,9 @@ __global__ void __launch_bounds__(kTBlock) k_template_bwd(Params p, PlanDev plan
     __syncthreads();
     double acc[ND] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (G.ok) {
+        const LensU U = lens_u(L, G.u.v, n_fp);
         for (int i = tid; i < n_fp; i += blockDim.x)
-            if (vis[i]) point_tangent(G, L, i, n_fp, adj[0][i], adj[1][i], adj[2][i], adj[3][i], acc);
+            if (vis[i]) point_tangent(G, L, U, i, adj[0][i], adj[1][i], adj[2][i], adj[3][i], acc);
     }
 #pragma unroll
     for (int d = 0; d < ND; ++d) {

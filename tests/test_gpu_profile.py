@@ -244,3 +244,24 @@ def test_phase_sub_samples_match_oracle(orc, synth, atm, small_lens, S):
     Ft, st = gpu_profile(w)
     assert st[0] == 0
     assert max_rel(Ft, orc.profile(w)) < 1e-3
+
+
+@pytest.mark.parametrize("n_fp", [8, 1024])
+def test_template_resolution_limits(orc, synth, atm, small_lens, n_fp):
+    """The smallest and the largest template resolution the library accepts
+    (8 and 1024 fine phases per ring; the paper uses 192) against the oracle,
+    and the first values outside the range are rejected."""
+    import paper_2510_07764_gb300 as ppm
+    from gpu_helpers import context
+    w = synth.atm_two_spot(n_theta=10, n_phi=20, n_phase=24, n_E=40, n_chan=8, atm=atm,
+                           lens=small_lens)
+    w.inst.n_fp = n_fp
+    got, st = gpu_profile(w)
+    assert st[0] == 0
+    assert max_rel(got, orc.profile(w)) < TOL_ATM
+    ctx = context(w)
+    bad = w.inst.replace()
+    bad.n_fp = 7 if n_fp == 8 else 1025
+    with pytest.raises(ppm.PPMError) as e:
+        ctx.profile(ppm.DeviceParams(bad))
+    assert e.value.status == ppm.PPM_EINVAL
