@@ -127,7 +127,11 @@ __device__ __forceinline__ long long healpix_first_pixel(int N, int i)
     return 12LL * n * n - 2 * k * (k + 1);
 }
 
-__global__ void __launch_bounds__(256) k_ring(Params p, PlanDev plan, LensDev L, AtmDev A,
+// 128 threads per ring: at about 100 registers a thread four ring blocks fit
+// on an SM, so that one block's FP64 set-up overlaps the others' points
+constexpr int kRingThreads = 128;
+
+__global__ void __launch_bounds__(kRingThreads, 4) k_ring(Params p, PlanDev plan, LensDev L, AtmDev A,
                                              RingRec *recs, float *tmpl, float *elems,
                                              int *status, unsigned *err,
                                              unsigned long long *triples, int nE, float2 *elemx)
@@ -507,7 +511,7 @@ cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L, 
                         unsigned long long *triples, int nE, cudaStream_t st, float2 *elemx)
 {
     if (plan.total_rings <= 0) return cudaSuccess;
-    k_ring<<<plan.total_rings, 256, 0, st>>>(p, plan, L, A, recs, tmpl, elems, status, err,
+    k_ring<<<plan.total_rings, kRingThreads, 0, st>>>(p, plan, L, A, recs, tmpl, elems, status, err,
                                              triples, nE, elemx);
     return cudaGetLastError();
 }
