@@ -18,7 +18,7 @@ namespace ppm {
 namespace {
 
 constexpr int ND = 5;  // tangents: M, R_e, incl, colat, zeta
-constexpr int kTBlock = 128;
+constexpr int kTBlock = 64;  // four blocks per SM at 255 registers: their serial set-ups overlap
 
 struct Dual {
     double v;
