@@ -729,6 +729,7 @@ struct Work {
     // gradient only
     float *lambda, *Aadj, *ringadj;
     double *ring_grad, *row_sums;
+    int *used;  // temperature maps: which work slots wrote a partial tile
 };
 }  // namespace
 
@@ -744,7 +745,9 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     const size_t o_tmpl = take((size_t)hp.total_rings * 4 * (n_fp + 1) * sizeof(float));
     const size_t o_elems = take(hp.total_elems * sizeof(float));
     const size_t o_elemx = take(p->logT_map ? hp.total_elems * sizeof(float2) : 0);
-    const size_t o_part = take((size_t)hp.items.size() * hp.pt * ctx->nEpad * sizeof(float));
+    const size_t parts = p->logT_map ? 2 : 1;
+    const size_t o_part = take(parts * hp.items.size() * hp.pt * ctx->nEpad * sizeof(float));
+    const size_t o_used = take(parts > 1 ? parts * hp.items.size() * sizeof(int) : 0);
     const size_t o_ft = take(need_ft ? (size_t)hp.total_rows * ctx->E.size() * sizeof(float) : 0);
     const size_t o_ll = take(need_ft ? (size_t)hp.total_rows * ct * sizeof(double) : 0);
     const size_t rows = grad ? (size_t)hp.total_rows : 0, rings = grad ? hp.total_rings : 0;
@@ -764,6 +767,7 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     w->elems = reinterpret_cast<float *>(base + o_elems);
     w->elemx = p->logT_map ? reinterpret_cast<float2 *>(base + o_elemx) : nullptr;
     w->partials = reinterpret_cast<float *>(base + o_part);
+    w->used = parts > 1 ? reinterpret_cast<int *>(base + o_used) : nullptr;
     w->Ft = reinterpret_cast<float *>(base + o_ft);
     w->row_ll = reinterpret_cast<double *>(base + o_ll);
     w->lambda = reinterpret_cast<float *>(base + o_lam);
@@ -797,6 +801,8 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
         d + b_inst + b_items + align256(hp.tiles.size() * sizeof(int2)));
     plan->queue = ctx->tile_persistent ? ctx->d_queue : nullptr;
     plan->err = ctx->d_err;
+    plan->parts = 1;
+    plan->used = nullptr;
     const ppm_lens_spec &s = ctx->lens;
     L->u_min = s.u_min; L->u_max = s.u_max; L->n_u = s.n_u;
     L->cpsi_min = s.cpsi_min; L->cpsi_max = s.cpsi_max; L->n_cpsi = s.n_cpsi;
@@ -829,6 +835,8 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
     AtmDev A;
     EnergyDev en;
     fill_devs(ctx, p, res->n_fp, &P, &plan, &L, &A, &en);
+    plan.parts = p->logT_map ? 2 : 1;
+    plan.used = w->used;
     // shared-memory budget of the shift-and-add kernel
     const size_t smem = shift_add_smem_bytes(P, plan, A, en, ctx->plan.n_phi_max);
     if (smem > ctx->smem_optin)
@@ -1403,6 +1411,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     plan.order = nullptr;
     plan.queue = nullptr;
     plan.err = ctx->d_err;
+    plan.parts = 1;
+    plan.used = nullptr;
     const ppm_lens_spec &ls = ctx->lens;
     LensDev Ld;
     Ld.u_min = ls.u_min; Ld.u_max = ls.u_max; Ld.n_u = ls.n_u;

@@ -124,6 +124,12 @@ struct PlanDev {
     const int *order;        // launch order of the items (largest first); null = identity
     int *queue;              // persistent schedule: next-entry counter (null = one block per item)
     unsigned *err;           // device error word (kErr* bits)
+    // work slots per item: 1, or 2 for temperature maps (slot 0: each ring's
+    // first logT cell, slot 1: its other cells), each with its own partial
+    // tile; used[slot] (null with one slot) says whether the slot's block
+    // wrote its partial tile (it writes nothing when it has no work)
+    int parts;
+    int *used;
 };
 
 // Energy-side arrays (device).

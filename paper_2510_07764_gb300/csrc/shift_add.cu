@@ -920,12 +920,29 @@ __global__ void __launch_bounds__(NT, 1)
             sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
             sm[lay.slab2 + A.nE * A.nmu_pad + i] = 0.0f;
         }
-    const int item_id = plan.order ? plan.order[blockIdx.x] : (int)blockIdx.x;
+    // work slot: item, and part (0: each ring's first logT cell, 1: its
+    // other cells; one part for the analytic blackbody)
+    const int parts = plan.parts, part = (int)blockIdx.x % parts;
+    const int item_id = plan.order ? plan.order[blockIdx.x / parts] : (int)blockIdx.x / parts;
+    const int slot = item_id * parts + part;
     const Item it = plan.items[item_id];
     const InstPlan ip = plan.inst[it.b];
     const int n_fp = plan.n_fp, pt = plan.pt, nEpad = en.nEpad, nE = en.nE;
     const int nch = nEpad / kEC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        // a slot without work writes no partial tile (the reduction skips it)
+        bool work = false;
+        if (status[it.b] == 0)
+            for (int r = it.r0; r < it.r1 && !work; ++r) {
+                const RingRec *rq = recs + ip.ring0 + it.spot * ip.n_theta + r;
+                work = rq->visible && (part == 0 || (EMIS == 1 && rq->tT > 1));
+            }
+        if (!work) {
+            if (tid == 0 && plan.used) plan.used[slot] = 0;
+            return;
+        }
+    }
     float *Fblk = sm + lay.fblk;
     float *spk = sm + lay.pk, *sE = sm + lay.E, *sE3 = sm + lay.E3;
     float *cs = sm + lay.cs, *cw = sm + lay.cw;
@@ -965,8 +982,10 @@ __global__ void __launch_bounds__(NT, 1)
         __syncthreads();
         for (int i = tid; i < 4 * (n_fp + 1); i += blockDim.x)
             sm[lay.tmpl + i] = tmpl[(size_t)ring * 4 * (n_fp + 1) + i];
+        // this slot's cells of the ring: the first, or the others
         const int c_lo = EMIS == 1 ? rp->iT : 0, c_n = EMIS == 1 ? rp->tT : 1;
-        for (int cell = c_lo; cell < c_lo + c_n; ++cell) {
+        const int c_a = part == 0 ? c_lo : c_lo + 1, c_b = part == 0 ? c_lo + 1 : c_lo + c_n;
+        for (int cell = c_a; cell < c_b; ++cell) {
             __syncthreads();  // previous cell (or ring) done with the staged data
             if (EMIS == 1) {
                 // the cell's two logT planes, interpolated linearly in logg
@@ -1114,8 +1133,9 @@ __global__ void __launch_bounds__(NT, 1)
         }
     }
     __syncthreads();
-    float *dst = partials + (size_t)item_id * pt * nEpad;
+    float *dst = partials + (size_t)slot * pt * nEpad;
     for (int i = tid; i < it.nj * nEpad; i += blockDim.x) dst[i] = Fblk[i];
+    if (tid == 0 && plan.used) plan.used[slot] = 1;
 }
 
 MapLayout map_layout(const Params &p, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
@@ -1168,7 +1188,28 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const size_t stride4 = (size_t)pt * nEpad / 4;
     const int n_sub = ip.n_sub;
-    if (4 * k4 < nEpad) {
+    if (plan.parts > 1) {
+        // several work slots per item (temperature maps): warp w adds the
+        // written slots w, w + 8, ... of the tile's items, reading 32 flags
+        // per ballot (every lane takes part; the loop bounds are the warp's)
+        // and the set ones in increasing slot order
+        const bool kin = 4 * k4 < nEpad;
+        const float4 *base = reinterpret_cast<const float4 *>(partials + (size_t)jl0 * nEpad) + k4;
+        const int lane = threadIdx.x & 31;
+        const int s0 = rng.x * plan.parts + warp, s1 = rng.y * plan.parts;
+        for (int c = s0; c < s1; c += 8 * 32) {
+            const int ql = c + 8 * lane;
+            unsigned set = __ballot_sync(0xffffffffu, ql < s1 && plan.used[ql] != 0);
+            while (set) {
+                const int q = c + 8 * (__ffs(set) - 1);
+                set &= set - 1;
+                for (int sub = 0; sub < n_sub && kin; ++sub) {
+                    const float4 a = base[(size_t)q * stride4 + (size_t)sub * nEpad / 4];
+                    acc.x += a.x; acc.y += a.y; acc.z += a.z; acc.w += a.w;
+                }
+            }
+        }
+    } else if (4 * k4 < nEpad) {
         const float4 *base = reinterpret_cast<const float4 *>(partials + (size_t)jl0 * nEpad) + k4;
         int i = rng.x + warp;
         for (; i + 8 < rng.y; i += 16) {
@@ -1245,8 +1286,8 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
             cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)bytes);
             if (r != cudaSuccess) return r;
-            kern<<<plan.n_items, nt, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, elemx,
-                                                  status, partials);
+            kern<<<plan.n_items * plan.parts, nt, bytes, st>>>(p, plan, A, en, lay, recs, tmpl,
+                                                               elems, elemx, status, partials);
             return cudaGetLastError();
         };
         if (p.emission == 0) return go(k_shift_add_map<0, false>, kSABlock);
