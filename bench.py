@@ -95,9 +95,10 @@ def parse(argv=None):
                     help="capture one step in a CUDA graph and time its replays")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the shift-and-add tiles with ppm_autotune before timing")
-    ap.add_argument("--walk", type=int, choices=[0, 1], default=0,
+    ap.add_argument("--walk", type=int, choices=[0, 1, 2], default=0,
                     help="energy walk of the atmosphere shift-and-add: 0 node-major where "
-                         "the energy grid allows it, 1 energy walk (ppm_tiles.walk)")
+                         "the energy grid allows it, 1 energy walk, 2 moment walk where it "
+                         "applies (ppm_tiles.walk)")
     return ap.parse_args(argv)
 
 

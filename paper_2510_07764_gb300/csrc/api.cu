@@ -96,7 +96,8 @@ struct ppm_ctx {
     int tile_pt = 0;          // output phases per item: 0 = automatic, 16 or 32
     int tile_waves = 16;      // target waves of 2 blocks per SM (sets the ring-group size)
     int tile_persistent = 0;  // 1: persistent blocks take items from a queue
-    int tile_walk = 0;        // 0: node-major walk where it applies, 1: energy walk
+    int tile_walk = 0;        // 0: node-major walk where it applies, 1: energy walk,
+                              // 2: moment walk where it applies (node-major elsewhere)
     int *d_queue = nullptr;
     // plan
     std::vector<int> plan_key;
@@ -500,7 +501,25 @@ static float walk_step_of(const ppm_ctx *ctx)
 // (spots and temperature maps alike)
 static bool node_walk_on(const ppm_ctx *ctx, const ppm_params *p, float step)
 {
-    return p->emission == 1 && ctx->tile_walk == 0 && step > 0.0f;
+    return p->emission == 1 && (ctx->tile_walk == 0 || ctx->tile_walk == 2) && step > 0.0f;
+}
+
+// the forward atmosphere shift-and-add of this call takes the moment walk:
+// spot emission, an interpolant linear in the table's node values (every
+// strategy but the clipped one), energies inside the table
+static bool moment_walk_on(const ppm_ctx *ctx, const ppm_params *p)
+{
+    return p->emission == 1 && ctx->tile_walk == 2 && !p->logT_map && ctx->interp != kInterpB &&
+           sliding_of(ctx);
+}
+
+// relative table nodes of a moment-walk group: the observed energies' span
+// in table nodes plus the stencil margins
+static int moment_rows(const ppm_ctx *ctx)
+{
+    const int nE = (int)ctx->E.size();
+    if (nE < 1) return 8;
+    return (int)std::ceil((double)pk_of(ctx, nE - 1) - (double)pk_of(ctx, 0)) + 8;
 }
 
 static ppm_status refresh_energies(ppm_ctx *ctx)
@@ -603,7 +622,7 @@ static ppm_status make_plan(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
     key.push_back(res->grid);
     key.push_back(res->phase_sub);
     key.push_back(p->logT_map ? 1 : 0);
-    const bool node = node_walk_on(ctx, p, ctx->walk_step);
+    const bool node = node_walk_on(ctx, p, ctx->walk_step) || moment_walk_on(ctx, p);
     key.push_back(node ? 1 : 0);
     for (int b = 0; b < B; ++b) {
         key.push_back(res->n_theta[b]);
@@ -819,6 +838,8 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     en->sliding = ctx->sliding;
     en->step = node_walk_on(ctx, p, ctx->walk_step) ? ctx->walk_step : 0.0f;
     en->inv_step = en->step > 0.0f ? 1.0f / en->step : 0.0f;
+    en->moments = moment_walk_on(ctx, p) ? 1 : 0;
+    en->nmom = moment_rows(ctx);
 }
 
 static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *res, float *Ft,
@@ -838,7 +859,7 @@ static ppm_status run_profile(ppm_ctx *ctx, const ppm_params *p, const ppm_res *
     plan.parts = p->logT_map ? 2 : 1;
     plan.used = w->used;
     // shared-memory budget of the shift-and-add kernel
-    const size_t smem = shift_add_smem_bytes(P, plan, A, en, ctx->plan.n_phi_max);
+    const size_t smem = shift_add_smem_bytes(P, plan, A, en, ctx->plan.n_phi_max, ctx->smem_optin);
     if (smem > ctx->smem_optin)
         return fail(ctx, PPM_EINVAL, "shared memory need %zu B exceeds %zu B (n_phi, nE too large)",
                     smem, ctx->smem_optin);
@@ -1051,7 +1072,7 @@ ppm_status ppm_set_tiles(ppm_ctx *ctx, const ppm_tiles *t)
     if (t->waves < 1 || t->waves > 256) return fail(ctx, PPM_EINVAL, "waves must be in [1, 256]");
     if (t->persistent != 0 && t->persistent != 1)
         return fail(ctx, PPM_EINVAL, "persistent must be 0 or 1");
-    if (t->walk != 0 && t->walk != 1) return fail(ctx, PPM_EINVAL, "walk must be 0 or 1");
+    if (t->walk < 0 || t->walk > 2) return fail(ctx, PPM_EINVAL, "walk must be 0, 1 or 2");
     ctx->tile_pt = t->phase_tile;
     ctx->tile_waves = t->waves;
     ctx->tile_persistent = t->persistent;
@@ -1325,7 +1346,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
                  res->n_phase[b] * res->phase_sub * (double)ctx->E.size();
     }
     const float step = walk_step_of(ctx);
-    int pt = (node_walk_on(ctx, p, step) || T32 < (long long)ctx->sm_count * 16) ? 16 : kPT;
+    int pt = (node_walk_on(ctx, p, step) || moment_walk_on(ctx, p) ||
+              T32 < (long long)ctx->sm_count * 16) ? 16 : kPT;
     if (ctx->tile_pt == 16 || ctx->tile_pt == 32) pt = ctx->tile_pt;
     if (const char *env = getenv("PPM_PHASE_TILE")) {
         const int v = atoi(env);
@@ -1429,11 +1451,13 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     en.nE = nE; en.nEpad = L.nEpad; en.sliding = sliding;
     en.step = node_walk_on(ctx, p, step) ? step : 0.0f;
     en.inv_step = en.step > 0.0f ? 1.0f / en.step : 0.0f;
+    en.moments = moment_walk_on(ctx, p) ? 1 : 0;
+    en.nmom = moment_rows(ctx);
     en.E = reinterpret_cast<const float *>(dev + L.o_E);
     en.E3 = reinterpret_cast<const float *>(dev + L.o_E3);
     en.pk = reinterpret_cast<const float *>(dev + L.o_pk);
     en.invE = reinterpret_cast<const float *>(dev + L.o_invE);
-    const size_t smem_need = shift_add_smem_bytes(P, plan, A, en, L.n_phi_max);
+    const size_t smem_need = shift_add_smem_bytes(P, plan, A, en, L.n_phi_max, ctx->smem_optin);
     if (smem_need > ctx->smem_optin)
         return fail(ctx, PPM_EINVAL, "shared memory need %zu B exceeds %zu B", smem_need,
                     ctx->smem_optin);
@@ -1449,7 +1473,8 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     PPM_CUDA(cudaMemsetAsync(dev + L.o_status, 0, sizeof(int) * p->B, st), "clear status");
     PPM_CUDA(launch_ring(P, plan, Ld, A, recs, tmpl, el, status, ctx->d_err, nullptr, nE, st),
              "ring kernel");
-    PPM_CUDA(launch_shift_add(P, plan, A, en, recs, tmpl, el, status, part, L.n_phi_max, st),
+    PPM_CUDA(launch_shift_add(P, plan, A, en, recs, tmpl, el, status, part, L.n_phi_max, st, 0,
+                              nullptr, ctx->smem_optin),
              "shift-and-add kernel");
     PPM_CUDA(launch_reduce(plan, en, part, status, L.total_rows, Ft, st), "reduce kernel");
     if (inst_status)

@@ -142,6 +142,8 @@ struct EnergyDev {
     int sliding;         // consecutive pk differ by < 1 (one node shift per step)
     float step;          // > 0: pk is uniform with this step (1/3 .. 1/2), node-major walk
     float inv_step;      // 1 / step
+    int moments;         // 1: the forward shift-and-add takes the moment walk
+    int nmom;            // moment walk: relative table nodes per group (pk span + 8)
 };
 
 // ---- launchers (defined in the .cu files) --------------------------------
@@ -156,7 +158,7 @@ cudaError_t launch_ring(const Params &p, const PlanDev &plan, const LensDev &L,
                         cudaStream_t st, float2 *elemx = nullptr);
 
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
-                            const EnergyDev &en, int n_phi_max);
+                            const EnergyDev &en, int n_phi_max, size_t smem_optin);
 // grid_blocks: resident blocks of the persistent schedule (ignored without plan.queue);
 // smem_optin: the device's opt-in shared memory per block (0: temperature maps
 // take 256-thread blocks)

@@ -196,10 +196,10 @@ __device__ __forceinline__ float dot4(const float *__restrict__ q, float w0, flo
 // strategies A, B, C), transposed to [E][mu]; kept out of line (per ring).
 __device__ __noinline__ void stage_slab_stencil(const AtmDev &A, const RingRec *rp,
                                                 const float *I0, int plane, int Pm, float *slab,
-                                                int tid)
+                                                int tid, int nt)
 {
     const int tT = rp->tT, tg = rp->tg;
-    for (int idx = tid; idx < plane; idx += kSABlock) {
+    for (int idx = tid; idx < plane; idx += nt) {
         float v = 0.0f;
         for (int a = 0; a < tT; ++a)
             for (int c = 0; c < tg; ++c)
@@ -213,7 +213,7 @@ __device__ __noinline__ void stage_slab_stencil(const AtmDev &A, const RingRec *
 // the 16 plane weights in registers and two words' 16 loads in flight per
 // thread; same sums as stage_slab_stencil, kept out of line (per ring).
 __device__ __noinline__ void stage_slab_4x4(const AtmDev &A, const RingRec *rp, const float *I0,
-                                            int plane, int Pm, float *slab, int tid)
+                                            int plane, int Pm, float *slab, int tid, int nt)
 {
     float wv[16];
 #pragma unroll
@@ -223,11 +223,11 @@ __device__ __noinline__ void stage_slab_4x4(const AtmDev &A, const RingRec *rp, 
     const size_t ps = (size_t)plane;
     const size_t gs = (size_t)A.ng * plane;
     constexpr int U = 2;
-    for (int base = tid; base < plane; base += U * kSABlock) {
+    for (int base = tid; base < plane; base += U * nt) {
         float v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int idx = base + u * kSABlock;
+            const int idx = base + u * nt;
             float acc = 0.0f;
             if (idx < plane) {
                 float x[16];
@@ -242,7 +242,7 @@ __device__ __noinline__ void stage_slab_4x4(const AtmDev &A, const RingRec *rp, 
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int idx = base + u * kSABlock;
+            const int idx = base + u * nt;
             if (idx < plane) {
                 const int m = idx / A.nE, n = idx - m * A.nE;
                 slab[n * Pm + m] = v[u];
@@ -407,6 +407,13 @@ constexpr int kSlabMargin = 3;  // rows past the table read by slots past their 
 static bool node_walk(const Params &p, const EnergyDev &en)
 {
     return p.emission == 1 && en.sliding && en.step > 0.0f;
+}
+
+// the moment walk applies (the host asked for it; spot emission from the
+// table with an interpolant linear in the table values)
+static bool moment_walk(const Params &p, const AtmDev &A, const EnergyDev &en)
+{
+    return p.emission == 1 && !p.logT_map && en.moments && en.sliding && A.strategy != kInterpB;
 }
 
 // rings of the block's warps plus the slack that aligns them to 4096 bytes
@@ -686,8 +693,315 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
     }
 }
 
-template <int EMIS, int MODE, bool NODES>
-__global__ void __launch_bounds__(kSABlock, 2)
+// ---------------------------------------------------------------------------
+// Moment walk (atmosphere spots; every interpolation strategy whose value is
+// linear in the table values, i.e. all but the clipped one).  The 64 slots
+// of a group sit at positions X_p + (pk_k - pk_0) in table nodes (X_p =
+// pk_0 + ln z_p / dlnE).  With a reference position ref (the midpoint of the
+// group's extreme X_p), slot p is split as X_p = ref + a_p + eps_p, a_p
+// integer, eps_p in [-1/2, 1/2], and its node values are indexed relative to
+// N0 + a_p, N0 = floor(ref).  On the reference interval r of an energy (its
+// reference position N0 + r + tau, tau in [0, 1)) the cubic of slot p at
+// tau + eps_p expands in powers of tau with coefficients linear in
+// eps_p^j u_p, so the group's sum needs only the four moments
+//   M_j[m] = sum_p eps_p^j u_p[m],   u_p[m] = sum_i w_pi S[N0 + a_p + m][s_p + i]
+// of each relative node m (S the staged slab, w_pi the mu stencil weights
+// times F_p).  The slots of a group are neighbouring elements: their
+// stencils cover a few (a, mu column) cells, so M_j[m] = sum_cells
+// Omega_j[cell] S[N0 + a + m][column], with the cell weights Omega_j summed
+// once per group.  The walk is then one short dot product per node and
+// moment instead of one stencil per slot and node.  From M_j[r - 1 .. r + 2]
+// each reference interval gets one combined cubic in tau, exact for every
+// slot whose own position tau + eps_p stays in [0, 1); a slot that crossed
+// into the next (previous) interval adds the difference of the two cubics,
+// the fourth difference of its node values on r - 1 .. r + 3 times
+// t (t - 1) (t - 2) / 6 at t = tau + eps_p (on r - 2 .. r + 2 times
+// -(t + 1) t (t - 1) / 6).  Energies that can need such terms lie within
+// max |eps| of a node: a few per cent when the group's ln z spread is well
+// below one node.  Groups whose stencils cover more than kMomCells cells
+// take the energy walk.
+// ---------------------------------------------------------------------------
+constexpr int kMomLead = 2;    // zero rows below the table (relative node -2 of the lowest slot)
+constexpr int kMomCells = 64;  // (row offset, mu column) cells of one group
+// per warp: moments, then combined cubics, of the group's relative nodes
+// [nmom] float4; cell weights [kMomCells + 4] float4; fourth differences of
+// the cells [2][kMomCells]
+__host__ __device__ inline int mom_warp_floats(int nmom)
+{
+    return 4 * nmom + 4 * (kMomCells + 4) + 2 * kMomCells;
+}
+
+// power-basis coefficients of the cubic through y0..y3 at -1, 0, 1, 2
+__device__ __forceinline__ float4 cubic_coefs(float y0, float y1, float y2, float y3)
+{
+    const float c2 = fmaf(0.5f, y0 + y2, -y1);
+    const float c3 = fmaf(y3 - y0, 1.0f / 6.0f, 0.5f * (y1 - y2));
+    const float c1 = fmaf(y2 - y0, 0.5f, -c3);
+    return make_float4(y1, c1, c2, c3);
+}
+
+__device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
+{
+    return make_float4(fmaf(a.x, s, c.x), fmaf(a.y, s, c.y), fmaf(a.z, s, c.z), fmaf(a.w, s, c.w));
+}
+
+// weight of stencil entry d (0..3) of a slot, 0 outside
+__device__ __forceinline__ float stencil_w(int d, float w0, float w1, float w2, float w3)
+{
+    float w = d == 0 ? w0 : 0.0f;
+    w = d == 1 ? w1 : w;
+    w = d == 2 ? w2 : w;
+    return d == 3 ? w3 : w;
+}
+
+template <int MODE>
+__device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, float phi_out,
+                                                  const float *sel, const float *ph,
+                                                  const float *mun, const float *slab, int Pm,
+                                                  int n_fp, int top, const AtmDev &A,
+                                                  float inv_dlnE, const float *spk, int nE,
+                                                  int nch, float pk0, float pkl, float lz_safe,
+                                                  int nmom, float *wbuf, float *frow,
+                                                  unsigned *errp)
+{
+    static_assert(MODE != 2, "the clipped interpolant is not linear in the table values");
+    constexpr bool ONESIDED = MODE != 0;
+    const float nEm2 = (float)(A.nE - 2);
+    float X[2], wv[2][4];
+    int s0v[2];
+    bool fast[2], slow[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = g0 + lane + 32 * e;
+        const PairW P = pair_weights<ONESIDED>(m < n_act, m < n_act ? sel[m] : 0.0f, phi_out, ph,
+                                               mun, n_fp, top, A, inv_dlnE);
+        fast[e] = P.on && (pk0 + P.lz >= 1.0f) && (pkl + P.lz < nEm2);
+        slow[e] = P.on && !fast[e];
+        X[e] = pk0 + P.lz;
+        wv[e][0] = fast[e] ? P.w0 : 0.0f;
+        wv[e][1] = fast[e] ? P.w1 : 0.0f;
+        wv[e][2] = fast[e] ? P.w2 : 0.0f;
+        wv[e][3] = fast[e] ? P.w3 : 0.0f;
+        s0v[e] = fast[e] ? P.s0 : 0;
+    }
+    // extreme positions of the group's slots inside the window
+    float xmax = fmaxf(fast[0] ? X[0] : -INFINITY, fast[1] ? X[1] : -INFINITY);
+    float xmin = fminf(fast[0] ? X[0] : INFINITY, fast[1] ? X[1] : INFINITY);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        xmax = fmaxf(xmax, __shfl_xor_sync(kFull, xmax, o));
+        xmin = fminf(xmin, __shfl_xor_sync(kFull, xmin, o));
+    }
+    if (!(xmax >= xmin)) {
+        // no slot of the group inside the window: only the general path below
+    } else {
+        const float ref = 0.5f * (xmax + xmin);
+        const float nf = floorf(ref);
+        const float dref = ref - nf;
+        const int N0 = (int)nf;
+        float ev[2];
+        int av[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float x = fast[e] ? X[e] - ref : 0.0f;
+            const float ae = rintf(x);
+            ev[e] = x - ae;
+            av[e] = (int)ae;
+        }
+        // the group's box of cells: row offsets amin..amax x mu columns cmin..cmax + 3
+        const int amin = __reduce_min_sync(kFull, min(fast[0] ? av[0] : INT_MAX, fast[1] ? av[1] : INT_MAX));
+        const int amax = __reduce_max_sync(kFull, max(fast[0] ? av[0] : INT_MIN, fast[1] ? av[1] : INT_MIN));
+        const int cmin = __reduce_min_sync(kFull, min(fast[0] ? s0v[0] : INT_MAX, fast[1] ? s0v[1] : INT_MAX));
+        const int cmax = __reduce_max_sync(kFull, max(fast[0] ? s0v[0] : INT_MIN, fast[1] ? s0v[1] : INT_MIN));
+        const int ncol = cmax - cmin + 4, na = amax - amin + 1, nbox = na * ncol;
+        const int rmax = (int)floorf(dref + (pkl - pk0));
+        PPM_CHECK(rmax + 6 <= nmom, errp);
+        if (nbox > kMomCells || rmax + 6 > nmom) {
+            // stencils too scattered for the cell table: the energy walk
+            atm_group<1, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top, A,
+                               inv_dlnE, spk, nch, true, pk0, pkl, lz_safe, frow, errp);
+            return;
+        }
+        // below 7/8 node of spread no slot is shifted (a_p = 0) and the
+        // extreme eps are those of the extreme slots; otherwise +-1/2 bound them
+        const bool narrow = xmax - xmin < 0.875f;
+        const float emax = narrow ? xmax - ref : 0.5f;
+        const float emin = narrow ? xmin - ref : -0.5f;
+        float4 *Mv = reinterpret_cast<float4 *>(wbuf);                  // [nmom]
+        float4 *Om = reinterpret_cast<float4 *>(wbuf + 4 * nmom);       // [kMomCells + 4]
+        float *Dp = wbuf + 4 * nmom + 4 * (kMomCells + 4);             // [kMomCells]
+        float *Dm = Dp + kMomCells;                                     // [kMomCells]
+        int cell0[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            cell0[e] = fast[e] ? (av[e] - amin) * ncol + (s0v[e] - cmin) : -8;
+        const float2 E1 = make_float2(ev[0], ev[1]);
+        const float2 E2 = __fmul2_rn(E1, E1);
+        const float2 E3 = __fmul2_rn(E2, E1);
+
+        // cell weights Omega_j, four cells per pass, summed over the slots in
+        // a fixed order (slot sums, then the warp transpose-reduction)
+        for (int cb = 0; cb < nbox; cb += 4) {
+            float acc[kEC];
+#pragma unroll
+            for (int qi = 0; qi < 4; ++qi) {
+                const int q = cb + qi;
+                const float2 W = make_float2(
+                    stencil_w(q - cell0[0], wv[0][0], wv[0][1], wv[0][2], wv[0][3]),
+                    stencil_w(q - cell0[1], wv[1][0], wv[1][1], wv[1][2], wv[1][3]));
+                const float2 v1 = __fmul2_rn(W, E1), v2 = __fmul2_rn(W, E2), v3 = __fmul2_rn(W, E3);
+                acc[4 * qi + 0] = W.x + W.y;
+                acc[4 * qi + 1] = v1.x + v1.y;
+                acc[4 * qi + 2] = v2.x + v2.y;
+                acc[4 * qi + 3] = v3.x + v3.y;
+            }
+            const float tot = transpose_reduce16(acc, lane);
+            if (lane < kEC) reinterpret_cast<float *>(Om)[4 * cb + lane] = tot;
+        }
+        __syncwarp();
+
+        // moments of relative nodes m = -2 .. rmax + 3 (index m + 2), one
+        // node per lane: lanes read 32 consecutive rows of one column (odd
+        // row pitch: no bank conflicts) and the cell weights by broadcast
+        const float *sbase = slab + (N0 + amin) * Pm + cmin;
+        for (int m0 = -2; m0 <= rmax + 3; m0 += 32) {
+            const int m = m0 + lane;
+            if (m <= rmax + 3) {
+                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                const float *srow = sbase + m * Pm;
+                PPM_CHECK(N0 + amin + m >= -kMomLead && N0 + amax + m < A.nE + kSlabMargin, errp);
+                int q = 0;
+                for (int qa = 0; qa < na; ++qa, srow += Pm) {
+#pragma unroll 4
+                    for (int qc = 0; qc < ncol; ++qc, ++q) acc = f4fma(Om[q], srow[qc], acc);
+                }
+                Mv[m + 2] = acc;
+            }
+        }
+        __syncwarp();
+        // combined cubic of reference interval r (moments of nodes r - 1 .. r + 2,
+        // indices r + 1 .. r + 4), written in place at index r + 1: a pass
+        // reads indices up to 32 past what it writes, which later passes no
+        // longer read
+        for (int r0 = 0; r0 <= rmax; r0 += 32) {
+            const int r = r0 + lane;
+            float4 Pv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (r <= rmax) {
+                const float4 m0 = Mv[r + 1], m1 = Mv[r + 2], m2 = Mv[r + 3], m3 = Mv[r + 4];
+                const float4 a = cubic_coefs(m0.x, m1.x, m2.x, m3.x);   // of M_0
+                const float4 b = cubic_coefs(m0.y, m1.y, m2.y, m3.y);   // of M_1
+                const float4 c2 = cubic_coefs(m0.z, m1.z, m2.z, m3.z);  // of M_2
+                const float4 c3 = cubic_coefs(m0.w, m1.w, m2.w, m3.w);  // of M_3
+                // sum_j c_j (tau + eps)^j collected by powers of tau
+                Pv.x = a.x + b.y + c2.z + c3.w;
+                Pv.y = fmaf(3.0f, c2.w, fmaf(2.0f, b.z, a.y));
+                Pv.z = fmaf(3.0f, b.w, a.z);
+                Pv.w = a.w;
+            }
+            __syncwarp();
+            if (r <= rmax) Mv[r + 1] = Pv;
+            __syncwarp();
+        }
+
+        // cells of each lane for the fourth differences
+        int qa_l[2], qc_l[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = lane + 32 * h;
+            qa_l[h] = q / ncol;
+            qc_l[h] = q - qa_l[h] * ncol;
+        }
+        // energies: one per lane, the combined cubic at tau, plus the
+        // difference terms of slots that left the reference interval
+        for (int k0 = 0; k0 < nE; k0 += 32) {
+            const int k = k0 + lane;
+            const bool in = k < nE;
+            float tau = 0.0f, val = 0.0f;
+            int r = 0;
+            if (in) {
+                const float y = dref + (spk[k] - pk0);
+                const float rf = floorf(y);
+                r = (int)rf;
+                tau = y - rf;
+                const float4 Pv = Mv[r + 1];
+                val = fmaf(tau, fmaf(tau, fmaf(tau, Pv.w, Pv.z), Pv.y), Pv.x);
+            }
+            unsigned cand = __ballot_sync(kFull, in && (tau + emax >= 1.0f || tau + emin < 0.0f));
+            while (cand) {
+                const int bl = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const float tb = __shfl_sync(kFull, tau, bl);
+                const int rb = __shfl_sync(kFull, r, bl);
+                const bool up = tb + emax >= 1.0f, down = tb + emin < 0.0f;
+                // fourth differences of the cells on relative nodes rb - 1 .. rb + 3
+                // (up) and rb - 2 .. rb + 2 (down)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = lane + 32 * h;
+                    if (q < nbox) {
+                        const float *c = sbase + (qa_l[h] + rb - 2) * Pm + qc_l[h];
+                        const float s0 = c[0], s1 = c[Pm], s2 = c[2 * Pm], s3 = c[3 * Pm];
+                        const float s4 = c[4 * Pm];
+                        if (up) {
+                            const float s5 = c[5 * Pm];
+                            Dp[q] = fmaf(6.0f, s3, fmaf(-4.0f, s2 + s4, s1 + s5));
+                        }
+                        if (down) Dm[q] = fmaf(6.0f, s2, fmaf(-4.0f, s1 + s3, s0 + s4));
+                    }
+                }
+                __syncwarp();
+                float cs = 0.0f;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const float te = tb + ev[e];
+                    if (fast[e] && (te >= 1.0f || te < 0.0f)) {
+                        const float *D = (te >= 1.0f ? Dp : Dm) + cell0[e];
+                        const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
+                                              fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
+                        const float g = te >= 1.0f ? te * (te - 1.0f) * (te - 2.0f)
+                                                   : -(te + 1.0f) * te * (te - 1.0f);
+                        cs = fmaf(g * (1.0f / 6.0f), dv, cs);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) cs += __shfl_xor_sync(kFull, cs, o);
+                if (lane == bl) val += cs;
+                __syncwarp();
+            }
+            if (in) frow[k] += val;
+        }
+        __syncwarp();
+    }
+
+    // slots whose window leaves the table interior: general evaluation per
+    // chunk of 16 energies, summed across the warp like the energy walk
+    if (__any_sync(kFull, slow[0] || slow[1])) {
+        for (int cc = 0; cc < nch; ++cc) {
+            float acc[kEC];
+#pragma unroll
+            for (int s = 0; s < kEC; ++s) acc[s] = 0.0f;
+            const float *pkc = spk + cc * kEC;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                if (slow[e]) {
+                    const int m = g0 + lane + 32 * e;
+                    const PairW P = pair_weights_slow<ONESIDED>(sel[m], phi_out, ph, mun, n_fp,
+                                                                top, A, inv_dlnE);
+#pragma unroll
+                    for (int k = 0; k < kEC; ++k)
+                        acc[k] += eval_general(P, slab, Pm, A.nE, pkc[k] + P.lz, ONESIDED);
+                }
+            }
+            const float tot = transpose_reduce16(acc, lane);
+            if (lane < kEC) frow[cc * kEC + lane] += tot;
+        }
+        __syncwarp();
+    }
+}
+
+// WALK: 0 = energy walk, 1 = node-major walk, 2 = moment walk; NT threads
+template <int EMIS, int MODE, int WALK, int NT = kSABlock>
+__global__ void __launch_bounds__(NT, NT > kSABlock ? 1 : 2)
     k_shift_add(Params p, PlanDev plan, AtmDev A, EnergyDev en, Layout lay,
                 const RingRec *__restrict__ recs, const float *__restrict__ tmpl,
                 const float *__restrict__ elems, const int *__restrict__ status,
@@ -695,9 +1009,15 @@ __global__ void __launch_bounds__(kSABlock, 2)
 {
     extern __shared__ float sm[];
     __shared__ int s_next;
-    if (NODES)  // rows past the table that the node-major walk may read
+    if (WALK == 1)  // rows past the table that the node-major walk may read
         for (int i = threadIdx.x; i < kSlabMargin * A.nmu_pad; i += blockDim.x)
             sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
+    if (WALK == 2) {  // rows below and past the table that the moment walk may read
+        for (int i = threadIdx.x; i < kMomLead * A.nmu_pad; i += blockDim.x)
+            sm[lay.slab - kMomLead * A.nmu_pad + i] = 0.0f;
+        for (int i = threadIdx.x; i < kSlabMargin * A.nmu_pad; i += blockDim.x)
+            sm[lay.slab + A.nE * A.nmu_pad + i] = 0.0f;
+    }
     // static schedule: block b runs item order[b]; persistent schedule
     // (plan.queue): blocks take the next entry of the order from a counter
     for (int slot = blockIdx.x;;) {
@@ -740,7 +1060,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
     const bool inst_ok = status[it.b] == 0;
     // this warp's ring (node-major walk): 4096-byte aligned shared address
     unsigned ring_w = 0;
-    if (NODES)
+    if (WALK == 1)
         ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
                  (unsigned)(warp * kRingWarpBytes);
 
@@ -774,11 +1094,11 @@ __global__ void __launch_bounds__(kSABlock, 2)
                 constexpr int U = 4;  // loads in flight per thread
                 if (lin2) {
                     // (logT, logg) bilinear (strategy D): four planes
-                    for (int base = tid; base < plane; base += U * kSABlock) {
+                    for (int base = tid; base < plane; base += U * NT) {
                         float v[U];
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            const int idx = base + u * kSABlock;
+                            const int idx = base + u * NT;
                             v[u] = 0.0f;
                             if (idx < plane)
                                 v[u] = w00 * __ldg(I0 + idx) + w01 * __ldg(I01 + idx) +
@@ -786,7 +1106,7 @@ __global__ void __launch_bounds__(kSABlock, 2)
                         }
 #pragma unroll
                         for (int u = 0; u < U; ++u) {
-                            const int idx = base + u * kSABlock;
+                            const int idx = base + u * NT;
                             if (idx < plane) {
                                 const int m = idx / A.nE, n = idx - m * A.nE;
                                 slab[n * Pm + m] = v[u];
@@ -794,9 +1114,9 @@ __global__ void __launch_bounds__(kSABlock, 2)
                         }
                     }
                 } else if (rec.tT == 4 && rec.tg == 4) {
-                    stage_slab_4x4(A, rp, I0, plane, Pm, slab, tid);
+                    stage_slab_4x4(A, rp, I0, plane, Pm, slab, tid, NT);
                 } else {
-                    stage_slab_stencil(A, rp, I0, plane, Pm, slab, tid);
+                    stage_slab_stencil(A, rp, I0, plane, Pm, slab, tid, NT);
                 }
             }
         }
@@ -811,9 +1131,16 @@ __global__ void __launch_bounds__(kSABlock, 2)
         const float lz_safe = 1.25f - pk0;
         const bool sliding = en.sliding != 0;
 
-        for (int jl = warp; jl < it.nj; jl += kSABlock / 32) {
+        for (int jl = warp; jl < it.nj; jl += NT / 32) {
             const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
-            if constexpr (EMIS == 1 && NODES) {
+            if constexpr (EMIS == 1 && WALK == 2) {
+                float *wbuf = sm + lay.ring + warp * mom_warp_floats(en.nmom);
+                for (int g0 = 0; g0 < n_act; g0 += 64)
+                    atm_group_moments<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp,
+                                            top, A, inv_dlnE, spk, en.nE, nch, pk0, pkl, lz_safe,
+                                            en.nmom, wbuf, Fblk + jl * nEpad, plan.err);
+                continue;
+            } else if constexpr (EMIS == 1 && WALK == 1) {
                 for (int g0 = 0; g0 < n_act; g0 += 64)
                     atm_group_nodes<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp,
                                           top, A, inv_dlnE, spk, en.nE, nch, en.step,
@@ -1251,24 +1578,60 @@ __global__ void __launch_bounds__(256) k_reduce(PlanDev plan, EnergyDev en,
 
 }  // namespace
 
+namespace {
+
+// walk, block size and shared-memory layout of the spot kernel: the moment
+// walk where it applies and its per-warp buffers fit the opt-in limit, else
+// the node-major walk (or the energy walk)
+struct SpotConfig {
+    Layout lay;
+    int walk, nt;
+};
+
+SpotConfig spot_config(const Params &p, const PlanDev &plan, const AtmDev &A, const EnergyDev &en,
+                       int n_phi_max, size_t smem_optin)
+{
+    auto layout = [&](int walk, int nt) {
+        Layout lay;
+        int off = 0;
+        auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
+        lay.tmpl = take(4 * (plan.n_fp + 1));
+        lay.elems = take(n_phi_max);
+        lay.munodes = take(p.emission == 1 ? A.nmu : 0);
+        take(walk == 2 ? kMomLead * A.nmu_pad : 0);  // zero rows below the slab
+        const int margin = walk != 0 ? kSlabMargin : 0;
+        lay.slab = take(p.emission == 1 ? (A.nE + margin) * A.nmu_pad : 0);
+        lay.pk = take(en.nEpad);
+        lay.E = take(en.nEpad);
+        lay.E3 = take(en.nEpad);
+        lay.fblk = take(plan.pt * en.nEpad);
+        lay.ring = take(walk == 2 ? (nt / 32) * mom_warp_floats(en.nmom)
+                                  : (walk == 1 ? ring_floats(nt / 32) : 0));
+        lay.total = off;
+        return lay;
+    };
+    SpotConfig c;
+    if (moment_walk(p, A, en)) {
+        c.walk = 2;
+        c.nt = kSABlock;
+        c.lay = layout(2, kSABlock);
+        if ((size_t)c.lay.total * sizeof(float) + 64 <= smem_optin) return c;
+    }
+    c.walk = node_walk(p, en) ? 1 : 0;
+    c.nt = kSABlock;
+    c.lay = layout(c.walk, kSABlock);
+    return c;
+}
+
+}  // namespace
+
 size_t shift_add_smem_bytes(const Params &p, const PlanDev &plan, const AtmDev &A,
-                            const EnergyDev &en, int n_phi_max)
+                            const EnergyDev &en, int n_phi_max, size_t smem_optin)
 {
     // the 256-thread map layout is the minimum; 512 threads are taken only where they fit
     if (p.logT_map)
         return (size_t)map_layout(p, plan, A, en, n_phi_max, kSABlock).total * sizeof(float);
-    int off = 0;
-    auto take = [&](int n) { off += (n + 3) & ~3; };
-    take(4 * (plan.n_fp + 1));
-    take(n_phi_max);
-    take(p.emission == 1 ? A.nmu : 0);
-    take(p.emission == 1 ? (A.nE + (node_walk(p, en) ? kSlabMargin : 0)) * A.nmu_pad : 0);
-    take(en.nEpad);
-    take(en.nEpad);
-    take(en.nEpad);
-    take(plan.pt * en.nEpad);
-    take(node_walk(p, en) ? ring_floats() : 0);
-    return (size_t)off * sizeof(float);
+    return (size_t)spot_config(p, plan, A, en, n_phi_max, smem_optin).lay.total * sizeof(float);
 }
 
 cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev &A,
@@ -1298,46 +1661,38 @@ cudaError_t launch_shift_add(const Params &p, const PlanDev &plan, const AtmDev 
         if (wide + stat <= smem_optin) return go(k_shift_add_map<1, true, 512>, 512);
         return go(k_shift_add_map<1, true>, kSABlock);
     }
-    // persistent schedule: the queue counter must start at zero on the stream
+    const SpotConfig cfg = spot_config(p, plan, A, en, n_phi_max, smem_optin);
+    // persistent schedule: the queue counter must start at zero on the stream;
+    // grid_blocks counts 256-thread blocks (two per SM)
     if (plan.queue) {
         cudaError_t e0 = cudaMemsetAsync(plan.queue, 0, sizeof(int), st);
         if (e0 != cudaSuccess) return e0;
+        grid_blocks = grid_blocks * kSABlock / cfg.nt;
         grid_blocks = std::max(1, std::min(grid_blocks, plan.n_items));
     } else {
         grid_blocks = plan.n_items;
     }
-    Layout lay;
-    int off = 0;
-    auto take = [&](int n) { int o = off; off += (n + 3) & ~3; return o; };
-    lay.tmpl = take(4 * (plan.n_fp + 1));
-    lay.elems = take(n_phi_max);
-    lay.munodes = take(p.emission == 1 ? A.nmu : 0);
-    const bool nodes = node_walk(p, en);
-    lay.slab = take(p.emission == 1 ? (A.nE + (nodes ? kSlabMargin : 0)) * A.nmu_pad : 0);
-    lay.pk = take(en.nEpad);
-    lay.E = take(en.nEpad);
-    lay.E3 = take(en.nEpad);
-    lay.fblk = take(plan.pt * en.nEpad);
-    lay.ring = take(nodes ? ring_floats() : 0);
-    lay.total = off;
-    const size_t bytes = (size_t)off * sizeof(float);
+    const Layout lay = cfg.lay;
+    const size_t bytes = (size_t)lay.total * sizeof(float);
     cudaError_t e;
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bytes);
         if (r != cudaSuccess) return r;
-        kern<<<grid_blocks, kSABlock, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, status,
-                                                   partials);
+        kern<<<grid_blocks, cfg.nt, bytes, st>>>(p, plan, A, en, lay, recs, tmpl, elems, status,
+                                                 partials);
         return cudaSuccess;
     };
-    (void)grid_blocks;
-    if (p.emission == 0) e = go(k_shift_add<0, 0, false>);
-    else if (nodes && A.strategy == kInterpA) e = go(k_shift_add<1, 1, true>);
-    else if (nodes && A.strategy == kInterpB) e = go(k_shift_add<1, 2, true>);
-    else if (nodes) e = go(k_shift_add<1, 0, true>);
-    else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1, false>);
-    else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2, false>);
-    else e = go(k_shift_add<1, 0, false>);
+    const int walk = cfg.walk;
+    if (p.emission == 0) e = go(k_shift_add<0, 0, 0>);
+    else if (walk == 2 && A.strategy == kInterpA) e = go(k_shift_add<1, 1, 2>);
+    else if (walk == 2) e = go(k_shift_add<1, 0, 2>);
+    else if (walk == 1 && A.strategy == kInterpA) e = go(k_shift_add<1, 1, 1>);
+    else if (walk == 1 && A.strategy == kInterpB) e = go(k_shift_add<1, 2, 1>);
+    else if (walk == 1) e = go(k_shift_add<1, 0, 1>);
+    else if (A.strategy == kInterpA) e = go(k_shift_add<1, 1, 0>);
+    else if (A.strategy == kInterpB) e = go(k_shift_add<1, 2, 0>);
+    else e = go(k_shift_add<1, 0, 0>);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -1,8 +1,8 @@
 """The bounds-checked build (libppm_check.so, -DPPM_BOUNDS_CHECK) runs the
 forward, likelihood and gradient paths on workloads that reach the table
-edges, the node-major walks (with and without elements leaving the table),
-the HEALPix mesh and a temperature map, and reports no failed index check
-through ppm_sync; its results equal the ordinary build's."""
+edges, the node-major and moment walks (with and without elements leaving
+the table), the HEALPix mesh and a temperature map, and reports no failed
+index check through ppm_sync; its results equal the ordinary build's."""
 import os
 import subprocess
 import sys
@@ -57,6 +57,29 @@ c = synth.crescent_extreme(n_theta=24, n_phi=24, n_phase=32, n_E=48, n_chan=8, a
 ctx = context(c)
 out["crescent"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
 ctx.sync()
+# the moment walk (walk 2): both table edges, groups wider than a node, the crescent
+for name, (lo, hi, n, spin, zeta) in {"mw": (0.5, 6.0, 159, 205.0, None),
+                                      "mwlow": (0.052, 0.32, 58, 205.0, None),
+                                      "mwedge": (3.5, 7.8, 56, 205.0, None),
+                                      "mwwide": (0.6, 2.6, 96, 600.0, [0.6, 0.7])}.items():
+    v = synth.atm_two_spot(n_theta=12, n_phi=40, n_phase=24, n_E=n, n_chan=20, atm=atm, lens=lens)
+    v.E_keV = synth.logspace(lo, hi, n)
+    v.inst.spin_hz[:] = spin
+    if zeta is not None:
+        v.inst.zeta[0] = zeta
+    for s in "da":
+        v.interp = s
+        ctx = context(v)
+        ctx.set_tiles(walk=2)
+        out[name + "_Ft_" + s] = ctx.profile(ppm.DeviceParams(v.inst)).cpu().numpy()
+        ctx.sync()
+        ctx.set_tiles()
+c = synth.crescent_extreme(n_theta=24, n_phi=96, n_phase=32, n_E=300, n_chan=8, atm=atm)
+ctx = context(c)
+ctx.set_tiles(walk=2)
+out["crescent_mw"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
+ctx.sync()
+ctx.set_tiles()
 hm = synth.healpix_map(n_side=8, n_phase=16, n_E=96, n_chan=8, atm=atm, lens=lens)
 hm.E_keV = synth.logspace(0.6, 2.6, 96)
 hm.R = synth.response(hm.E_keV, 8)

@@ -31,13 +31,13 @@ def _step(w, atm):
     return math.log(w.E_keV[-1] / w.E_keV[0]) / (len(w.E_keV) - 1) / dln
 
 
-def _both_walks(w):
+def _walks(w, walks=(0, 1)):
     import paper_2510_07764_gb300 as ppm
     ctx = context(w)
     dp = ppm.DeviceParams(w.inst)
     out = []
     try:
-        for walk in (0, 1):
+        for walk in walks:
             ctx.set_tiles(walk=walk)
             Ft = ctx.profile(dp)
             ctx.sync()
@@ -45,6 +45,10 @@ def _both_walks(w):
     finally:
         ctx.set_tiles()
     return out
+
+
+def _both_walks(w):
+    return _walks(w, (0, 1))
 
 
 @pytest.mark.parametrize("interp", ["d", "a", "b", "c"])
@@ -227,3 +231,123 @@ def test_node_walk_temperature_map(orc, synth, atm, small_lens):
     assert not np.array_equal(node, energy)
     assert max_rel(node, energy) < TOL_WALKS
     assert max_rel(node, orc.profile(w)) < TOL_ATM
+
+
+# ---- the moment walk (ppm_tiles.walk = 2) ---------------------------------
+# Per group of 64 elements the walk sums the moments sum_p eps_p^j u_p of the
+# contracted node values and evaluates one combined cubic per energy, plus
+# the exact difference terms of elements whose own position crossed a node.
+# It applies to every grid whose steps stay below one table node (not only
+# the uniform ones of the node-major walk) and to every strategy but B.
+
+@pytest.mark.parametrize("interp", ["d", "a", "c"])
+def test_moment_walk_matches_oracle_and_other_walks(orc, synth, atm, small_lens, interp):
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, interp)
+    mom, node, energy = _walks(w, (2, 0, 1))
+    assert not np.array_equal(mom, node)          # the moment walk ran
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
+def test_moment_walk_leaves_strategy_b_on_the_node_walk(synth, atm, small_lens):
+    """The clipped interpolant is not linear in the table values: the
+    setting keeps strategy B on the node-major walk, bit for bit."""
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, "b")
+    mom, node = _walks(w, (2, 0))
+    assert np.array_equal(mom, node)
+
+
+@pytest.mark.parametrize("n_E,lo,hi,wiggle", [
+    (159, 0.5, 6.0, 0.0),     # step 0.49
+    (230, 0.5, 6.6, 0.0),     # step 0.349
+    (300, 0.1, 5.215, 0.0),   # the crescent workload's grid, step 0.41
+    (64, 0.6, 2.6, 0.0),      # step 0.73: beyond the node-major walk
+    (96, 0.6, 2.6, 0.01),     # not uniform in ln E
+    (17, 0.6, 0.9, 0.0),      # one chunk of nodes
+])
+def test_moment_walk_grids(orc, synth, atm, small_lens, n_E, lo, hi, wiggle):
+    w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=16)
+    w.E_keV = w.E_keV * (1.0 + wiggle * np.sin(np.arange(n_E)))
+    mom, energy = _walks(w, (2, 1))
+    assert not np.array_equal(mom, energy)
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
+@pytest.mark.parametrize("lo,hi", [(0.052, 0.32), (3.5, 7.8)])
+def test_moment_walk_with_table_edges(orc, synth, atm, small_lens, lo, hi):
+    """Elements of a group split between the walk and the general path."""
+    n_E = int(round(math.log(hi / lo) / (0.45 * 0.0321))) + 1
+    w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=20)
+    mom, energy = _walks(w, (2, 1))
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
+def test_moment_walk_wide_groups(orc, synth, atm, small_lens):
+    """Large spots at 600 Hz: most groups spread over more than one table
+    node in ln z (offsets a_p != 0, every energy a candidate for the
+    difference terms)."""
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, n_phase=24)
+    w.inst.spin_hz[:] = 600.0
+    w.inst.zeta[0] = [0.6, 0.7]
+    mom, energy = _walks(w, (2, 1))
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
+def test_moment_walk_crescent(orc, synth, atm):
+    """The crescent geometry (narrow groups: difference terms at a few per
+    cent of the energies) on its 300-energy grid."""
+    w = synth.crescent_extreme(n_theta=24, n_phi=96, n_phase=32, n_E=300, n_chan=8, atm=atm)
+    mom, energy = _walks(w, (2, 1))
+    assert not np.array_equal(mom, energy)
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
+def test_moment_walk_persistent_schedule_is_bitwise_identical(synth, atm, small_lens):
+    import paper_2510_07764_gb300 as ppm
+    w = _workload(synth, atm, small_lens, 120, 0.4, 2.6, n_theta=20, n_phi=72, n_phase=40)
+    inst = w.inst.select(np.zeros(5, dtype=int))
+    inst.incl_rad[:] = np.linspace(0.3, 1.4, 5)
+    w.inst = inst
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    res = []
+    try:
+        for pers in (False, True):
+            ctx.set_tiles(16, 16, pers, walk=2)
+            Ft = ctx.profile(dp)
+            ctx.sync()
+            res.append(Ft.cpu().numpy())
+    finally:
+        ctx.set_tiles()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_moment_walk_likelihood_and_gradient(synth, atm, small_lens):
+    """ppm_loglike_grad with the moment walk in its forward pass equals the
+    node-major run to FP32 rounding."""
+    import torch
+    import paper_2510_07764_gb300 as ppm
+    from grad_helpers import grad_tol
+    w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, n_theta=10, n_phi=24, n_phase=20)
+    w.R = synth.response(w.E_keV, 8)
+    w.sigma_ism = synth.sigma_ism(w.E_keV)
+    ctx = context(w)
+    dp = ppm.DeviceParams(w.inst)
+    cnt = torch.from_numpy(w.counts).cuda()
+    out = []
+    try:
+        for walk in (2, 0):
+            ctx.set_tiles(walk=walk)
+            ll, g = ctx.loglike_grad(dp, cnt, w.tau)
+            ctx.sync()
+            out.append((ll.cpu().numpy(), g.cpu().numpy()))
+    finally:
+        ctx.set_tiles()
+    (ll2, g2), (ll0, g0) = out
+    assert abs(ll2[0] - ll0[0]) <= 1e-6 * abs(ll0[0])
+    ref = g0[0, :13]
+    assert np.all(np.abs(g2[0, :13] - ref) <= 0.1 * grad_tol(ref))
