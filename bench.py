@@ -96,9 +96,9 @@ def parse(argv=None):
     ap.add_argument("--autotune", action="store_true",
                     help="pick the shift-and-add tiles with ppm_autotune before timing")
     ap.add_argument("--walk", type=int, choices=[0, 1, 2], default=0,
-                    help="energy walk of the atmosphere shift-and-add: 0 node-major where "
-                         "the energy grid allows it, 1 energy walk, 2 moment walk where it "
-                         "applies (ppm_tiles.walk)")
+                    help="walk of the atmosphere shift-and-add: 0 moment walk, else "
+                         "node-major walk, where they apply; 1 energy walk; 2 node-major walk "
+                         "where it applies (ppm_tiles.walk)")
     return ap.parse_args(argv)
 
 
@@ -258,7 +258,7 @@ def forward_kernel_name(w):
 
 def profiled_config(args, name=None):
     """Whether this run launches the kernel configuration of a committed ncu
-    summary (default interpolation, point phases, node-major walk, default
+    summary (default interpolation, point phases, default walk, default
     tiles), whose DRAM bytes per launch may then be reported as traffic."""
     name = name or headline_name(args)
     return (name in ("atm_two_spot", "crescent_extreme") and args.interp in (None, "d")

@@ -326,16 +326,28 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
  * block per item (persistent = 0) or as a queue drained by two resident
  * blocks per SM (persistent = 1).  phase_tile = 0 picks 16 or 32 from the
  * problem size.  walk selects how a warp steps through the energies with
- * the atmosphere table: 0 (default) takes the node-major walk wherever the
- * observed energy grid is uniform in ln E with a step of 0.34 to 0.498
- * table nodes (every table interval then holds two or three observed
- * energies; one interval per iteration for all elements of a warp), and the
- * energy walk elsewhere; 1 always takes the energy walk (one observed
- * energy per iteration, interval changes per element).  The two sum the
- * same terms in a different order.  With the node-major walk, phase_tile = 0
- * picks 16 (its shared-memory rings leave room for two blocks per SM only
- * with 16-phase tiles).  The backward pass of ppm_loglike_grad follows the
- * same setting.  The setting applies to later calls of the context.
+ * the atmosphere table:
+ *   - 1: the energy walk (one observed energy per iteration, interval
+ *     changes per element), everywhere;
+ *   - 2: the node-major walk wherever the observed energy grid is uniform in
+ *     ln E with a step of 0.34 to 0.498 table nodes (every table interval
+ *     then holds two or three observed energies; one interval per iteration
+ *     for all elements of a warp), the energy walk elsewhere;
+ *   - 0 (default): as 2, except that the forward shift-and-add of spots takes
+ *     the moment walk wherever the observed energies step by less than one
+ *     table node and the interpolation strategy is not B: per group of 64
+ *     elements the moments sum_p eps_p^j u_p of the node values (eps_p the
+ *     element's offset from the group's reference position, j = 0..3) are
+ *     contracted once per table node from cell weights over the group's
+ *     stencil cells, and each energy evaluates one combined cubic, plus exact
+ *     difference terms for elements on the other side of a node.
+ * All walks evaluate the same interpolants; they differ in the order of the
+ * FP32 sums (and, for the node-major walk, in positions accumulated along
+ * the grid).  With the node-major or moment walk, phase_tile = 0 picks 16
+ * (their shared-memory buffers leave room for two blocks per SM only with
+ * 16-phase tiles).  The backward pass of ppm_loglike_grad takes the
+ * node-major walk under 0 and 2.  The setting applies to later calls of the
+ * context.
  *
  * ppm_autotune runs the forward profile of (p, res) once per candidate
  * (phase_tile 16/32 x waves 8/16/32/64 x persistent 0/1, one untimed and one
@@ -347,7 +359,8 @@ typedef struct {
     int phase_tile;   /* 0 (automatic), 16 or 32 */
     int waves;        /* 1 .. 256, default 16 */
     int persistent;   /* 0 or 1 */
-    int walk;         /* 0 (node-major where it applies) or 1 (energy walk) */
+    int walk;         /* 0 (moment, else node-major, where they apply), 1 (energy walk)
+                         or 2 (node-major where it applies) */
     double ms;        /* ppm_autotune: time of the chosen candidate */
 } ppm_tiles;
 

@@ -96,8 +96,8 @@ struct ppm_ctx {
     int tile_pt = 0;          // output phases per item: 0 = automatic, 16 or 32
     int tile_waves = 16;      // target waves of 2 blocks per SM (sets the ring-group size)
     int tile_persistent = 0;  // 1: persistent blocks take items from a queue
-    int tile_walk = 0;        // 0: node-major walk where it applies, 1: energy walk,
-                              // 2: moment walk where it applies (node-major elsewhere)
+    int tile_walk = 0;        // 0: moment walk, else node-major walk, where they apply;
+                              // 1: energy walk; 2: node-major walk where it applies
     int *d_queue = nullptr;
     // plan
     std::vector<int> plan_key;
@@ -497,11 +497,12 @@ static float walk_step_of(const ppm_ctx *ctx)
     return (float)d;
 }
 
-// the atmosphere shift-and-add of this call takes the node-major walk
-// (spots and temperature maps alike)
+// the node-major walk applies to the atmosphere shift-and-add of this call
+// (spots and temperature maps, forward and backward; the forward spot kernel
+// takes the moment walk instead where that applies)
 static bool node_walk_on(const ppm_ctx *ctx, const ppm_params *p, float step)
 {
-    return p->emission == 1 && (ctx->tile_walk == 0 || ctx->tile_walk == 2) && step > 0.0f;
+    return p->emission == 1 && ctx->tile_walk != 1 && step > 0.0f;
 }
 
 // the forward atmosphere shift-and-add of this call takes the moment walk:
@@ -509,7 +510,7 @@ static bool node_walk_on(const ppm_ctx *ctx, const ppm_params *p, float step)
 // strategy but the clipped one), energies inside the table
 static bool moment_walk_on(const ppm_ctx *ctx, const ppm_params *p)
 {
-    return p->emission == 1 && ctx->tile_walk == 2 && !p->logT_map && ctx->interp != kInterpB &&
+    return p->emission == 1 && ctx->tile_walk == 0 && !p->logT_map && ctx->interp != kInterpB &&
            sliding_of(ctx);
 }
 

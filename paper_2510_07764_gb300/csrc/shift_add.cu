@@ -698,37 +698,45 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
 // linear in the table values, i.e. all but the clipped one).  The 64 slots
 // of a group sit at positions X_p + (pk_k - pk_0) in table nodes (X_p =
 // pk_0 + ln z_p / dlnE).  With a reference position ref (the midpoint of the
-// group's extreme X_p), slot p is split as X_p = ref + a_p + eps_p, a_p
-// integer, eps_p in [-1/2, 1/2], and its node values are indexed relative to
-// N0 + a_p, N0 = floor(ref).  On the reference interval r of an energy (its
-// reference position N0 + r + tau, tau in [0, 1)) the cubic of slot p at
-// tau + eps_p expands in powers of tau with coefficients linear in
+// group's extreme X_p) and a group spread below kMomSpread node, slot p is
+// X_p = ref + eps_p with |eps_p| < kMomSpread / 2, and its node values are
+// indexed relative to N0 = floor(ref).  On the reference interval r of an
+// energy (its reference position N0 + r + tau, tau in [0, 1)) the cubic of
+// slot p at tau + eps_p expands in powers of tau with coefficients linear in
 // eps_p^j u_p, so the group's sum needs only the four moments
-//   M_j[m] = sum_p eps_p^j u_p[m],   u_p[m] = sum_i w_pi S[N0 + a_p + m][s_p + i]
+//   M_j[m] = sum_p eps_p^j u_p[m],   u_p[m] = sum_i w_pi S[N0 + m][s_p + i]
 // of each relative node m (S the staged slab, w_pi the mu stencil weights
-// times F_p).  The slots of a group are neighbouring elements: their
-// stencils cover a few (a, mu column) cells, so M_j[m] = sum_cells
-// Omega_j[cell] S[N0 + a + m][column], with the cell weights Omega_j summed
-// once per group.  The walk is then one short dot product per node and
-// moment instead of one stencil per slot and node.  From M_j[r - 1 .. r + 2]
-// each reference interval gets one combined cubic in tau, exact for every
-// slot whose own position tau + eps_p stays in [0, 1); a slot that crossed
-// into the next (previous) interval adds the difference of the two cubics,
-// the fourth difference of its node values on r - 1 .. r + 3 times
-// t (t - 1) (t - 2) / 6 at t = tau + eps_p (on r - 2 .. r + 2 times
-// -(t + 1) t (t - 1) / 6).  Energies that can need such terms lie within
-// max |eps| of a node: a few per cent when the group's ln z spread is well
-// below one node.  Groups whose stencils cover more than kMomCells cells
-// take the energy walk.
+// times F_p).  The slots of a group are neighbouring elements whose
+// stencils cover a few mu columns, so M_j[m] = sum_c Omega_j[c] S[N0 + m][c]
+// with the column weights Omega_j summed once per group: the walk is one
+// short dot product per node and moment instead of one stencil per slot and
+// node.  From M_j[r - 1 .. r + 2] each reference interval gets one combined
+// cubic in tau, exact for every slot whose own position tau + eps_p stays in
+// [0, 1); a slot that crossed into the next (previous) interval adds the
+// difference of the two cubics, the fourth difference of its node values on
+// r - 1 .. r + 3 times t (t - 1) (t - 2) / 6 at t = tau + eps_p (on r - 2 ..
+// r + 2 times -(t + 1) t (t - 1) / 6).  Energies that can need such terms
+// lie within max |eps| of a node, a fraction of about the spread.  Groups
+// with a wider spread, or stencils over more than kMomCells columns, are
+// left to the node-major walk (uniform grids) or the energy walk.
 // ---------------------------------------------------------------------------
-constexpr int kMomLead = 2;    // zero rows below the table (relative node -2 of the lowest slot)
-constexpr int kMomCells = 64;  // (row offset, mu column) cells of one group
+constexpr int kMomLead = 2;         // zero rows below the table (relative node -2)
+constexpr int kMomCells = 32;       // mu columns of one group's stencils
+constexpr float kMomSpread = 0.35f; // widest ln z spread of a group, in table nodes
 // per warp: moments, then combined cubics, of the group's relative nodes
-// [nmom] float4; cell weights [kMomCells + 4] float4; fourth differences of
-// the cells [2][kMomCells]
+// [nmom] float4; column weights [kMomCells + 4] float4; fourth differences
+// [2][kMomCells]
 __host__ __device__ inline int mom_warp_floats(int nmom)
 {
     return 4 * nmom + 4 * (kMomCells + 4) + 2 * kMomCells;
+}
+// bytes per warp of the moment kernel's buffers: the moment buffers and the
+// node-major walk's ring share them (a group takes one walk or the other),
+// in 4096-byte aligned slots
+__host__ __device__ inline int mom_slot_bytes(int nmom)
+{
+    const int b = 4 * mom_warp_floats(nmom);
+    return ((b > kRingWarpBytes ? b : kRingWarpBytes) + 4095) / 4096 * 4096;
 }
 
 // power-basis coefficients of the cubic through y0..y3 at -1, 0, 1, 2
@@ -754,15 +762,16 @@ __device__ __forceinline__ float stencil_w(int d, float w0, float w1, float w2, 
     return d == 3 ? w3 : w;
 }
 
+// One group of 64 slots (as atm_group_nodes) by the moment walk; returns
+// false, having written nothing, when the group is too wide for it.
 template <int MODE>
-__device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, float phi_out,
+__device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, float phi_out,
                                                   const float *sel, const float *ph,
                                                   const float *mun, const float *slab, int Pm,
                                                   int n_fp, int top, const AtmDev &A,
                                                   float inv_dlnE, const float *spk, int nE,
-                                                  int nch, float pk0, float pkl, float lz_safe,
-                                                  int nmom, float *wbuf, float *frow,
-                                                  unsigned *errp)
+                                                  int nch, float pk0, float pkl, int nmom,
+                                                  float *wbuf, float *frow, unsigned *errp)
 {
     static_assert(MODE != 2, "the clipped interpolant is not linear in the table values");
     constexpr bool ONESIDED = MODE != 0;
@@ -784,7 +793,7 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
         wv[e][3] = fast[e] ? P.w3 : 0.0f;
         s0v[e] = fast[e] ? P.s0 : 0;
     }
-    // extreme positions of the group's slots inside the window
+    // extreme positions and stencil columns of the group's slots inside the window
     float xmax = fmaxf(fast[0] ? X[0] : -INFINITY, fast[1] ? X[1] : -INFINITY);
     float xmin = fminf(fast[0] ? X[0] : INFINITY, fast[1] ? X[1] : INFINITY);
 #pragma unroll
@@ -792,56 +801,35 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
         xmax = fmaxf(xmax, __shfl_xor_sync(kFull, xmax, o));
         xmin = fminf(xmin, __shfl_xor_sync(kFull, xmin, o));
     }
-    if (!(xmax >= xmin)) {
-        // no slot of the group inside the window: only the general path below
-    } else {
+    const int cmin = __reduce_min_sync(kFull, min(fast[0] ? s0v[0] : INT_MAX, fast[1] ? s0v[1] : INT_MAX));
+    const int cmax = __reduce_max_sync(kFull, max(fast[0] ? s0v[0] : INT_MIN, fast[1] ? s0v[1] : INT_MIN));
+    const int ncol = cmax - cmin + 4;
+    if (xmax >= xmin) {  // some slot of the group is inside the window (warp-uniform)
         const float ref = 0.5f * (xmax + xmin);
         const float nf = floorf(ref);
         const float dref = ref - nf;
         const int N0 = (int)nf;
-        float ev[2];
-        int av[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const float x = fast[e] ? X[e] - ref : 0.0f;
-            const float ae = rintf(x);
-            ev[e] = x - ae;
-            av[e] = (int)ae;
-        }
-        // the group's box of cells: row offsets amin..amax x mu columns cmin..cmax + 3
-        const int amin = __reduce_min_sync(kFull, min(fast[0] ? av[0] : INT_MAX, fast[1] ? av[1] : INT_MAX));
-        const int amax = __reduce_max_sync(kFull, max(fast[0] ? av[0] : INT_MIN, fast[1] ? av[1] : INT_MIN));
-        const int cmin = __reduce_min_sync(kFull, min(fast[0] ? s0v[0] : INT_MAX, fast[1] ? s0v[1] : INT_MAX));
-        const int cmax = __reduce_max_sync(kFull, max(fast[0] ? s0v[0] : INT_MIN, fast[1] ? s0v[1] : INT_MIN));
-        const int ncol = cmax - cmin + 4, na = amax - amin + 1, nbox = na * ncol;
         const int rmax = (int)floorf(dref + (pkl - pk0));
         PPM_CHECK(rmax + 6 <= nmom, errp);
-        if (nbox > kMomCells || rmax + 6 > nmom) {
-            // stencils too scattered for the cell table: the energy walk
-            atm_group<1, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top, A,
-                               inv_dlnE, spk, nch, true, pk0, pkl, lz_safe, frow, errp);
-            return;
-        }
-        // below 7/8 node of spread no slot is shifted (a_p = 0) and the
-        // extreme eps are those of the extreme slots; otherwise +-1/2 bound them
-        const bool narrow = xmax - xmin < 0.875f;
-        const float emax = narrow ? xmax - ref : 0.5f;
-        const float emin = narrow ? xmin - ref : -0.5f;
+        if (!(xmax - xmin < kMomSpread) || ncol > kMomCells || rmax + 6 > nmom) return false;
+        // |X_p - ref| <= spread / 2 < 1/2: every slot has a_p = 0 and the
+        // extreme eps are those of the extreme slots
+        const float emax = xmax - ref, emin = xmin - ref;
+        const float ev[2] = {fast[0] ? X[0] - ref : 0.0f, fast[1] ? X[1] - ref : 0.0f};
         float4 *Mv = reinterpret_cast<float4 *>(wbuf);                  // [nmom]
         float4 *Om = reinterpret_cast<float4 *>(wbuf + 4 * nmom);       // [kMomCells + 4]
         float *Dp = wbuf + 4 * nmom + 4 * (kMomCells + 4);             // [kMomCells]
         float *Dm = Dp + kMomCells;                                     // [kMomCells]
         int cell0[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e)
-            cell0[e] = fast[e] ? (av[e] - amin) * ncol + (s0v[e] - cmin) : -8;
+        for (int e = 0; e < 2; ++e) cell0[e] = fast[e] ? s0v[e] - cmin : -8;
         const float2 E1 = make_float2(ev[0], ev[1]);
         const float2 E2 = __fmul2_rn(E1, E1);
         const float2 E3 = __fmul2_rn(E2, E1);
 
-        // cell weights Omega_j, four cells per pass, summed over the slots in
-        // a fixed order (slot sums, then the warp transpose-reduction)
-        for (int cb = 0; cb < nbox; cb += 4) {
+        // column weights Omega_j, four columns per pass, summed over the
+        // slots in a fixed order (slot sums, then the warp transpose-reduction)
+        for (int cb = 0; cb < ncol; cb += 4) {
             float acc[kEC];
 #pragma unroll
             for (int qi = 0; qi < 4; ++qi) {
@@ -862,19 +850,16 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
 
         // moments of relative nodes m = -2 .. rmax + 3 (index m + 2), one
         // node per lane: lanes read 32 consecutive rows of one column (odd
-        // row pitch: no bank conflicts) and the cell weights by broadcast
-        const float *sbase = slab + (N0 + amin) * Pm + cmin;
+        // row pitch: no bank conflicts) and the column weights by broadcast
+        const float *sbase = slab + N0 * Pm + cmin;
         for (int m0 = -2; m0 <= rmax + 3; m0 += 32) {
             const int m = m0 + lane;
             if (m <= rmax + 3) {
                 float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 const float *srow = sbase + m * Pm;
-                PPM_CHECK(N0 + amin + m >= -kMomLead && N0 + amax + m < A.nE + kSlabMargin, errp);
-                int q = 0;
-                for (int qa = 0; qa < na; ++qa, srow += Pm) {
+                PPM_CHECK(N0 + m >= -kMomLead && N0 + m < A.nE + kSlabMargin, errp);
 #pragma unroll 4
-                    for (int qc = 0; qc < ncol; ++qc, ++q) acc = f4fma(Om[q], srow[qc], acc);
-                }
+                for (int q = 0; q < ncol; ++q) acc = f4fma(Om[q], srow[q], acc);
                 Mv[m + 2] = acc;
             }
         }
@@ -903,14 +888,6 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
             __syncwarp();
         }
 
-        // cells of each lane for the fourth differences
-        int qa_l[2], qc_l[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = lane + 32 * h;
-            qa_l[h] = q / ncol;
-            qc_l[h] = q - qa_l[h] * ncol;
-        }
         // energies: one per lane, the combined cubic at tau, plus the
         // difference terms of slots that left the reference interval
         for (int k0 = 0; k0 < nE; k0 += 32) {
@@ -933,21 +910,17 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
                 const float tb = __shfl_sync(kFull, tau, bl);
                 const int rb = __shfl_sync(kFull, r, bl);
                 const bool up = tb + emax >= 1.0f, down = tb + emin < 0.0f;
-                // fourth differences of the cells on relative nodes rb - 1 .. rb + 3
-                // (up) and rb - 2 .. rb + 2 (down)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int q = lane + 32 * h;
-                    if (q < nbox) {
-                        const float *c = sbase + (qa_l[h] + rb - 2) * Pm + qc_l[h];
-                        const float s0 = c[0], s1 = c[Pm], s2 = c[2 * Pm], s3 = c[3 * Pm];
-                        const float s4 = c[4 * Pm];
-                        if (up) {
-                            const float s5 = c[5 * Pm];
-                            Dp[q] = fmaf(6.0f, s3, fmaf(-4.0f, s2 + s4, s1 + s5));
-                        }
-                        if (down) Dm[q] = fmaf(6.0f, s2, fmaf(-4.0f, s1 + s3, s0 + s4));
+                // fourth differences of the columns on relative nodes rb - 1 ..
+                // rb + 3 (up) and rb - 2 .. rb + 2 (down)
+                if (lane < ncol) {
+                    const float *c = sbase + (rb - 2) * Pm + lane;
+                    const float s0 = c[0], s1 = c[Pm], s2 = c[2 * Pm], s3 = c[3 * Pm];
+                    const float s4 = c[4 * Pm];
+                    if (up) {
+                        const float s5 = c[5 * Pm];
+                        Dp[lane] = fmaf(6.0f, s3, fmaf(-4.0f, s2 + s4, s1 + s5));
                     }
+                    if (down) Dm[lane] = fmaf(6.0f, s2, fmaf(-4.0f, s1 + s3, s0 + s4));
                 }
                 __syncwarp();
                 float cs = 0.0f;
@@ -997,6 +970,35 @@ __device__ __forceinline__ void atm_group_moments(int g0, int n_act, int lane, f
         }
         __syncwarp();
     }
+    return true;
+}
+
+// the walks a group of the moment kernel falls back to (out of line: rare)
+template <int MODE>
+__device__ __noinline__ void group_nodes_fallback(int g0, int n_act, int lane, float phi_out,
+                                                  const float *sel, const float *ph,
+                                                  const float *mun, const float *slab, int Pm,
+                                                  int n_fp, int top, const AtmDev &A,
+                                                  float inv_dlnE, const float *spk, int nE,
+                                                  int nch, float d, float inv_d, float pk0,
+                                                  float pkl, float lz_safe, unsigned ring,
+                                                  float *frow, unsigned *errp)
+{
+    atm_group_nodes<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top, A,
+                          inv_dlnE, spk, nE, nch, d, inv_d, pk0, pkl, lz_safe, ring, frow, errp);
+}
+
+template <int MODE>
+__device__ __noinline__ void group_energy_fallback(int g0, int n_act, int lane, float phi_out,
+                                                   const float *sel, const float *ph,
+                                                   const float *mun, const float *slab, int Pm,
+                                                   int n_fp, int top, const AtmDev &A,
+                                                   float inv_dlnE, const float *spk, int nch,
+                                                   float pk0, float pkl, float lz_safe,
+                                                   float *frow, unsigned *errp)
+{
+    atm_group<1, MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp, top, A, inv_dlnE,
+                       spk, nch, true, pk0, pkl, lz_safe, frow, errp);
 }
 
 // WALK: 0 = energy walk, 1 = node-major walk, 2 = moment walk; NT threads
@@ -1058,11 +1060,17 @@ __global__ void __launch_bounds__(NT, NT > kSABlock ? 1 : 2)
     const float inv_dlnE = (EMIS == 1) ? (float)(1.0 / A.dlnE) : 0.0f;
     const int Pm = A.nmu_pad;
     const bool inst_ok = status[it.b] == 0;
-    // this warp's ring (node-major walk): 4096-byte aligned shared address
+    // this warp's ring (node-major walk; in the moment kernel the slot that
+    // the moment buffers and the fallback's ring share): 4096-byte aligned
+    // shared address
     unsigned ring_w = 0;
-    if (WALK == 1)
-        ring_w = (((unsigned)__cvta_generic_to_shared(sm + lay.ring) + 4095u) & ~4095u) +
-                 (unsigned)(warp * kRingWarpBytes);
+    float *wbuf = nullptr;
+    if (WALK != 0) {
+        const unsigned slot = WALK == 2 ? (unsigned)mom_slot_bytes(en.nmom) : (unsigned)kRingWarpBytes;
+        const unsigned s0 = (unsigned)__cvta_generic_to_shared(sm);
+        ring_w = ((s0 + 4u * (unsigned)lay.ring + 4095u) & ~4095u) + (unsigned)warp * slot;
+        wbuf = sm + (ring_w - s0) / 4u;
+    }
 
     for (int r = it.r0; r < it.r1 && inst_ok; ++r) {
         const int ring = ip.ring0 + it.spot * ip.n_theta + r;
@@ -1134,11 +1142,25 @@ __global__ void __launch_bounds__(NT, NT > kSABlock ? 1 : 2)
         for (int jl = warp; jl < it.nj; jl += NT / 32) {
             const float phi_out = ((float)(it.j0 + jl) - q_half) * inv_nphase;
             if constexpr (EMIS == 1 && WALK == 2) {
-                float *wbuf = sm + lay.ring + warp * mom_warp_floats(en.nmom);
-                for (int g0 = 0; g0 < n_act; g0 += 64)
-                    atm_group_moments<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm, n_fp,
-                                            top, A, inv_dlnE, spk, en.nE, nch, pk0, pkl, lz_safe,
-                                            en.nmom, wbuf, Fblk + jl * nEpad, plan.err);
+                float *frow = Fblk + jl * nEpad;
+                for (int g0 = 0; g0 < n_act; g0 += 64) {
+                    if (atm_group_moments<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm,
+                                                n_fp, top, A, inv_dlnE, spk, en.nE, nch, pk0, pkl,
+                                                en.nmom, wbuf, frow, plan.err))
+                        continue;
+                    // too wide for the moment walk
+                    __syncwarp();
+                    if (en.step > 0.0f)
+                        group_nodes_fallback<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab, Pm,
+                                                   n_fp, top, A, inv_dlnE, spk, en.nE, nch,
+                                                   en.step, en.inv_step, pk0, pkl, lz_safe,
+                                                   ring_w, frow, plan.err);
+                    else
+                        group_energy_fallback<MODE>(g0, n_act, lane, phi_out, sel, ph, mun, slab,
+                                                    Pm, n_fp, top, A, inv_dlnE, spk, nch, pk0,
+                                                    pkl, lz_safe, frow, plan.err);
+                    __syncwarp();
+                }
                 continue;
             } else if constexpr (EMIS == 1 && WALK == 1) {
                 for (int g0 = 0; g0 < n_act; g0 += 64)
@@ -1605,7 +1627,7 @@ SpotConfig spot_config(const Params &p, const PlanDev &plan, const AtmDev &A, co
         lay.E = take(en.nEpad);
         lay.E3 = take(en.nEpad);
         lay.fblk = take(plan.pt * en.nEpad);
-        lay.ring = take(walk == 2 ? (nt / 32) * mom_warp_floats(en.nmom)
+        lay.ring = take(walk == 2 ? ((nt / 32) * mom_slot_bytes(en.nmom) + 4096) / 4
                                   : (walk == 1 ? ring_floats(nt / 32) : 0));
         lay.total = off;
         return lay;

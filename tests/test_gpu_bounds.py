@@ -37,7 +37,7 @@ for s in "dab":
     out["Ft_" + s] = ctx.profile(dp).cpu().numpy()
     ctx.sync()
 # uniform ln E grids of 0.49 and 0.45 table node per step: the node-major walks
-# of the forward and backward, the second with elements leaving the table top
+# (walk 2) of the forward and backward, the second with elements leaving the table top
 for name, (lo, hi, n) in {"nw": (0.5, 6.0, 159), "nwedge": (3.5, 7.8, 56)}.items():
     v = synth.atm_two_spot(n_theta=12, n_phi=40, n_phase=24, n_E=n, n_chan=20, atm=atm, lens=lens)
     v.E_keV = synth.logspace(lo, hi, n)
@@ -46,6 +46,7 @@ for name, (lo, hi, n) in {"nw": (0.5, 6.0, 159), "nwedge": (3.5, 7.8, 56)}.items
     for s in "db":
         v.interp = s
         ctx = context(v)
+        ctx.set_tiles(walk=2)
         dp = ppm.DeviceParams(v.inst)
         cnt = torch.from_numpy(v.counts).cuda()
         ll, g = ctx.loglike_grad(dp, cnt, v.tau)
@@ -53,11 +54,12 @@ for name, (lo, hi, n) in {"nw": (0.5, 6.0, 159), "nwedge": (3.5, 7.8, 56)}.items
         out[name + "_grad_" + s] = g.cpu().numpy()
         out[name + "_Ft_" + s] = ctx.profile(dp).cpu().numpy()
         ctx.sync()
+        ctx.set_tiles()
 c = synth.crescent_extreme(n_theta=24, n_phi=24, n_phase=32, n_E=48, n_chan=8, atm=atm)
 ctx = context(c)
 out["crescent"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
 ctx.sync()
-# the moment walk (walk 2): both table edges, groups wider than a node, the crescent
+# the moment walk (the default): both table edges, groups wider than a node, the crescent
 for name, (lo, hi, n, spin, zeta) in {"mw": (0.5, 6.0, 159, 205.0, None),
                                       "mwlow": (0.052, 0.32, 58, 205.0, None),
                                       "mwedge": (3.5, 7.8, 56, 205.0, None),
@@ -70,16 +72,12 @@ for name, (lo, hi, n, spin, zeta) in {"mw": (0.5, 6.0, 159, 205.0, None),
     for s in "da":
         v.interp = s
         ctx = context(v)
-        ctx.set_tiles(walk=2)
         out[name + "_Ft_" + s] = ctx.profile(ppm.DeviceParams(v.inst)).cpu().numpy()
         ctx.sync()
-        ctx.set_tiles()
 c = synth.crescent_extreme(n_theta=24, n_phi=96, n_phase=32, n_E=300, n_chan=8, atm=atm)
 ctx = context(c)
-ctx.set_tiles(walk=2)
 out["crescent_mw"] = ctx.profile(ppm.DeviceParams(c.inst)).cpu().numpy()
 ctx.sync()
-ctx.set_tiles()
 hm = synth.healpix_map(n_side=8, n_phase=16, n_E=96, n_chan=8, atm=atm, lens=lens)
 hm.E_keV = synth.logspace(0.6, 2.6, 96)
 hm.R = synth.response(hm.E_keV, 8)

@@ -1,8 +1,9 @@
-"""The node-major walk of the atmosphere shift-and-add (observed energies
-uniform in ln E with a step of 0.34-0.498 table nodes: every table interval
-holds two or three of them) against the FP64 oracle, and against the energy
-walk (ppm_tiles.walk = 1) on the same inputs: the two walks evaluate the
-same interpolants and sum them in a different order."""
+"""The walks of the atmosphere shift-and-add against the FP64 oracle and
+against the energy walk (ppm_tiles.walk = 1) on the same inputs: the
+node-major walk (walk = 2; observed energies uniform in ln E with a step of
+0.34-0.498 table nodes, every table interval holds two or three of them) and
+the moment walk (the default, walk = 0) evaluate the same interpolants and
+sum them in a different order."""
 import math
 
 import numpy as np
@@ -48,7 +49,8 @@ def _walks(w, walks=(0, 1)):
 
 
 def _both_walks(w):
-    return _walks(w, (0, 1))
+    """(node-major walk, energy walk)"""
+    return _walks(w, (2, 1))
 
 
 @pytest.mark.parametrize("interp", ["d", "a", "b", "c"])
@@ -111,7 +113,7 @@ def test_node_walk_persistent_schedule_is_bitwise_identical(synth, atm, small_le
     res = []
     try:
         for pers in (False, True):
-            ctx.set_tiles(16, 16, pers)
+            ctx.set_tiles(16, 16, pers, walk=2)
             Ft = ctx.profile(dp)
             ctx.sync()
             res.append(Ft.cpu().numpy())
@@ -129,7 +131,7 @@ def _grad_both_walks(w):
     cnt = torch.from_numpy(np.ascontiguousarray(w.counts)).cuda()
     out = []
     try:
-        for walk in (0, 1):
+        for walk in (2, 1):
             ctx.set_tiles(walk=walk)
             ll, g = ctx.loglike_grad(dp, cnt, w.tau)
             ctx.sync()
@@ -182,40 +184,45 @@ def test_node_walk_gradient_with_table_edges(orc, synth, atm, small_lens):
     tg._check(g1[0, :13], ref)
 
 
-def test_node_walk_cuda_graph_replay(synth, atm, small_lens):
-    """ppm_loglike_grad on the node-major walks captured once in a CUDA graph
-    and replayed after in-place parameter updates equals the direct call bit
-    for bit."""
+@pytest.mark.parametrize("walk", [2, 0])
+def test_node_walk_cuda_graph_replay(synth, atm, small_lens, walk):
+    """ppm_loglike_grad on the node-major walks (walk 2; the default walk 0
+    takes the moment walk forward) captured once in a CUDA graph and replayed
+    after in-place parameter updates equals the direct call bit for bit."""
     import torch
     import paper_2510_07764_gb300 as ppm
     w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, n_theta=10, n_phi=24, n_phase=20)
     w.R = synth.response(w.E_keV, 8)
     w.sigma_ism = synth.sigma_ism(w.E_keV)
     ctx = context(w)
-    dp = ppm.DeviceParams(w.inst)
-    cnt = torch.from_numpy(w.counts).cuda()
-    out = torch.empty(dp.B, dtype=torch.float64, device="cuda")
-    grad = torch.empty((dp.B, ppm.N_GRAD), dtype=torch.float64, device="cuda")
-    s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        for _ in range(2):
+    ctx.set_tiles(walk=walk)
+    try:
+        dp = ppm.DeviceParams(w.inst)
+        cnt = torch.from_numpy(w.counts).cuda()
+        out = torch.empty(dp.B, dtype=torch.float64, device="cuda")
+        grad = torch.empty((dp.B, ppm.N_GRAD), dtype=torch.float64, device="cuda")
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                ctx.loglike_grad(dp, cnt, w.tau, out=out, grad=grad, stream=s)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
             ctx.loglike_grad(dp, cnt, w.tau, out=out, grad=grad, stream=s)
-    s.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=s):
-        ctx.loglike_grad(dp, cnt, w.tau, out=out, grad=grad, stream=s)
-    th0 = dp.theta()
-    for k in range(2):
-        th = th0.clone()
-        th[:, 2] += 0.04 * (k + 1)
-        dp.set_theta(th)
-        g.replay()
-        torch.cuda.synchronize()
-        got_ll, got_g = out.clone(), grad.clone()
-        ref_ll, ref_g = ctx.loglike_grad(dp, cnt, w.tau)
-        torch.cuda.synchronize()
-        assert torch.equal(got_ll, ref_ll)
-        assert torch.equal(torch.nan_to_num(got_g), torch.nan_to_num(ref_g))
+        th0 = dp.theta()
+        for k in range(2):
+            th = th0.clone()
+            th[:, 2] += 0.04 * (k + 1)
+            dp.set_theta(th)
+            g.replay()
+            torch.cuda.synchronize()
+            got_ll, got_g = out.clone(), grad.clone()
+            ref_ll, ref_g = ctx.loglike_grad(dp, cnt, w.tau)
+            torch.cuda.synchronize()
+            assert torch.equal(got_ll, ref_ll)
+            assert torch.equal(torch.nan_to_num(got_g), torch.nan_to_num(ref_g))
+    finally:
+        ctx.set_tiles()
 
 
 def test_node_walk_temperature_map(orc, synth, atm, small_lens):
@@ -233,7 +240,7 @@ def test_node_walk_temperature_map(orc, synth, atm, small_lens):
     assert max_rel(node, orc.profile(w)) < TOL_ATM
 
 
-# ---- the moment walk (ppm_tiles.walk = 2) ---------------------------------
+# ---- the moment walk (the default, ppm_tiles.walk = 0) --------------------
 # Per group of 64 elements the walk sums the moments sum_p eps_p^j u_p of the
 # contracted node values and evaluates one combined cubic per energy, plus
 # the exact difference terms of elements whose own position crossed a node.
@@ -243,7 +250,7 @@ def test_node_walk_temperature_map(orc, synth, atm, small_lens):
 @pytest.mark.parametrize("interp", ["d", "a", "c"])
 def test_moment_walk_matches_oracle_and_other_walks(orc, synth, atm, small_lens, interp):
     w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, interp)
-    mom, node, energy = _walks(w, (2, 0, 1))
+    mom, node, energy = _walks(w, (0, 2, 1))
     assert not np.array_equal(mom, node)          # the moment walk ran
     assert max_rel(mom, energy) < TOL_WALKS
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
@@ -253,7 +260,7 @@ def test_moment_walk_leaves_strategy_b_on_the_node_walk(synth, atm, small_lens):
     """The clipped interpolant is not linear in the table values: the
     setting keeps strategy B on the node-major walk, bit for bit."""
     w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, "b")
-    mom, node = _walks(w, (2, 0))
+    mom, node = _walks(w, (0, 2))
     assert np.array_equal(mom, node)
 
 
@@ -268,7 +275,7 @@ def test_moment_walk_leaves_strategy_b_on_the_node_walk(synth, atm, small_lens):
 def test_moment_walk_grids(orc, synth, atm, small_lens, n_E, lo, hi, wiggle):
     w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=16)
     w.E_keV = w.E_keV * (1.0 + wiggle * np.sin(np.arange(n_E)))
-    mom, energy = _walks(w, (2, 1))
+    mom, energy = _walks(w, (0, 1))
     assert not np.array_equal(mom, energy)
     assert max_rel(mom, energy) < TOL_WALKS
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
@@ -279,19 +286,22 @@ def test_moment_walk_with_table_edges(orc, synth, atm, small_lens, lo, hi):
     """Elements of a group split between the walk and the general path."""
     n_E = int(round(math.log(hi / lo) / (0.45 * 0.0321))) + 1
     w = _workload(synth, atm, small_lens, n_E, lo, hi, n_phase=20)
-    mom, energy = _walks(w, (2, 1))
+    mom, energy = _walks(w, (0, 1))
     assert max_rel(mom, energy) < TOL_WALKS
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
 
 
-def test_moment_walk_wide_groups(orc, synth, atm, small_lens):
+@pytest.mark.parametrize("wiggle", [0.0, 0.01])
+def test_moment_walk_wide_groups(orc, synth, atm, small_lens, wiggle):
     """Large spots at 600 Hz: most groups spread over more than one table
-    node in ln z (offsets a_p != 0, every energy a candidate for the
-    difference terms)."""
+    node in ln z and leave the moment walk for the node-major walk (uniform
+    grid) or the energy walk (a grid not uniform in ln E), the others take
+    it, in the same call."""
     w = _workload(synth, atm, small_lens, 96, 0.6, 2.6, n_phase=24)
+    w.E_keV = w.E_keV * (1.0 + wiggle * np.sin(np.arange(96)))
     w.inst.spin_hz[:] = 600.0
     w.inst.zeta[0] = [0.6, 0.7]
-    mom, energy = _walks(w, (2, 1))
+    mom, energy = _walks(w, (0, 1))
     assert max_rel(mom, energy) < TOL_WALKS
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
 
@@ -300,7 +310,7 @@ def test_moment_walk_crescent(orc, synth, atm):
     """The crescent geometry (narrow groups: difference terms at a few per
     cent of the energies) on its 300-energy grid."""
     w = synth.crescent_extreme(n_theta=24, n_phi=96, n_phase=32, n_E=300, n_chan=8, atm=atm)
-    mom, energy = _walks(w, (2, 1))
+    mom, energy = _walks(w, (0, 1))
     assert not np.array_equal(mom, energy)
     assert max_rel(mom, energy) < TOL_WALKS
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
@@ -317,7 +327,7 @@ def test_moment_walk_persistent_schedule_is_bitwise_identical(synth, atm, small_
     res = []
     try:
         for pers in (False, True):
-            ctx.set_tiles(16, 16, pers, walk=2)
+            ctx.set_tiles(16, 16, pers)
             Ft = ctx.profile(dp)
             ctx.sync()
             res.append(Ft.cpu().numpy())
@@ -340,7 +350,7 @@ def test_moment_walk_likelihood_and_gradient(synth, atm, small_lens):
     cnt = torch.from_numpy(w.counts).cuda()
     out = []
     try:
-        for walk in (2, 0):
+        for walk in (0, 2):
             ctx.set_tiles(walk=walk)
             ll, g = ctx.loglike_grad(dp, cnt, w.tau)
             ctx.sync()
