@@ -83,6 +83,8 @@ struct ppm_ctx {
     int interp = kInterpD;  // interpolation strategy (Sect. 4)
     double lnE0_t = 0.0, dlnE_t = 0.0;
     DevBuf d_I, d_logT, d_logg, d_mu;
+    DevBuf d_mu_aux;   // mu bin index, reciprocal Lagrange denominators, reciprocal spacings
+    float mu_bin = 0.0f;
     // energies
     std::vector<double> E;
     DevBuf d_E, d_E3, d_pk, d_invE;
@@ -247,7 +249,7 @@ void ppm_destroy(ppm_ctx *ctx)
     DeviceGuard g(ctx->device);
     cudaDeviceSynchronize();
     for (DevBuf *b : {&ctx->d_Ca, &ctx->d_LF, &ctx->d_TD, &ctx->d_I, &ctx->d_logT, &ctx->d_logg,
-                      &ctx->d_mu, &ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
+                      &ctx->d_mu, &ctx->d_mu_aux, &ctx->d_E, &ctx->d_E3, &ctx->d_pk, &ctx->d_invE, &ctx->d_R,
                       &ctx->d_sigma, &ctx->d_Rtc, &ctx->d_plan, &ctx->ws})
         b->release();
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -359,6 +361,38 @@ ppm_status ppm_set_atmosphere(ppm_ctx *ctx, const float *I, const double *logT, 
     PPM_CUDA(cudaMemcpy(ctx->d_logg.p, logg, ng * 8, cudaMemcpyHostToDevice), "copy");
     std::vector<float> muf(mu, mu + nmu);
     PPM_CUDA(cudaMemcpy(ctx->d_mu.p, muf.data(), nmu * 4, cudaMemcpyHostToDevice), "copy");
+    {
+        // lookups of the FP32 mu nodes: bin -> an interval near the bin's
+        // start (the kernels correct it by linear steps to the exact
+        // interval), Lagrange and linear reciprocal denominators
+        const double m0 = muf[0], m1 = muf[nmu - 1];
+        const double bin = kMuBins / (m1 - m0);
+        std::vector<int> idx(kMuBins);
+        for (int b = 0; b < kMuBins; ++b) {
+            const double edge = m0 + b / bin;
+            int c = 0;
+            while (c + 1 <= nmu - 2 && (double)muf[c + 1] <= edge) ++c;
+            idx[b] = c;
+        }
+        std::vector<float> rden(4 * (size_t)nmu, 0.0f), rlin(nmu, 0.0f);
+        for (int s0 = 0; s0 + 3 < nmu; ++s0)
+            for (int a = 0; a < 4; ++a) {
+                double den = 1.0;
+                for (int b2 = 0; b2 < 4; ++b2)
+                    if (b2 != a) den *= (double)muf[s0 + a] - (double)muf[s0 + b2];
+                rden[4 * s0 + a] = (float)(1.0 / den);
+            }
+        for (int i = 0; i + 1 < nmu; ++i) rlin[i] = (float)(1.0 / ((double)muf[i + 1] - muf[i]));
+        const size_t o_rden = kMuBins * sizeof(int), o_rlin = o_rden + rden.size() * 4;
+        PPM_CUDA(ctx->d_mu_aux.ensure(o_rlin + rlin.size() * 4), "alloc");
+        char *base = ctx->d_mu_aux.as<char>();
+        PPM_CUDA(cudaMemcpy(base, idx.data(), kMuBins * sizeof(int), cudaMemcpyHostToDevice), "copy");
+        PPM_CUDA(cudaMemcpy(base + o_rden, rden.data(), rden.size() * 4, cudaMemcpyHostToDevice),
+                 "copy");
+        PPM_CUDA(cudaMemcpy(base + o_rlin, rlin.data(), rlin.size() * 4, cudaMemcpyHostToDevice),
+                 "copy");
+        ctx->mu_bin = (float)bin;
+    }
     ctx->nT = nT; ctx->ng = ng; ctx->nmu = nmu; ctx->nEt = nE; ctx->n_protect = n_protect;
     ctx->nmu_pad = pad; ctx->lnE0_t = lnE[0]; ctx->dlnE_t = d;
     ctx->atm_ready = true;
@@ -798,6 +832,21 @@ static ppm_status ensure_workspace(ppm_ctx *ctx, const ppm_params *p, int n_fp, 
     return PPM_OK;
 }
 
+// the mu lookups of the table (AtmDev.mu_idx, mu_rden, mu_rlin, mu_bin)
+static void set_mu_lookups(const ppm_ctx *ctx, AtmDev *A)
+{
+    const char *base = ctx->d_mu_aux.as<char>();
+    const size_t o_rden = kMuBins * sizeof(int);
+    if (!base) {  // no atmosphere table
+        A->mu_idx = nullptr; A->mu_rden = nullptr; A->mu_rlin = nullptr; A->mu_bin = 0.0f;
+        return;
+    }
+    A->mu_idx = reinterpret_cast<const int *>(base);
+    A->mu_rden = reinterpret_cast<const float4 *>(base + o_rden);
+    A->mu_rlin = reinterpret_cast<const float *>(base + o_rden + 16 * (size_t)ctx->nmu);
+    A->mu_bin = ctx->mu_bin;
+}
+
 static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, PlanDev *plan,
                       LensDev *L, AtmDev *A, EnergyDev *en)
 {
@@ -832,6 +881,7 @@ static void fill_devs(ppm_ctx *ctx, const ppm_params *p, int n_fp, Params *P, Pl
     A->n_protect = ctx->n_protect; A->nmu_pad = ctx->nmu_pad; A->strategy = ctx->interp;
     A->I = ctx->d_I.as<float>(); A->logT = ctx->d_logT.as<double>();
     A->logg = ctx->d_logg.as<double>(); A->mu = ctx->d_mu.as<float>();
+    set_mu_lookups(ctx, A);
     A->lnE0 = ctx->lnE0_t; A->dlnE = ctx->dlnE_t;
     en->nE = (int)ctx->E.size(); en->nEpad = ctx->nEpad;
     en->E = ctx->d_E.as<float>(); en->E3 = ctx->d_E3.as<float>();
@@ -1447,6 +1497,7 @@ extern "C" ppm_status ppm_profile_noalloc(ppm_ctx *ctx, const ppm_params *p, con
     A.n_protect = ctx->n_protect; A.nmu_pad = ctx->nmu_pad; A.strategy = ctx->interp;
     A.I = ctx->d_I.as<float>(); A.logT = ctx->d_logT.as<double>();
     A.logg = ctx->d_logg.as<double>(); A.mu = ctx->d_mu.as<float>();
+    set_mu_lookups(ctx, &A);
     A.lnE0 = ctx->lnE0_t; A.dlnE = ctx->dlnE_t;
     EnergyDev en;
     en.nE = nE; en.nEpad = L.nEpad; en.sliding = sliding;

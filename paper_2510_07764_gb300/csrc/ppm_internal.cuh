@@ -75,7 +75,16 @@ struct AtmDev {
     const double *logg;      // [ng]
     const float *mu;         // [nmu]
     double lnE0, dlnE;       // uniform ln E axis
+    // mu lookups: mu_idx[b] an interval near the start of bin b of kMuBins
+    // equal bins over [mu_0, mu_last] (mu_bin = kMuBins / (mu_last - mu_0));
+    // mu_rden[s] the reciprocal denominators of the four Lagrange weights on
+    // nodes s .. s + 3; mu_rlin[i] = 1 / (mu_{i+1} - mu_i)
+    const int *mu_idx;
+    const float4 *mu_rden;
+    const float *mu_rlin;
+    float mu_bin;
 };
+constexpr int kMuBins = 1024;
 
 // Per-instance plan entry (host-built).
 struct InstPlan {

@@ -63,16 +63,19 @@ __device__ __forceinline__ float transpose_reduce16(float (&acc)[kEC], int lane)
     return acc[0] + __shfl_xor_sync(kFull, acc[0], 16);
 }
 
-// Template value at observed phase phip (linear, lower-bound search on phi_o).
+// Template value at observed phase phip (linear in the interval of phi_o
+// that holds it: the last lo <= n_fp - 1 with phi_o[lo] <= phip, else 0).
+// The fine phases are nearly uniform over one cycle (phi_o = fine phase plus
+// a slowly varying time delay), so the search starts at the uniform guess
+// and moves by single steps.
 __device__ __forceinline__ void template_at(const float *__restrict__ ph, int n_fp, int top,
                                             float phip, float &Fp, float &zp, float &mp)
 {
+    (void)top;
     const float *F = ph + (n_fp + 1), *Z = F + (n_fp + 1), *M = Z + (n_fp + 1);
-    int lo = 0;
-    for (int step = top; step > 0; step >>= 1) {
-        const int c = lo + step;
-        if (c <= n_fp - 1 && ph[c] <= phip) lo = c;
-    }
+    int lo = min(max((int)((phip - ph[0]) * (float)n_fp), 0), n_fp - 1);
+    while (lo > 0 && ph[lo] > phip) --lo;
+    while (lo + 1 <= n_fp - 1 && ph[lo + 1] <= phip) ++lo;
     float w = (phip - ph[lo]) / (ph[lo + 1] - ph[lo]);
     w = fminf(fmaxf(w, 0.0f), 1.0f);
     Fp = fmaf(F[lo + 1] - F[lo], w, F[lo]);
@@ -105,13 +108,12 @@ __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, c
     template_at(ph, n_fp, top, phip, Fp, zp, mp);
     if (!(Fp != 0.0f && zp > 0.0f && zp < 1e30f)) return P;
     const int nmu = A.nmu;
-    // mu: clamp, interval, mixed-order weights (Sect. 4)
+    // mu: clamp, interval (the last i <= nmu - 2 with mu_i <= mu: from the
+    // bin's entry by single steps), mixed-order weights (Sect. 4)
     const float mu = fminf(fmaxf(mp, mun[0]), mun[nmu - 1]);
-    int i = 0;
-    for (int step = 64; step > 0; step >>= 1) {
-        const int c = i + step;
-        if (c <= nmu - 2 && mun[c] <= mu) i = c;
-    }
+    int i = __ldg(A.mu_idx + min(max((int)((mu - mun[0]) * A.mu_bin), 0), kMuBins - 1));
+    while (i > 0 && mun[i] > mu) --i;
+    while (i + 1 <= nmu - 2 && mun[i + 1] <= mu) ++i;
     float w[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     int s0;
     // A, B (ONESIDED): cubic on four nodes moved inside the grid; C, D:
@@ -119,13 +121,15 @@ __device__ __forceinline__ PairW pair_weights(bool on, float s, float phi_out, c
     if (ONESIDED || (i >= 1 && i + 2 <= nmu - 1 && i >= A.n_protect - 1)) {
         s0 = ONESIDED ? min(max(i - 1, 0), nmu - 4) : i - 1;
         const float x0 = mun[s0], x1 = mun[s0 + 1], x2 = mun[s0 + 2], x3 = mun[s0 + 3];
-        w[0] = (mu - x1) * (mu - x2) * (mu - x3) / ((x0 - x1) * (x0 - x2) * (x0 - x3));
-        w[1] = (mu - x0) * (mu - x2) * (mu - x3) / ((x1 - x0) * (x1 - x2) * (x1 - x3));
-        w[2] = (mu - x0) * (mu - x1) * (mu - x3) / ((x2 - x0) * (x2 - x1) * (x2 - x3));
-        w[3] = (mu - x0) * (mu - x1) * (mu - x2) / ((x3 - x0) * (x3 - x1) * (x3 - x2));
+        const float4 rd = __ldg(A.mu_rden + s0);  // reciprocal Lagrange denominators
+        const float d0 = mu - x0, d1 = mu - x1, d2 = mu - x2, d3 = mu - x3;
+        w[0] = d1 * d2 * d3 * rd.x;
+        w[1] = d0 * d2 * d3 * rd.y;
+        w[2] = d0 * d1 * d3 * rd.z;
+        w[3] = d0 * d1 * d2 * rd.w;
     } else {
         s0 = min(max(i - 1, 0), nmu - 4);
-        const float t = (mu - mun[i]) / (mun[i + 1] - mun[i]);
+        const float t = (mu - mun[i]) * __ldg(A.mu_rlin + i);
         const int o = i - s0;
 #pragma unroll
         for (int a = 0; a < 4; ++a) w[a] = (a == o) ? 1.0f - t : ((a == o + 1) ? t : 0.0f);
