@@ -757,6 +757,20 @@ __device__ __forceinline__ float4 f4fma(float4 a, float s, float4 c)
     return make_float4(fmaf(a.x, s, c.x), fmaf(a.y, s, c.y), fmaf(a.z, s, c.z), fmaf(a.w, s, c.w));
 }
 
+// combined cubic of a reference interval from the moments of its four
+// nodes m[0..3] (relative nodes r - 1 .. r + 2): sum_j c_j(M_j) (tau + eps)^j
+// collected by powers of tau
+__device__ __forceinline__ float4 combined_cubic(const float4 *m)
+{
+    const float4 m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+    const float4 a = cubic_coefs(m0.x, m1.x, m2.x, m3.x);   // of M_0
+    const float4 b = cubic_coefs(m0.y, m1.y, m2.y, m3.y);   // of M_1
+    const float4 c2 = cubic_coefs(m0.z, m1.z, m2.z, m3.z);  // of M_2
+    const float4 c3 = cubic_coefs(m0.w, m1.w, m2.w, m3.w);  // of M_3
+    return make_float4(a.x + b.y + c2.z + c3.w, fmaf(3.0f, c2.w, fmaf(2.0f, b.z, a.y)),
+                       fmaf(3.0f, b.w, a.z), a.w);
+}
+
 // weight of stencil entry d (0..3) of a slot, 0 outside
 __device__ __forceinline__ float stencil_w(int d, float w0, float w1, float w2, float w3)
 {
@@ -852,43 +866,41 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
         }
         __syncwarp();
 
-        // moments of relative nodes m = -2 .. rmax + 3 (index m + 2), one
-        // node per lane: lanes read 32 consecutive rows of one column (odd
-        // row pitch: no bank conflicts) and the column weights by broadcast
+        // moments of relative nodes m = -2 .. rmax + 3 (index m + 2), two
+        // nodes per lane (m and m + 32): lanes read 32 consecutive rows of
+        // one column (odd row pitch: no bank conflicts) and the column
+        // weights by broadcast
         const float *sbase = slab + N0 * Pm + cmin;
-        for (int m0 = -2; m0 <= rmax + 3; m0 += 32) {
-            const int m = m0 + lane;
-            if (m <= rmax + 3) {
-                float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                const float *srow = sbase + m * Pm;
-                PPM_CHECK(N0 + m >= -kMomLead && N0 + m < A.nE + kSlabMargin, errp);
+        for (int m0 = -2; m0 <= rmax + 3; m0 += 64) {
+            const int ma = m0 + lane, mb = ma + 32;
+            if (ma <= rmax + 3) {
+                const bool inb = mb <= rmax + 3;
+                float4 acc_a = make_float4(0.0f, 0.0f, 0.0f, 0.0f), acc_b = acc_a;
+                const float *ra = sbase + ma * Pm;
+                const float *rb = inb ? ra + 32 * Pm : ra;
+                PPM_CHECK(N0 + ma >= -kMomLead && N0 + (inb ? mb : ma) < A.nE + kSlabMargin, errp);
 #pragma unroll 4
-                for (int q = 0; q < ncol; ++q) acc = f4fma(Om[q], srow[q], acc);
-                Mv[m + 2] = acc;
+                for (int q = 0; q < ncol; ++q) {
+                    const float4 om = Om[q];
+                    acc_a = f4fma(om, ra[q], acc_a);
+                    acc_b = f4fma(om, rb[q], acc_b);
+                }
+                Mv[ma + 2] = acc_a;
+                if (inb) Mv[mb + 2] = acc_b;
             }
         }
         __syncwarp();
         // combined cubic of reference interval r (moments of nodes r - 1 .. r + 2,
-        // indices r + 1 .. r + 4), written in place at index r + 1: a pass
-        // reads indices up to 32 past what it writes, which later passes no
-        // longer read
-        for (int r0 = 0; r0 <= rmax; r0 += 32) {
-            const int r = r0 + lane;
-            float4 Pv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (r <= rmax) {
-                const float4 m0 = Mv[r + 1], m1 = Mv[r + 2], m2 = Mv[r + 3], m3 = Mv[r + 4];
-                const float4 a = cubic_coefs(m0.x, m1.x, m2.x, m3.x);   // of M_0
-                const float4 b = cubic_coefs(m0.y, m1.y, m2.y, m3.y);   // of M_1
-                const float4 c2 = cubic_coefs(m0.z, m1.z, m2.z, m3.z);  // of M_2
-                const float4 c3 = cubic_coefs(m0.w, m1.w, m2.w, m3.w);  // of M_3
-                // sum_j c_j (tau + eps)^j collected by powers of tau
-                Pv.x = a.x + b.y + c2.z + c3.w;
-                Pv.y = fmaf(3.0f, c2.w, fmaf(2.0f, b.z, a.y));
-                Pv.z = fmaf(3.0f, b.w, a.z);
-                Pv.w = a.w;
-            }
+        // indices r + 1 .. r + 4), written in place at index r + 1, two
+        // intervals per lane: a pass reads indices up to 67 past its first
+        // and writes 64, which later passes no longer read
+        for (int r0 = 0; r0 <= rmax; r0 += 64) {
+            const int ra = r0 + lane, rb = ra + 32;
+            const float4 Pa = ra <= rmax ? combined_cubic(Mv + ra + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 Pb = rb <= rmax ? combined_cubic(Mv + rb + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
             __syncwarp();
-            if (r <= rmax) Mv[r + 1] = Pv;
+            if (ra <= rmax) Mv[ra + 1] = Pa;
+            if (rb <= rmax) Mv[rb + 1] = Pb;
             __syncwarp();
         }
 
