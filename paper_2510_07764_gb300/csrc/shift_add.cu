@@ -63,6 +63,24 @@ __device__ __forceinline__ float transpose_reduce16(float (&acc)[kEC], int lane)
     return acc[0] + __shfl_xor_sync(kFull, acc[0], 16);
 }
 
+// 8 accumulators per lane -> lanes l, l ^ 8, l ^ 16, l ^ 24 receive the warp
+// sum of accumulator l & 7
+__device__ __forceinline__ float transpose_reduce8(float (&acc)[8], int lane)
+{
+#pragma unroll
+    for (int off = 4; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const float send = upper ? acc[i] : acc[i + off];
+            const float keep = upper ? acc[i + off] : acc[i];
+            acc[i] = keep + __shfl_xor_sync(kFull, send, off);
+        }
+    }
+    const float t = acc[0] + __shfl_xor_sync(kFull, acc[0], 8);
+    return t + __shfl_xor_sync(kFull, t, 16);
+}
+
 // Template value at observed phase phip (linear in the interval of phi_o
 // that holds it: the last lo <= n_fp - 1 with phi_o[lo] <= phip, else 0).
 // The fine phases are nearly uniform over one cycle (phi_o = fine phase plus
@@ -727,12 +745,25 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
 constexpr int kMomLead = 2;         // zero rows below the table (relative node -2)
 constexpr int kMomCells = 32;       // mu columns of one group's stencils
 constexpr float kMomSpread = 0.35f; // widest ln z spread of a group, in table nodes
-// per warp: moments, then combined cubics, of the group's relative nodes
-// [nmom] float4; column weights [kMomCells + 4] float4; fourth differences
-// [2][kMomCells]
+constexpr int kMomBatch = 8;        // candidate energies whose difference terms run together
+constexpr int kCandCap = 4 * (kMomCells + 4);  // candidates listed per group
+// per warp, three regions:
+//   R0: moments, then combined cubics, of the group's relative nodes
+//       [nmom] float4; afterwards the fourth-difference rows and positions of
+//       a batch of candidates [kMomBatch][ncol] + [kMomBatch];
+//   R1: column weights [kMomCells + 4] float4; afterwards the list of
+//       candidate energies [kCandCap];
+//   R2: a small batch area [2 kMomCells] + [kMomBatch] (a full list is
+//       emptied during the pass over the energies, while R0 still holds
+//       the cubics)
+__host__ __device__ inline int mom_r0_floats(int nmom)
+{
+    const int a = 4 * nmom, b = kMomBatch * kMomCells + kMomBatch;
+    return a > b ? a : b;
+}
 __host__ __device__ inline int mom_warp_floats(int nmom)
 {
-    return 4 * nmom + 4 * (kMomCells + 4) + 2 * kMomCells;
+    return mom_r0_floats(nmom) + 4 * (kMomCells + 4) + 2 * kMomCells + kMomBatch;
 }
 // bytes per warp of the moment kernel's buffers: the moment buffers and the
 // node-major walk's ring share them (a group takes one walk or the other),
@@ -834,10 +865,10 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
         // extreme eps are those of the extreme slots
         const float emax = xmax - ref, emin = xmin - ref;
         const float ev[2] = {fast[0] ? X[0] - ref : 0.0f, fast[1] ? X[1] - ref : 0.0f};
-        float4 *Mv = reinterpret_cast<float4 *>(wbuf);                  // [nmom]
-        float4 *Om = reinterpret_cast<float4 *>(wbuf + 4 * nmom);       // [kMomCells + 4]
-        float *Dp = wbuf + 4 * nmom + 4 * (kMomCells + 4);             // [kMomCells]
-        float *Dm = Dp + kMomCells;                                     // [kMomCells]
+        const int r0f = mom_r0_floats(nmom);
+        float4 *Mv = reinterpret_cast<float4 *>(wbuf);                  // R0: [nmom]
+        float4 *Om = reinterpret_cast<float4 *>(wbuf + r0f);            // R1: [kMomCells + 4]
+        float *Dp = wbuf + r0f + 4 * (kMomCells + 4);                  // R2: [2 kMomCells + kMomBatch]
         int cell0[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) cell0[e] = fast[e] ? s0v[e] - cmin : -8;
@@ -904,60 +935,87 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
             __syncwarp();
         }
 
-        // energies: one per lane, the combined cubic at tau, plus the
-        // difference terms of slots that left the reference interval
-        for (int k0 = 0; k0 < nE; k0 += 32) {
-            const int k = k0 + lane;
-            const bool in = k < nE;
-            float tau = 0.0f, val = 0.0f;
-            int r = 0;
-            if (in) {
-                const float y = dref + (spk[k] - pk0);
-                const float rf = floorf(y);
-                r = (int)rf;
-                tau = y - rf;
-                const float4 Pv = Mv[r + 1];
-                val = fmaf(tau, fmaf(tau, fmaf(tau, Pv.w, Pv.z), Pv.y), Pv.x);
-            }
-            unsigned cand = __ballot_sync(kFull, in && (tau + emax >= 1.0f || tau + emin < 0.0f));
-            while (cand) {
-                const int bl = __ffs(cand) - 1;
-                cand &= cand - 1;
-                const float tb = __shfl_sync(kFull, tau, bl);
-                const int rb = __shfl_sync(kFull, r, bl);
-                const bool up = tb + emax >= 1.0f, down = tb + emin < 0.0f;
-                // fourth differences of the columns on relative nodes rb - 1 ..
-                // rb + 3 (up) and rb - 2 .. rb + 2 (down)
-                if (lane < ncol) {
-                    const float *c = sbase + (rb - 2) * Pm + lane;
-                    const float s0 = c[0], s1 = c[Pm], s2 = c[2 * Pm], s3 = c[3 * Pm];
-                    const float s4 = c[4 * Pm];
-                    if (up) {
-                        const float s5 = c[5 * Pm];
-                        Dp[lane] = fmaf(6.0f, s3, fmaf(-4.0f, s2 + s4, s1 + s5));
-                    }
-                    if (down) Dm[lane] = fmaf(6.0f, s2, fmaf(-4.0f, s1 + s3, s0 + s4));
+        // energies: one per lane, the combined cubic at tau.  Energies
+        // within the group's spread of a node (candidates) also need the
+        // difference terms of slots on the far side of the node: they are
+        // listed, and their terms are added kMomBatch at a time after the
+        // last pass (R0 is free then: the cubics are spent), or during the
+        // passes when the list is full (in R2).  A candidate within emax of
+        // the node above (tau + emax >= 1) has slots only past that node
+        // (|eps| < 1/2 keeps tau + eps > 0), one within -emin of the node
+        // below only slots before it, so each needs one row of fourth
+        // differences of the group's columns, on relative nodes r - 1 .. r + 3
+        // or r - 2 .. r + 2; the terms of a batch are reduced by one
+        // transposition and added in candidate order.
+        int *clist = reinterpret_cast<int *>(Om);  // R1 (the column weights are spent)
+        int nc = 0;
+        const float inv_ncol = 1.0f / (float)ncol;
+        for (int k0 = 0;; k0 += 32) {
+            const bool last = k0 >= nE;
+            unsigned cand = 0u;
+            int k = k0 + lane;
+            if (!last) {
+                float tau = 0.0f;
+                const bool in = k < nE;
+                if (in) {
+                    const float y = dref + (spk[k] - pk0);
+                    const float rf = floorf(y);
+                    tau = y - rf;
+                    const float4 Pv = Mv[(int)rf + 1];
+                    frow[k] += fmaf(tau, fmaf(tau, fmaf(tau, Pv.w, Pv.z), Pv.y), Pv.x);
                 }
-                __syncwarp();
-                float cs = 0.0f;
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const float te = tb + ev[e];
-                    if (fast[e] && (te >= 1.0f || te < 0.0f)) {
-                        const float *D = (te >= 1.0f ? Dp : Dm) + cell0[e];
-                        const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
-                                              fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
-                        const float g = te >= 1.0f ? te * (te - 1.0f) * (te - 2.0f)
-                                                   : -(te + 1.0f) * te * (te - 1.0f);
-                        cs = fmaf(g * (1.0f / 6.0f), dv, cs);
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) cs += __shfl_xor_sync(kFull, cs, o);
-                if (lane == bl) val += cs;
-                __syncwarp();
+                cand = __ballot_sync(kFull, in && (tau + emax >= 1.0f || tau + emin < 0.0f));
             }
-            if (in) frow[k] += val;
+            if (last || nc + __popc(cand) > kCandCap) {
+                __syncwarp();
+                float *Drow = last ? wbuf : Dp;
+                float *tauc = Drow + (last ? kMomBatch * kMomCells : 2 * kMomCells);
+                const int nbmax = last ? kMomBatch : min(kMomBatch, 2 * kMomCells / ncol);
+                for (int cb = 0; cb < nc; cb += nbmax) {
+                    const int nb = min(nbmax, nc - cb);
+                    for (int q = lane; q < nb * ncol; q += 32) {
+                        const int ci = (int)(((float)q + 0.5f) * inv_ncol);
+                        const int col = q - ci * ncol;
+                        const int kc = clist[cb + ci];
+                        const float y = dref + (spk[kc] - pk0);
+                        const float rf = floorf(y);
+                        const float tau = y - rf;
+                        const int base = (int)rf - (tau + emax >= 1.0f ? 1 : 2);
+                        const float *c = sbase + base * Pm + col;
+                        Drow[ci * ncol + col] =
+                            fmaf(6.0f, c[2 * Pm], fmaf(-4.0f, c[Pm] + c[3 * Pm], c[0] + c[4 * Pm]));
+                        if (col == 0) tauc[ci] = tau;
+                    }
+                    __syncwarp();
+                    float acc[kMomBatch];
+#pragma unroll
+                    for (int ci = 0; ci < kMomBatch; ++ci) {
+                        acc[ci] = 0.0f;
+                        if (ci < nb) {
+                            const float tb = tauc[ci];
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float te = tb + ev[e];
+                                if (fast[e] && (te >= 1.0f || te < 0.0f)) {
+                                    const float *D = Drow + ci * ncol + cell0[e];
+                                    const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
+                                                          fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
+                                    const float g = te >= 1.0f ? te * (te - 1.0f) * (te - 2.0f)
+                                                               : -(te + 1.0f) * te * (te - 1.0f);
+                                    acc[ci] = fmaf(g * (1.0f / 6.0f), dv, acc[ci]);
+                                }
+                            }
+                        }
+                    }
+                    const float tot = transpose_reduce8(acc, lane);
+                    if (lane < nb) frow[clist[cb + lane]] += tot;
+                    __syncwarp();
+                }
+                nc = 0;
+                if (last) break;
+            }
+            if (cand & (1u << lane)) clist[nc + __popc(cand & ((1u << lane) - 1u))] = k;
+            nc += __popc(cand);
         }
         __syncwarp();
     }

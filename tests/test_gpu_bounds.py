@@ -63,7 +63,8 @@ ctx.sync()
 for name, (lo, hi, n, spin, zeta) in {"mw": (0.5, 6.0, 159, 205.0, None),
                                       "mwlow": (0.052, 0.32, 58, 205.0, None),
                                       "mwedge": (3.5, 7.8, 56, 205.0, None),
-                                      "mwwide": (0.6, 2.6, 96, 600.0, [0.6, 0.7])}.items():
+                                      "mwwide": (0.6, 2.6, 96, 600.0, [0.6, 0.7]),
+                                      "mwfine": (0.6, 2.6, 900, 205.0, None)}.items():
     v = synth.atm_two_spot(n_theta=12, n_phi=40, n_phase=24, n_E=n, n_chan=20, atm=atm, lens=lens)
     v.E_keV = synth.logspace(lo, hi, n)
     v.inst.spin_hz[:] = spin

@@ -306,6 +306,20 @@ def test_moment_walk_wide_groups(orc, synth, atm, small_lens, wiggle):
     assert max_rel(mom, orc.profile(w)) < TOL_ATM
 
 
+def test_moment_walk_fine_grid(orc, synth, atm, small_lens):
+    """900 energies at 0.05 table node per step: groups list more candidate
+    energies (energies within their spread of a node) than the per-group
+    list holds, and the rest of a pass takes them one at a time; groups
+    too wide for the moment walk take the energy walk (the step is below
+    the node-major walk's)."""
+    w = _workload(synth, atm, small_lens, 900, 0.6, 2.6, n_phase=12)
+    assert _step(w, atm) < 0.06
+    mom, energy = _walks(w, (0, 1))
+    assert not np.array_equal(mom, energy)
+    assert max_rel(mom, energy) < TOL_WALKS
+    assert max_rel(mom, orc.profile(w)) < TOL_ATM
+
+
 def test_moment_walk_crescent(orc, synth, atm):
     """The crescent geometry (narrow groups: difference terms at a few per
     cent of the energies) on its 300-energy grid."""
