@@ -871,7 +871,7 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
         float *Dp = wbuf + r0f + 4 * (kMomCells + 4);                  // R2: [2 kMomCells + kMomBatch]
         int cell0[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) cell0[e] = fast[e] ? s0v[e] - cmin : -8;
+        for (int e = 0; e < 2; ++e) cell0[e] = fast[e] ? s0v[e] - cmin : 0;  // zero weights outside
         const float2 E1 = make_float2(ev[0], ev[1]);
         const float2 E2 = __fmul2_rn(E1, E1);
         const float2 E3 = __fmul2_rn(E2, E1);
@@ -973,6 +973,7 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
                 const int nbmax = last ? kMomBatch : min(kMomBatch, 2 * kMomCells / ncol);
                 for (int cb = 0; cb < nc; cb += nbmax) {
                     const int nb = min(nbmax, nc - cb);
+#pragma unroll 2
                     for (int q = lane; q < nb * ncol; q += 32) {
                         const int ci = (int)(((float)q + 0.5f) * inv_ncol);
                         const int col = q - ci * ncol;
@@ -992,18 +993,20 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
                     for (int ci = 0; ci < kMomBatch; ++ci) {
                         acc[ci] = 0.0f;
                         if (ci < nb) {
+                            // branch-free (the eight candidates interleave): a
+                            // slot on the near side has g = 0, one outside the
+                            // window zero weights
                             const float tb = tauc[ci];
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const float te = tb + ev[e];
-                                if (fast[e] && (te >= 1.0f || te < 0.0f)) {
-                                    const float *D = Drow + ci * ncol + cell0[e];
-                                    const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
-                                                          fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
-                                    const float g = te >= 1.0f ? te * (te - 1.0f) * (te - 2.0f)
-                                                               : -(te + 1.0f) * te * (te - 1.0f);
-                                    acc[ci] = fmaf(g * (1.0f / 6.0f), dv, acc[ci]);
-                                }
+                                const float *D = Drow + ci * ncol + cell0[e];
+                                const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
+                                                      fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
+                                const float gp = te * (te - 1.0f) * (te - 2.0f);
+                                const float gm = -(te + 1.0f) * te * (te - 1.0f);
+                                const float g = te >= 1.0f ? gp : (te < 0.0f ? gm : 0.0f);
+                                acc[ci] = fmaf(g * (1.0f / 6.0f), dv, acc[ci]);
                             }
                         }
                     }
