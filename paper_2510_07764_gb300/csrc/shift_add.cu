@@ -875,6 +875,8 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
         const float2 E1 = make_float2(ev[0], ev[1]);
         const float2 E2 = __fmul2_rn(E1, E1);
         const float2 E3 = __fmul2_rn(E2, E1);
+        const float2 W0 = make_float2(wv[0][0], wv[1][0]), W1 = make_float2(wv[0][1], wv[1][1]);
+        const float2 W2 = make_float2(wv[0][2], wv[1][2]), W3 = make_float2(wv[0][3], wv[1][3]);
 
         // column weights Omega_j, four columns per pass, summed over the
         // slots in a fixed order (slot sums, then the warp transpose-reduction)
@@ -993,24 +995,35 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
                     for (int ci = 0; ci < kMomBatch; ++ci) {
                         acc[ci] = 0.0f;
                         if (ci < nb) {
-                            // branch-free (the eight candidates interleave): a
-                            // slot on the near side has g = 0, one outside the
-                            // window zero weights
+                            // both slots packed, without data-dependent branches
+                            // (the candidates interleave): a slot on the near
+                            // side gets g = 0, one outside the window has zero
+                            // weights.  Past the node above, 6 g = t (t - 1) (t - 2)
+                            // = t (t (t - 3) + 2); before the node below,
+                            // 6 g = -(t + 1) t (t - 1) = t (1 - t^2)
                             const float tb = tauc[ci];
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float te = tb + ev[e];
-                                const float *D = Drow + ci * ncol + cell0[e];
-                                const float dv = fmaf(wv[e][3], D[3], fmaf(wv[e][2], D[2],
-                                                      fmaf(wv[e][1], D[1], wv[e][0] * D[0])));
-                                const float gp = te * (te - 1.0f) * (te - 2.0f);
-                                const float gm = -(te + 1.0f) * te * (te - 1.0f);
-                                const float g = te >= 1.0f ? gp : (te < 0.0f ? gm : 0.0f);
-                                acc[ci] = fmaf(g * (1.0f / 6.0f), dv, acc[ci]);
+                            const float2 te = __fadd2_rn(make_float2(tb, tb), E1);
+                            const float *D0 = Drow + ci * ncol;
+                            const float *Da = D0 + cell0[0], *Db = D0 + cell0[1];
+                            float2 dv = __fmul2_rn(W0, make_float2(Da[0], Db[0]));
+                            dv = __ffma2_rn(W1, make_float2(Da[1], Db[1]), dv);
+                            dv = __ffma2_rn(W2, make_float2(Da[2], Db[2]), dv);
+                            dv = __ffma2_rn(W3, make_float2(Da[3], Db[3]), dv);
+                            float2 g;
+                            if (tb + emax >= 1.0f) {  // warp-uniform
+                                const float2 p = __fmul2_rn(te, __ffma2_rn(te, __fadd2_rn(te, make_float2(-3.0f, -3.0f)),
+                                                                            make_float2(2.0f, 2.0f)));
+                                g = make_float2(te.x >= 1.0f ? p.x : 0.0f, te.y >= 1.0f ? p.y : 0.0f);
+                            } else {
+                                const float2 p = __fmul2_rn(te, __ffma2_rn(__fmul2_rn(te, make_float2(-1.0f, -1.0f)), te,
+                                                                            make_float2(1.0f, 1.0f)));
+                                g = make_float2(te.x < 0.0f ? p.x : 0.0f, te.y < 0.0f ? p.y : 0.0f);
                             }
+                            const float2 c = __fmul2_rn(g, dv);
+                            acc[ci] = c.x + c.y;
                         }
                     }
-                    const float tot = transpose_reduce8(acc, lane);
+                    const float tot = transpose_reduce8(acc, lane) * (1.0f / 6.0f);
                     if (lane < nb) frow[clist[cb + lane]] += tot;
                     __syncwarp();
                 }
