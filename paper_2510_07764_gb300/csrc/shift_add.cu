@@ -744,7 +744,7 @@ __device__ __forceinline__ void atm_group_nodes(int g0, int n_act, int lane, flo
 // ---------------------------------------------------------------------------
 constexpr int kMomLead = 2;         // zero rows below the table (relative node -2)
 constexpr int kMomCells = 32;       // mu columns of one group's stencils
-constexpr float kMomSpread = 0.35f; // widest ln z spread of a group, in table nodes
+constexpr float kMomSpread = 0.45f; // widest ln z spread of a group, in table nodes
 constexpr int kMomBatch = 8;        // candidate energies whose difference terms run together
 constexpr int kCandCap = 4 * (kMomCells + 4);  // candidates listed per group
 // per warp, three regions:
@@ -952,87 +952,84 @@ __device__ __forceinline__ bool atm_group_moments(int g0, int n_act, int lane, f
         int *clist = reinterpret_cast<int *>(Om);  // R1 (the column weights are spent)
         int nc = 0;
         const float inv_ncol = 1.0f / (float)ncol;
-        for (int k0 = 0;; k0 += 32) {
-            const bool last = k0 >= nE;
-            unsigned cand = 0u;
-            int k = k0 + lane;
-            if (!last) {
-                float tau = 0.0f;
-                const bool in = k < nE;
-                if (in) {
-                    const float y = dref + (spk[k] - pk0);
-                    const float rf = floorf(y);
-                    tau = y - rf;
-                    const float4 Pv = Mv[(int)rf + 1];
-                    frow[k] += fmaf(tau, fmaf(tau, fmaf(tau, Pv.w, Pv.z), Pv.y), Pv.x);
-                }
-                cand = __ballot_sync(kFull, in && (tau + emax >= 1.0f || tau + emin < 0.0f));
-            }
-            if (last || nc + __popc(cand) > kCandCap) {
-                __syncwarp();
-                float *Drow = last ? wbuf : Dp;
-                float *tauc = Drow + (last ? kMomBatch * kMomCells : 2 * kMomCells);
-                const int nbmax = last ? kMomBatch : min(kMomBatch, 2 * kMomCells / ncol);
-                for (int cb = 0; cb < nc; cb += nbmax) {
-                    const int nb = min(nbmax, nc - cb);
+        auto flush = [&](float *Drow, float *tauc, int nbmax) {
+            for (int cb = 0; cb < nc; cb += nbmax) {
+                const int nb = min(nbmax, nc - cb);
 #pragma unroll 2
-                    for (int q = lane; q < nb * ncol; q += 32) {
-                        const int ci = (int)(((float)q + 0.5f) * inv_ncol);
-                        const int col = q - ci * ncol;
-                        const int kc = clist[cb + ci];
-                        const float y = dref + (spk[kc] - pk0);
-                        const float rf = floorf(y);
-                        const float tau = y - rf;
-                        const int base = (int)rf - (tau + emax >= 1.0f ? 1 : 2);
-                        const float *c = sbase + base * Pm + col;
-                        Drow[ci * ncol + col] =
-                            fmaf(6.0f, c[2 * Pm], fmaf(-4.0f, c[Pm] + c[3 * Pm], c[0] + c[4 * Pm]));
-                        if (col == 0) tauc[ci] = tau;
-                    }
-                    __syncwarp();
-                    float acc[kMomBatch];
-#pragma unroll
-                    for (int ci = 0; ci < kMomBatch; ++ci) {
-                        acc[ci] = 0.0f;
-                        if (ci < nb) {
-                            // both slots packed, without data-dependent branches
-                            // (the candidates interleave): a slot on the near
-                            // side gets g = 0, one outside the window has zero
-                            // weights.  Past the node above, 6 g = t (t - 1) (t - 2)
-                            // = t (t (t - 3) + 2); before the node below,
-                            // 6 g = -(t + 1) t (t - 1) = t (1 - t^2)
-                            const float tb = tauc[ci];
-                            const float2 te = __fadd2_rn(make_float2(tb, tb), E1);
-                            const float *D0 = Drow + ci * ncol;
-                            const float *Da = D0 + cell0[0], *Db = D0 + cell0[1];
-                            float2 dv = __fmul2_rn(W0, make_float2(Da[0], Db[0]));
-                            dv = __ffma2_rn(W1, make_float2(Da[1], Db[1]), dv);
-                            dv = __ffma2_rn(W2, make_float2(Da[2], Db[2]), dv);
-                            dv = __ffma2_rn(W3, make_float2(Da[3], Db[3]), dv);
-                            float2 g;
-                            if (tb + emax >= 1.0f) {  // warp-uniform
-                                const float2 p = __fmul2_rn(te, __ffma2_rn(te, __fadd2_rn(te, make_float2(-3.0f, -3.0f)),
-                                                                            make_float2(2.0f, 2.0f)));
-                                g = make_float2(te.x >= 1.0f ? p.x : 0.0f, te.y >= 1.0f ? p.y : 0.0f);
-                            } else {
-                                const float2 p = __fmul2_rn(te, __ffma2_rn(__fmul2_rn(te, make_float2(-1.0f, -1.0f)), te,
-                                                                            make_float2(1.0f, 1.0f)));
-                                g = make_float2(te.x < 0.0f ? p.x : 0.0f, te.y < 0.0f ? p.y : 0.0f);
-                            }
-                            const float2 c = __fmul2_rn(g, dv);
-                            acc[ci] = c.x + c.y;
-                        }
-                    }
-                    const float tot = transpose_reduce8(acc, lane) * (1.0f / 6.0f);
-                    if (lane < nb) frow[clist[cb + lane]] += tot;
-                    __syncwarp();
+                for (int q = lane; q < nb * ncol; q += 32) {
+                    const int ci = (int)(((float)q + 0.5f) * inv_ncol);
+                    const int col = q - ci * ncol;
+                    const int kc = clist[cb + ci];
+                    const float y = dref + (spk[kc] - pk0);
+                    const float rf = floorf(y);
+                    const float tau = y - rf;
+                    const int base = (int)rf - (tau + emax >= 1.0f ? 1 : 2);
+                    const float *c = sbase + base * Pm + col;
+                    Drow[ci * ncol + col] =
+                        fmaf(6.0f, c[2 * Pm], fmaf(-4.0f, c[Pm] + c[3 * Pm], c[0] + c[4 * Pm]));
+                    if (col == 0) tauc[ci] = tau;
                 }
-                nc = 0;
-                if (last) break;
+                __syncwarp();
+                float acc[kMomBatch];
+#pragma unroll
+                for (int ci = 0; ci < kMomBatch; ++ci) {
+                    acc[ci] = 0.0f;
+                    if (ci < nb) {
+                        // both slots packed, without data-dependent branches
+                        // (the candidates interleave): a slot on the near
+                        // side gets g = 0, one outside the window has zero
+                        // weights.  Past the node above, 6 g = t (t - 1) (t - 2)
+                        // = t (t (t - 3) + 2); before the node below,
+                        // 6 g = -(t + 1) t (t - 1) = t (1 - t^2)
+                        const float tb = tauc[ci];
+                        const float2 te = __fadd2_rn(make_float2(tb, tb), E1);
+                        const float *D0 = Drow + ci * ncol;
+                        const float *Da = D0 + cell0[0], *Db = D0 + cell0[1];
+                        float2 dv = __fmul2_rn(W0, make_float2(Da[0], Db[0]));
+                        dv = __ffma2_rn(W1, make_float2(Da[1], Db[1]), dv);
+                        dv = __ffma2_rn(W2, make_float2(Da[2], Db[2]), dv);
+                        dv = __ffma2_rn(W3, make_float2(Da[3], Db[3]), dv);
+                        float2 g;
+                        if (tb + emax >= 1.0f) {  // warp-uniform
+                            const float2 p = __fmul2_rn(te, __ffma2_rn(te, __fadd2_rn(te, make_float2(-3.0f, -3.0f)),
+                                                                        make_float2(2.0f, 2.0f)));
+                            g = make_float2(te.x >= 1.0f ? p.x : 0.0f, te.y >= 1.0f ? p.y : 0.0f);
+                        } else {
+                            const float2 p = __fmul2_rn(te, __ffma2_rn(__fmul2_rn(te, make_float2(-1.0f, -1.0f)), te,
+                                                                        make_float2(1.0f, 1.0f)));
+                            g = make_float2(te.x < 0.0f ? p.x : 0.0f, te.y < 0.0f ? p.y : 0.0f);
+                        }
+                        const float2 c = __fmul2_rn(g, dv);
+                        acc[ci] = c.x + c.y;
+                    }
+                }
+                const float tot = transpose_reduce8(acc, lane) * (1.0f / 6.0f);
+                if (lane < nb) frow[clist[cb + lane]] += tot;
+                __syncwarp();
+            }
+            nc = 0;
+        };
+        for (int k0 = 0; k0 < nE; k0 += 32) {
+            const int k = k0 + lane;
+            const bool in = k < nE;
+            float tau = 0.0f;
+            if (in) {
+                const float y = dref + (spk[k] - pk0);
+                const float rf = floorf(y);
+                tau = y - rf;
+                const float4 Pv = Mv[(int)rf + 1];
+                frow[k] += fmaf(tau, fmaf(tau, fmaf(tau, Pv.w, Pv.z), Pv.y), Pv.x);
+            }
+            const unsigned cand = __ballot_sync(kFull, in && (tau + emax >= 1.0f || tau + emin < 0.0f));
+            if (nc + __popc(cand) > kCandCap) {  // the list is full: its terms now, in R2
+                __syncwarp();
+                flush(Dp, Dp + 2 * kMomCells, min(kMomBatch, 2 * kMomCells / ncol));
             }
             if (cand & (1u << lane)) clist[nc + __popc(cand & ((1u << lane) - 1u))] = k;
             nc += __popc(cand);
         }
+        __syncwarp();
+        flush(wbuf, wbuf + kMomBatch * kMomCells, kMomBatch);  // R0: the cubics are spent
         __syncwarp();
     }
 
