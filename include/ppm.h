@@ -336,11 +336,13 @@ ppm_status ppm_loglike_grad(ppm_ctx *ctx, const ppm_params *p, const ppm_res *re
  *   - 0 (default): as 2, except that the forward shift-and-add of spots takes
  *     the moment walk wherever the observed energies step by less than one
  *     table node and the interpolation strategy is not B: per group of 64
- *     elements the moments sum_p eps_p^j u_p of the node values (eps_p the
- *     element's offset from the group's reference position, j = 0..3) are
- *     contracted once per table node from cell weights over the group's
- *     stencil cells, and each energy evaluates one combined cubic, plus exact
- *     difference terms for elements on the other side of a node.
+ *     elements whose ln z spread is below 0.45 table node and whose mu
+ *     stencils span at most 32 columns, the moments sum_p eps_p^j u_p of the
+ *     node values (eps_p the element's offset from the group's reference
+ *     position, j = 0..3) are contracted once per table node from column
+ *     weights, and each energy evaluates one combined cubic, plus exact
+ *     difference terms for elements on the other side of a node; other
+ *     groups take the node-major walk (uniform grids) or the energy walk.
  * All walks evaluate the same interpolants; they differ in the order of the
  * FP32 sums (and, for the node-major walk, in positions accumulated along
  * the grid).  With the node-major or moment walk, phase_tile = 0 picks 16
