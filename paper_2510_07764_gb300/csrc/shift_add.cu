@@ -10,11 +10,20 @@
 //     of a stencil are four consecutive words).
 // Each warp owns one output phase at a time; its lanes are 32 elements of
 // the ring (neighbouring elements see nearly the same redshift and emission
-// angle, so their table reads are broadcast-friendly).  For each element the
-// mu stencil is contracted once per table energy node (4 FMA) and the cubic
-// in ln E of the current node interval is kept as power-basis coefficients
-// in registers (packed FP32 pairs of elements).  Two walks through the
-// observed energies:
+// angle, so their table reads are broadcast-friendly).  Three walks through
+// the observed energies:
+//   - moment walk (the default for spots; atm_group_moments): per group of
+//     64 elements with a ln z spread below 0.45 table node, the moments
+//     sum_p eps_p^j u_p of the elements' node values are contracted once
+//     per table node from column weights over the group's mu stencils; each
+//     energy evaluates one combined cubic, and energies within the group's
+//     spread of a node add exact difference terms for the elements on the
+//     far side (listed, then handled eight at a time); other groups take
+//     one of the two walks below.
+// In those two, each element's mu stencil is contracted once per table
+// energy node (4 FMA) and the cubic in ln E of the current node interval is
+// kept as power-basis coefficients in registers (packed FP32 pairs of
+// elements):
 //   - node-major (energy grids uniform in ln E with 0.34-0.498 table node
 //     per step): every element of the warp moves one table interval per
 //     iteration and evaluates the two or three energies inside it; the
